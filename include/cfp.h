@@ -1,0 +1,237 @@
+/*
+ * cfp.h -- C ABI of the GB300 (sm_103a) fourth-order compact Poisson solver
+ * with immersed Dirichlet bodies (Hosseinverdi & Fasel, arXiv 1901.08269).
+ *
+ * Problem (Sec. 1, Eq. poisson): Laplace(u) = f in the fluid region of the
+ * box [x_1,x_nx] x [y_1,y_ny] x [z_1,z_nz]; u = g on the box faces and on
+ * the body surfaces Gamma; u = 0 inside the bodies.
+ *
+ * Conventions shared by every entry point:
+ *  - Grid: three strictly increasing coordinate arrays (Sec. 2).  Node
+ *    (i,j,k), 0-based, has linear index i + nx*(j + ny*k) (x fastest).
+ *    A "field" is an FP64 array of N = nx*ny*nz values in that order.
+ *  - Pointers named *_dev are CUDA device pointers on the context's device
+ *    (for instance torch CUDA tensors); *_host are host pointers.
+ *  - The caller owns every array it passes; the context owns its internal
+ *    buffers and frees them in cfp_ctx_destroy.
+ *  - Calls are ordered on the context's stream.  Calls that return host
+ *    values (counts, cfp_info) synchronise that stream before returning.
+ *  - Errors: every call returns a cfp_status; no call aborts, traps or
+ *    exits.  cfp_last_error() returns a message for the calling thread.
+ *  - One context may be used by one host thread at a time.
+ */
+#ifndef CFP_H
+#define CFP_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CFP_OK = 0,
+    CFP_EINVAL = 1,      /* bad argument (size, pointer, non-monotone grid) */
+    CFP_ENOMEM = 2,      /* device allocation failed                       */
+    CFP_ECUDA = 3,       /* a CUDA runtime call failed                      */
+    CFP_EGEOM = 4,       /* geometry outside what the stencils support      */
+    CFP_ENOCONV = 5,     /* iteration cap reached before the tolerance      */
+    CFP_EBREAKDOWN = 6,  /* BiCGSTAB breakdown persisted after restarts     */
+    CFP_ENAN = 7,        /* non-finite value met in the solve               */
+    CFP_ESTATE = 8       /* call out of order (e.g. solve before classify)  */
+} cfp_status;
+
+/* point types of Sec. 2, as written by cfp_classify_points */
+enum { CFP_BOUNDARY = 0, CFP_REGULAR = 1, CFP_IRREGULAR = 2, CFP_SOLID = 3 };
+
+/* implicit bodies: phi < 0 inside; a union of bodies takes the minimum */
+enum { CFP_SPHERE = 0, CFP_ELLIPSOID = 1, CFP_TORUS = 2 };
+
+typedef struct {
+    int kind;      /* CFP_SPHERE, CFP_ELLIPSOID or CFP_TORUS                */
+    double c[3];   /* centre                                               */
+    double R[9];   /* row-major body-to-world rotation (identity if none)  */
+    double p[3];   /* sphere: radius; ellipsoid: semi-axes; torus: major
+                      radius, minor radius (torus axis = body z axis)      */
+} cfp_body;
+
+enum { CFP_PREC_FP64 = 0,   /* the whole solve in FP64                       */
+       CFP_PREC_MIXED = 1   /* FP32 inner BiCGSTAB inside FP64 iterative
+                               refinement; residuals, the irregular rows of
+                               the residual and the right-hand side in FP64 */ };
+
+typedef struct {
+    int precision;     /* CFP_PREC_FP64 (default) or CFP_PREC_MIXED            */
+    int sweeps;        /* red-black Gauss-Seidel sweeps of the preconditioner
+                          solve (Sec. 3.3 uses 8 inner iterations; default 8) */
+    int maxit;         /* cap on BiCGSTAB iterations (default 50000)           */
+    int max_restarts;  /* restarts after a breakdown or a failed true-residual
+                          check (default 3)                                  */
+    double inner_tol;  /* CFP_PREC_MIXED: relative residual reduction of each
+                          FP32 inner solve (default 1e-5)                    */
+    int max_refine;    /* CFP_PREC_MIXED: cap on refinement steps (default 40) */
+    int use_graph;     /* 1 (default): the iteration runs as one CUDA graph
+                          with a device-side while loop; 0: plain launches   */
+} cfp_opts;
+
+typedef struct {
+    int status;            /* cfp_status of the solve                        */
+    int iterations;        /* BiCGSTAB iterations over all restarts and
+                              refinement steps                               */
+    int restarts;
+    int refinements;       /* CFP_PREC_MIXED outer steps                      */
+    double rel_residual;   /* ||rhs - B u||_2 / ||rhs||_2, recomputed in FP64 */
+    int64_t n_irregular;
+    int64_t n_ibi;
+    int64_t n_degenerate;  /* modified operators built with fewer points than
+                              the paper's six (five) because a body or the box
+                              ended the stencil early                        */
+    double ms_setup, ms_rhs, ms_solve;  /* host wall time of each phase       */
+    int64_t launches;      /* kernels this call launched (graph bodies counted
+                              once per executed iteration)                   */
+} cfp_info;
+
+typedef struct cfp_ctx cfp_ctx;
+
+/* Fill opts with the defaults listed above. */
+void cfp_default_opts(cfp_opts* opts);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* cfp_last_error(void);
+
+/*
+ * Create a context on the current CUDA device (Sec. 2 grid).
+ *   x, y, z  host arrays of nx, ny, nz >= 3 strictly increasing coordinates
+ *            (a_1 = x_1 < x_2 < ... < x_nx = a_2); copied.
+ *   bodies   host array of nbodies >= 0 bodies; copied.
+ *   fluid_inside  0: the fluid is outside the bodies (Omega^+ of Sec. 1);
+ *            1: the fluid is the inside (interior problems, Problem 4).
+ *   stream   cudaStream_t to enqueue on (NULL: the legacy default stream).
+ *   out      receives the context.
+ * Builds the 1D grid metrics of Eq. app_xxx and Eq. 2ndorder_coef.
+ * Errors: CFP_EINVAL, CFP_ENOMEM, CFP_ECUDA.
+ */
+cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny,
+                          const double* z, int nz, const cfp_body* bodies,
+                          int nbodies, int fluid_inside, void* stream,
+                          cfp_ctx** out);
+
+/* Release the context and every buffer it owns.  NULL is ignored. */
+void cfp_ctx_destroy(cfp_ctx* ctx);
+
+/*
+ * Point classification (Sec. 2) and the set-up that depends on it: solid
+ * points (inside a body, u = 0 by Sec. 1), irregular points (fluid points
+ * with a solid point among their 26 neighbours), IBI points (Gamma cut by
+ * the grid line between a fluid point and a solid axis neighbour), the
+ * modified stencils of Secs. 2.2-2.3 at every irregular point and the
+ * modified preconditioner rows of Sec. 3.3.
+ *   type_dev     NULL or a device array of N bytes; receives CFP_BOUNDARY,
+ *                CFP_REGULAR, CFP_IRREGULAR or CFP_SOLID per node.  Box
+ *                nodes are CFP_BOUNDARY whatever phi says.
+ *   n_irregular, n_ibi  NULL or host pointers receiving the counts.
+ * The IBI points are ordered by (linear index of the fluid point, direction
+ * -x,+x,-y,+y,-z,+z).  Synchronises.  Errors: CFP_EGEOM (a stencil that
+ * would need a node outside the grid or more than the supported points, a
+ * body touching the box), CFP_ENOMEM, CFP_ECUDA.
+ */
+cfp_status cfp_classify_points(cfp_ctx* ctx, uint8_t* type_dev,
+                               int64_t* n_irregular, int64_t* n_ibi);
+
+/*
+ * Coordinates of the IBI points, where the caller evaluates g on Gamma
+ * (Eq. bc uses u at the IBI points).
+ *   xyz      device (on_host = 0) or host (on_host = 1) array of 3*n_ibi
+ *            doubles, (x, y, z) per point in the order of cfp_classify_points.
+ * Errors: CFP_ESTATE before classification, CFP_EINVAL, CFP_ECUDA.
+ */
+cfp_status cfp_ibi_points(cfp_ctx* ctx, double* xyz, int on_host);
+
+/*
+ * Right-hand side of Eq. Bu=q for every unknown (interior fluid node): the
+ * source term of Eq. q with the weights of solid points dropped (Q-bar of
+ * Eq. A27_mod), minus the IBI term of Eqs. bc / qb_case2, minus the box
+ * Dirichlet values times their matrix entries.  Zero at box and solid nodes.
+ *   f_dev        field, source f (values at solid nodes are not read)
+ *   g_nodes_dev  field, Dirichlet data (only box nodes are read)
+ *   g_ibi_dev    n_ibi values of g at the IBI points (may be NULL if n_ibi=0)
+ *   rhs_dev      field, output
+ * Errors: CFP_ESTATE, CFP_EINVAL, CFP_ECUDA.
+ */
+cfp_status cfp_assemble_rhs(cfp_ctx* ctx, const double* f_dev,
+                            const double* g_nodes_dev, const double* g_ibi_dev,
+                            double* rhs_dev);
+
+/*
+ * y = B x at every unknown (Eq. Bdec: the 27-point compact stencil of Eq.
+ * A27 matrix-free plus the modified rows of the irregular points); y = 0 at
+ * box and solid nodes.  x is read at all nodes (box values included), so
+ * callers that want the operator on unknowns only pass x = 0 there.
+ * x_dev and y_dev: fields, must not overlap.  Errors: CFP_ESTATE, CFP_EINVAL.
+ */
+cfp_status cfp_apply(cfp_ctx* ctx, const double* x_dev, double* y_dev);
+
+/*
+ * phi = P(rho): `sweeps` red-black Gauss-Seidel sweeps on K phi = rho from
+ * phi = 0 (K: the 7-point second-order operator of Eq. A7 with the
+ * Shortley-Weller rows of Eq. A7_mod and zero Dirichlet data; Sec. 3.3),
+ * red = (i+j+k) even first.  sweeps = 0 copies rho.  rho is read at the
+ * unknowns only; phi is 0 at box and solid nodes.  Fields, no overlap.
+ * Errors: CFP_ESTATE, CFP_EINVAL.
+ */
+cfp_status cfp_precondition(cfp_ctx* ctx, int sweeps, const double* rho_dev,
+                            double* phi_dev);
+
+/*
+ * Solve Eq. Bu=q with BiCGSTAB (Algorithm 1, Sec. 3.2) right-preconditioned
+ * by P (Sec. 3.3), the update being u += alpha*p_hat + omega*s_hat.
+ *   f_dev, g_nodes_dev, g_ibi_dev  as for cfp_assemble_rhs
+ *   u_dev   field; in: initial guess at the unknowns (other nodes ignored);
+ *           out: the solution, g at box nodes, 0 at solid nodes.
+ *   tol     stop when ||r||_2 <= tol ||rhs||_2; the true residual is then
+ *           recomputed and the iteration restarted if it fails the test.
+ *   opts    NULL for defaults.  info: NULL or receives the statistics.
+ * Classifies first if cfp_classify_points has not run.  Synchronises.
+ * Errors: CFP_ENOCONV, CFP_EBREAKDOWN, CFP_ENAN, CFP_EGEOM, CFP_EINVAL,
+ * CFP_ENOMEM, CFP_ECUDA.  The iteration always ends (maxit bound).
+ */
+cfp_status cfp_solve(cfp_ctx* ctx, const double* f_dev, const double* g_nodes_dev,
+                     const double* g_ibi_dev, double* u_dev, double tol,
+                     const cfp_opts* opts, cfp_info* info);
+
+/*
+ * cfp_solve with host buffers: copies f, g (box values), g_ibi and the
+ * initial guess u to context-owned device buffers, solves, copies u back.
+ * The host buffers are best page-locked.  Same arguments and errors.
+ */
+cfp_status cfp_solve_host(cfp_ctx* ctx, const double* f_host,
+                          const double* g_nodes_host, const double* g_ibi_host,
+                          double* u_host, double tol, const cfp_opts* opts,
+                          cfp_info* info);
+
+enum { CFP_KERNEL_APPLY = 0,   /* B x with the fused (r_hat0, v) dot, as in
+                                  Algorithm 1 line 5                         */
+       CFP_KERNEL_RBGS = 1,    /* one red-black Gauss-Seidel half-sweep      */
+       CFP_KERNEL_UPDATE = 2   /* the fused x/r update with two dots (lines
+                                  11-12)                                     */ };
+
+/*
+ * Profiling aid: time `reps` >= 1 back-to-back launches of one kernel of the
+ * solve (CFP_KERNEL_*) in FP64 (precision CFP_PREC_FP64) or FP32
+ * (CFP_PREC_MIXED) with CUDA events on the context's stream, on the
+ * context's own work vectors (their contents are overwritten).
+ *   ms_per_launch     host pointer: mean device time of one launch
+ *   bytes_per_launch  host pointer or NULL: algorithmic bytes of one launch
+ *                     (minimum traffic: per unknown, apply 3 values (x, y
+ *                     and the dot operand), half-sweep 1.5 values (the
+ *                     other colour of phi, rho and phi of its own colour),
+ *                     update 8 values over all nodes)
+ * Requires classification.  Synchronises.  Errors: CFP_ESTATE, CFP_EINVAL,
+ * CFP_ECUDA.
+ */
+cfp_status cfp_time_kernel(cfp_ctx* ctx, int kernel, int precision, int reps,
+                           double* ms_per_launch, double* bytes_per_launch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,295 @@
+// C-ABI entry points of include/cfp.h: context life cycle, argument checks,
+// error reporting, and the 1D grid metrics (Eq. app_xxx, Eq. 2ndorder_coef).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "cfp_internal.cuh"
+
+namespace cfp {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+cfp_status fail(cfp_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+cfp_status cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? CFP_ENOMEM : CFP_ECUDA;
+}
+
+cfp_status solve_impl(cfp_ctx* c, const double* f, const double* g, const double* gi, double* u, double tol,
+                      const cfp_opts* opts, cfp_info* info);
+
+namespace {
+
+// Eq. app_xxx (compact, b = 1) and Eq. 2ndorder_coef at interior nodes;
+// layout per axis: a, c, ar, br, cr, ka, kb, kc (n each), zero at the ends.
+__global__ void k_metrics(const double* __restrict__ x, int n, double* __restrict__ out, float* __restrict__ out32) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (i > 0 && i < n - 1) {
+            const double f = x[i + 1] - x[i];
+            const double b = x[i] - x[i - 1];
+            const double D = f * f * f + 4.0 * f * f * b + 4.0 * f * b * b + b * b * b;
+            v[0] = f * (b * b + b * f - f * f) / D;
+            v[1] = b * (f * f + b * f - b * b) / D;
+            v[2] = 12.0 * f / D;
+            v[3] = -12.0 / (f * f + 3.0 * f * b + b * b);
+            v[4] = 12.0 * b / D;
+            v[5] = 2.0 / (b * (f + b));
+            v[6] = -2.0 / (b * f);
+            v[7] = 2.0 / (f * (f + b));
+        }
+        for (int q = 0; q < 8; ++q) {
+            out[(int64_t)q * n + i] = v[q];
+            out32[(int64_t)q * n + i] = (float)v[q];
+        }
+    }
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cfp_status need_classified(cfp_ctx* c) {
+    if (!c) return fail(CFP_EINVAL, "null context");
+    if (c->class_status != CFP_OK) return fail(c->class_status, "classification failed earlier");
+    if (!c->classified) return fail(CFP_ESTATE, "call cfp_classify_points first");
+    return CFP_OK;
+}
+
+cfp_status need_field(const void* p, const char* name) {
+    if (!p) return fail(CFP_EINVAL, std::string(name) + " is NULL");
+    if (!is_device_ptr(p)) return fail(CFP_EINVAL, std::string(name) + " is not a device pointer");
+    return CFP_OK;
+}
+
+}  // namespace
+}  // namespace cfp
+
+using namespace cfp;
+
+extern "C" {
+
+void cfp_default_opts(cfp_opts* o) {
+    if (!o) return;
+    o->precision = CFP_PREC_FP64;
+    o->sweeps = 8;
+    o->maxit = 50000;
+    o->max_restarts = 3;
+    o->inner_tol = 1e-5;
+    o->max_refine = 40;
+    o->use_graph = 1;
+}
+
+const char* cfp_last_error(void) { return g_last_error.c_str(); }
+
+cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny, const double* z, int nz,
+                          const cfp_body* bodies, int nbodies, int fluid_inside, void* stream, cfp_ctx** out) {
+    if (!out) return fail(CFP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!x || !y || !z) return fail(CFP_EINVAL, "coordinate array is NULL");
+    if (nx < 3 || ny < 3 || nz < 3) return fail(CFP_EINVAL, "need at least 3 nodes per axis");
+    if (nbodies < 0 || (nbodies > 0 && !bodies)) return fail(CFP_EINVAL, "bad body list");
+    const int64_t N = (int64_t)nx * ny * nz;
+    if (N >= ((int64_t)1 << 31)) return fail(CFP_EINVAL, "grid too large (N must be below 2^31)");
+    const double* src[3] = {x, y, z};
+    const int n[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; ++d)
+        for (int i = 0; i + 1 < n[d]; ++i)
+            if (!(src[d][i + 1] > src[d][i]) || !isfinite(src[d][i]) || !isfinite(src[d][i + 1]))
+                return fail(CFP_EINVAL, "coordinates must be finite and strictly increasing");
+    for (int m = 0; m < nbodies; ++m) {
+        const cfp_body& b = bodies[m];
+        if (b.kind < CFP_SPHERE || b.kind > CFP_TORUS) return fail(CFP_EINVAL, "unknown body kind");
+        const int np = b.kind == CFP_SPHERE ? 1 : (b.kind == CFP_TORUS ? 2 : 3);
+        for (int q = 0; q < np; ++q)
+            if (!(b.p[q] > 0.0)) return fail(CFP_EINVAL, "body sizes must be positive");
+    }
+    cfp_ctx* c = new cfp_ctx();
+    c->N = N;
+    c->stream = (cudaStream_t)stream;
+    c->fluid_inside = fluid_inside ? 1 : 0;
+    c->bodies.assign(bodies, bodies + nbodies);
+    cudaGetDevice(&c->device);
+    cfp_status st = CFP_OK;
+    auto chk = [&](cudaError_t e, const char* w) {
+        if (e != cudaSuccess && st == CFP_OK) st = cuda_fail(e, w);
+    };
+    int64_t ncoef = 0;
+    for (int d = 0; d < 3; ++d) {
+        c->n[d] = n[d];
+        c->X[d].assign(src[d], src[d] + n[d]);
+        ncoef += 8 * (int64_t)n[d];
+    }
+    chk(cudaMalloc(&c->dcoef64, sizeof(double) * ncoef), "cudaMalloc");
+    chk(cudaMalloc(&c->dcoef32, sizeof(float) * ncoef), "cudaMalloc");
+    for (int d = 0; d < 3; ++d) chk(cudaMalloc(&c->dX[d], sizeof(double) * n[d]), "cudaMalloc");
+    chk(cudaMalloc(&c->dbodies, sizeof(cfp_body) * std::max(nbodies, 1)), "cudaMalloc");
+    chk(cudaMalloc(&c->type, (size_t)N), "cudaMalloc");
+    chk(cudaMalloc(&c->slot, sizeof(int32_t) * (size_t)N), "cudaMalloc");
+    chk(cudaMalloc(&c->dtotal, sizeof(long long) * 8), "cudaMalloc");
+    chk(cudaMalloc(&c->derr, sizeof(DevError)), "cudaMalloc");
+    chk(cudaMalloc(&c->kst, sizeof(KState) * 2), "cudaMalloc");
+    chk(cudaMallocHost(&c->hkst, sizeof(KState) * 2), "cudaMallocHost");
+    if (st == CFP_OK) {
+        int64_t off = 0;
+        for (int d = 0; d < 3; ++d) {
+            chk(cudaMemcpyAsync(c->dX[d], src[d], sizeof(double) * n[d], cudaMemcpyHostToDevice, c->stream),
+                "cudaMemcpyAsync");
+            k_metrics<<<(n[d] + 255) / 256, 256, 0, c->stream>>>(c->dX[d], n[d], c->dcoef64 + off, c->dcoef32 + off);
+            off += 8 * (int64_t)n[d];
+        }
+        if (nbodies)
+            chk(cudaMemcpyAsync(c->dbodies, bodies, sizeof(cfp_body) * nbodies, cudaMemcpyHostToDevice, c->stream),
+                "cudaMemcpyAsync");
+        chk(cudaGetLastError(), "k_metrics");
+        chk(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    }
+    if (st != CFP_OK) {
+        cfp_ctx_destroy(c);
+        return st;
+    }
+    *out = c;
+    return CFP_OK;
+}
+
+void cfp_ctx_destroy(cfp_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (int q = 0; q < 2; ++q)
+        if (c->gexec[q]) cudaGraphExecDestroy(c->gexec[q]);
+    void* ptrs[] = {c->dcoef64, c->dcoef32, c->dX[0], c->dX[1], c->dX[2], c->dbodies, c->type, c->slot, c->irr_lin,
+                    c->ibi_off, c->ibi_xyz, c->corr_ptr, c->corr_off, c->corr_val, c->corr_val32, c->bib_ptr,
+                    c->bib_idx, c->bib_val, c->krow, c->krow32, c->scan_bsum, c->dtotal, c->derr, c->v64, c->v32,
+                    c->partial, c->kst, c->hs_f, c->hs_g, c->hs_u, c->hs_gi};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->hkst) cudaFreeHost(c->hkst);
+    delete c;
+}
+
+cfp_status cfp_classify_points(cfp_ctx* c, uint8_t* type_dev, int64_t* n_irregular, int64_t* n_ibi) {
+    if (!c) return fail(CFP_EINVAL, "null context");
+    if (type_dev && !is_device_ptr(type_dev)) return fail(CFP_EINVAL, "type_dev is not a device pointer");
+    CFP_TRY(classify(c));
+    if (type_dev) CFP_CUDA(cudaMemcpyAsync(type_dev, c->type, (size_t)c->N, cudaMemcpyDeviceToDevice, c->stream));
+    CFP_CUDA(cudaStreamSynchronize(c->stream));
+    if (n_irregular) *n_irregular = c->n_irr;
+    if (n_ibi) *n_ibi = c->n_ibi;
+    return CFP_OK;
+}
+
+cfp_status cfp_ibi_points(cfp_ctx* c, double* xyz, int on_host) {
+    CFP_TRY(need_classified(c));
+    if (c->n_ibi == 0) return CFP_OK;
+    if (!xyz) return fail(CFP_EINVAL, "xyz is NULL");
+    if (!on_host && !is_device_ptr(xyz)) return fail(CFP_EINVAL, "xyz is not a device pointer");
+    CFP_CUDA(cudaMemcpyAsync(xyz, c->ibi_xyz, sizeof(double) * 3 * c->n_ibi,
+                             on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+    if (on_host) CFP_CUDA(cudaStreamSynchronize(c->stream));
+    return CFP_OK;
+}
+
+cfp_status cfp_assemble_rhs(cfp_ctx* c, const double* f, const double* g, const double* gi, double* rhs) {
+    CFP_TRY(need_classified(c));
+    CFP_TRY(need_field(f, "f_dev"));
+    CFP_TRY(need_field(g, "g_nodes_dev"));
+    CFP_TRY(need_field(rhs, "rhs_dev"));
+    if (c->n_ibi > 0) CFP_TRY(need_field(gi, "g_ibi_dev"));
+    CFP_TRY(ensure_work(c, false));
+    const int64_t N = c->N;
+    double* gb = c->v64 + V_TMP * N;
+    double* bg = c->v64 + V_TMP2 * N;
+    double* qf = c->v64 + V_T * N;
+    if (rhs == gb || rhs == bg || rhs == qf) return fail(CFP_EINVAL, "rhs aliases the context's work space");
+    launch_boundary_lift(c, g, gb, c->stream);
+    launch_apply<double>(c, gb, bg, nullptr, 0, nullptr, c->stream, nullptr);
+    launch_qf(c, f, qf, c->stream);
+    launch_rhs_finish(c, qf, bg, c->n_ibi ? gi : c->ibi_xyz, rhs, c->stream);
+    CFP_CUDA(cudaGetLastError());
+    return CFP_OK;
+}
+
+cfp_status cfp_apply(cfp_ctx* c, const double* x, double* y) {
+    CFP_TRY(need_classified(c));
+    CFP_TRY(need_field(x, "x_dev"));
+    CFP_TRY(need_field(y, "y_dev"));
+    if (x == y) return fail(CFP_EINVAL, "x and y must not overlap");
+    CFP_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * c->N, c->stream));
+    launch_apply<double>(c, x, y, nullptr, 0, nullptr, c->stream, nullptr);
+    CFP_CUDA(cudaGetLastError());
+    return CFP_OK;
+}
+
+cfp_status cfp_precondition(cfp_ctx* c, int sweeps, const double* rho, double* phi) {
+    CFP_TRY(need_classified(c));
+    CFP_TRY(need_field(rho, "rho_dev"));
+    CFP_TRY(need_field(phi, "phi_dev"));
+    if (sweeps < 0) return fail(CFP_EINVAL, "sweeps must be >= 0");
+    if (rho == phi) return fail(CFP_EINVAL, "rho and phi must not overlap");
+    CFP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * c->N, c->stream));
+    launch_precond<double>(c, sweeps, rho, phi, c->stream);
+    CFP_CUDA(cudaGetLastError());
+    return CFP_OK;
+}
+
+cfp_status cfp_solve(cfp_ctx* c, const double* f, const double* g, const double* gi, double* u, double tol,
+                     const cfp_opts* opts, cfp_info* info) {
+    if (!c) return fail(CFP_EINVAL, "null context");
+    CFP_TRY(need_field(f, "f_dev"));
+    CFP_TRY(need_field(g, "g_nodes_dev"));
+    CFP_TRY(need_field(u, "u_dev"));
+    if (!c->classified) CFP_TRY(classify(c));
+    if (c->n_ibi > 0) CFP_TRY(need_field(gi, "g_ibi_dev"));
+    return solve_impl(c, f, g, gi, u, tol, opts, info);
+}
+
+cfp_status cfp_solve_host(cfp_ctx* c, const double* f, const double* g, const double* gi, double* u, double tol,
+                          const cfp_opts* opts, cfp_info* info) {
+    if (!c) return fail(CFP_EINVAL, "null context");
+    if (!f || !g || !u) return fail(CFP_EINVAL, "NULL host buffer");
+    if (!c->classified) CFP_TRY(classify(c));
+    if (c->n_ibi > 0 && !gi) return fail(CFP_EINVAL, "g_ibi_host is NULL");
+    const size_t bytes = sizeof(double) * (size_t)c->N;
+    if (!c->hs_f) CFP_CUDA(cudaMalloc(&c->hs_f, bytes));
+    if (!c->hs_g) CFP_CUDA(cudaMalloc(&c->hs_g, bytes));
+    if (!c->hs_u) CFP_CUDA(cudaMalloc(&c->hs_u, bytes));
+    if (c->hs_gi_cap < std::max<int64_t>(c->n_ibi, 1)) {
+        if (c->hs_gi) cudaFree(c->hs_gi);
+        c->hs_gi = nullptr;
+        CFP_CUDA(cudaMalloc(&c->hs_gi, sizeof(double) * std::max<int64_t>(c->n_ibi, 1)));
+        c->hs_gi_cap = std::max<int64_t>(c->n_ibi, 1);
+    }
+    CFP_CUDA(cudaMemcpyAsync(c->hs_f, f, bytes, cudaMemcpyHostToDevice, c->stream));
+    CFP_CUDA(cudaMemcpyAsync(c->hs_g, g, bytes, cudaMemcpyHostToDevice, c->stream));
+    CFP_CUDA(cudaMemcpyAsync(c->hs_u, u, bytes, cudaMemcpyHostToDevice, c->stream));
+    if (c->n_ibi)
+        CFP_CUDA(cudaMemcpyAsync(c->hs_gi, gi, sizeof(double) * c->n_ibi, cudaMemcpyHostToDevice, c->stream));
+    const cfp_status st = solve_impl(c, c->hs_f, c->hs_g, c->hs_gi, c->hs_u, tol, opts, info);
+    const std::string msg = g_last_error;
+    CFP_CUDA(cudaMemcpyAsync(u, c->hs_u, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CFP_CUDA(cudaStreamSynchronize(c->stream));
+    if (st != CFP_OK) g_last_error = msg;
+    return st;
+}
+
+cfp_status cfp_time_kernel(cfp_ctx* c, int kernel, int precision, int reps, double* ms, double* bytes) {
+    CFP_TRY(need_classified(c));
+    return time_kernel(c, kernel, precision, reps, ms, bytes);
+}
+
+}  // extern "C"

@@ -1,0 +1,802 @@
+// Point classification, IBI location and the irregular-point side list.
+//
+// Sec. 2: a node is solid if it lies inside a body (phi <= 0; box nodes are
+// Dirichlet nodes whatever phi says), irregular if it is an interior fluid
+// node with a solid node among its 26 neighbours, regular otherwise.  IBI
+// points are where a grid line between a fluid node and a solid axis
+// neighbour crosses Gamma.  Secs. 2.2-2.3 replace, at each irregular point,
+// the RHS operator of every grid line of its 3x3x3 block that has a solid
+// node by a moment-matched operator (Eqs. mod1-mat4, M, mod2_case2,
+// mod2_case22); Sec. 3.3 gives the Shortley-Weller rows of K (Eqs.
+// 2ndorder_xx, 2ndorder_coef_mod, A7_mod).
+//
+// The level set is evaluated with explicitly rounded operations (no
+// contraction) so that the classification is reproducible bit for bit.
+#include <math.h>
+
+#include <algorithm>
+
+#include "cfp_internal.cuh"
+
+namespace cfp {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t lin3(int i, int j, int k, int nx, int ny) {
+    return (int64_t)i + (int64_t)nx * ((int64_t)j + (int64_t)ny * k);
+}
+
+// ---------------------------------------------------------------- level set
+__device__ double body_phi(const cfp_body& b, double x, double y, double z) {
+    const double d0 = __dsub_rn(x, b.c[0]);
+    const double d1 = __dsub_rn(y, b.c[1]);
+    const double d2 = __dsub_rn(z, b.c[2]);
+    const double* R = b.R;
+    const double q0 = __dadd_rn(__dadd_rn(__dmul_rn(R[0], d0), __dmul_rn(R[3], d1)), __dmul_rn(R[6], d2));
+    const double q1 = __dadd_rn(__dadd_rn(__dmul_rn(R[1], d0), __dmul_rn(R[4], d1)), __dmul_rn(R[7], d2));
+    const double q2 = __dadd_rn(__dadd_rn(__dmul_rn(R[2], d0), __dmul_rn(R[5], d1)), __dmul_rn(R[8], d2));
+    if (b.kind == CFP_SPHERE) {
+        const double s = __dadd_rn(__dadd_rn(__dmul_rn(q0, q0), __dmul_rn(q1, q1)), __dmul_rn(q2, q2));
+        return __dsub_rn(s, __dmul_rn(b.p[0], b.p[0]));
+    }
+    if (b.kind == CFP_ELLIPSOID) {
+        const double e0 = __ddiv_rn(q0, b.p[0]);
+        const double e1 = __ddiv_rn(q1, b.p[1]);
+        const double e2 = __ddiv_rn(q2, b.p[2]);
+        const double s = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2));
+        return __dsub_rn(s, 1.0);
+    }
+    const double rho = __dsqrt_rn(__dadd_rn(__dmul_rn(q0, q0), __dmul_rn(q1, q1)));
+    const double s = __dsub_rn(rho, b.p[0]);
+    return __dsub_rn(__dadd_rn(__dmul_rn(s, s), __dmul_rn(q2, q2)), __dmul_rn(b.p[1], b.p[1]));
+}
+
+__device__ double union_phi(const cfp_body* bodies, int nb, int inside, double x, double y, double z) {
+    double phi = INFINITY;
+    for (int m = 0; m < nb; ++m) {
+        const double v = body_phi(bodies[m], x, y, z);
+        if (v < phi) phi = v;
+    }
+    return inside ? -phi : phi;
+}
+
+__device__ __forceinline__ double edge_pos(double xa, double xb, double t) {
+    return __dadd_rn(__dmul_rn(__dsub_rn(1.0, t), xa), __dmul_rn(t, xb));
+}
+
+struct GeoArgs {
+    const double* X[3];
+    const cfp_body* bodies;
+    int nb, inside;
+    int n[3];
+};
+
+// ------------------------------------------------------------ classification
+__global__ void k_classify_solid(GeoArgs g, uint8_t* type, int64_t N) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < N;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(l % nx);
+        const int j = (int)((l / nx) % ny);
+        const int k = (int)(l / ((int64_t)nx * ny));
+        uint8_t t;
+        if (i == 0 || j == 0 || k == 0 || i == nx - 1 || j == ny - 1 || k == nz - 1) {
+            t = CFP_BOUNDARY;
+        } else {
+            const double ph = union_phi(g.bodies, g.nb, g.inside, g.X[0][i], g.X[1][j], g.X[2][k]);
+            t = ph <= 0.0 ? CFP_SOLID : CFP_REGULAR;
+        }
+        type[l] = t;
+    }
+}
+
+__global__ void k_classify_irregular(uint8_t* type, int nx, int ny, int nz) {
+    const int64_t nin = (int64_t)(nx - 2) * (ny - 2) * (nz - 2);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nin;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = 1 + (int)(q % (nx - 2));
+        const int j = 1 + (int)((q / (nx - 2)) % (ny - 2));
+        const int k = 1 + (int)(q / ((int64_t)(nx - 2) * (ny - 2)));
+        const int64_t l = lin3(i, j, k, nx, ny);
+        if (type[l] != CFP_REGULAR) continue;
+        bool irr = false;
+        for (int r = -1; r <= 1; ++r)
+            for (int s = -1; s <= 1; ++s)
+                for (int o = -1; o <= 1; ++o)
+                    irr |= type[lin3(i + o, j + s, k + r, nx, ny)] == CFP_SOLID;
+        // Only the solid flags are read, and a node turns irregular only
+        // from regular, so the in-place update does not race.
+        if (irr) type[l] = CFP_IRREGULAR;
+    }
+}
+
+// -------------------------------------------------------------------- scans
+// Deterministic exclusive scan of per-item counts: per-chunk sums, a
+// single-block scan of the chunk sums, then a per-chunk scan and scatter.
+__device__ int block_excl_scan(int v, int* total) {
+    __shared__ int warp_tot[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        int t = lane < nw ? warp_tot[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    const int before = wid ? warp_tot[wid - 1] : 0;
+    if (total) *total = warp_tot[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+struct FlagIrregular {
+    const uint8_t* type;
+    __device__ int operator()(int64_t i) const { return type[i] == CFP_IRREGULAR; }
+};
+struct FetchInt {
+    const int* a;
+    __device__ int operator()(int64_t i) const { return a[i]; }
+};
+struct SinkSlots {
+    int32_t* slot;
+    int32_t* irr_lin;
+    __device__ void operator()(int64_t i, int off, int v) const {
+        slot[i] = v ? off : -1;
+        if (v) irr_lin[off] = (int32_t)i;
+    }
+};
+struct SinkOffsets {
+    int32_t* out;
+    __device__ void operator()(int64_t i, int off, int) const { out[i] = off; }
+};
+
+template <class F>
+__global__ void k_scan_reduce(F f, int64_t n, int* bsum) {
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+    int s = 0;
+    for (int q = threadIdx.x; q < kScanChunk; q += kScanThreads) {
+        const int64_t i = base + q;
+        if (i < n) s += f(i);
+    }
+    int tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_blocks(int* bsum, int nb, long long* total) {
+    __shared__ long long carry_s;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const int v = i < nb ? bsum[i] : 0;
+        int tot;
+        const int ex = block_excl_scan(v, &tot);
+        const long long carry = carry_s;
+        if (i < nb) bsum[i] = (int)(carry + ex);
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s = carry + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry_s;
+}
+
+template <class F, class S>
+__global__ void k_scan_scatter(F f, S sink, int64_t n, const int* boff) {
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        v[q] = (base + q < n) ? f(base + q) : 0;
+        s += v[q];
+    }
+    int off = boff[blockIdx.x] + block_excl_scan(s, nullptr);
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        if (base + q < n) {
+            sink(base + q, off, v[q]);
+            off += v[q];
+        }
+    }
+}
+
+template <class F, class S>
+cfp_status scan(cfp_ctx* c, F f, S sink, int64_t n, long long* dtotal, long long* htotal) {
+    const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    if (nb > c->scan_cap) {
+        if (c->scan_bsum) cudaFree(c->scan_bsum);
+        c->scan_bsum = nullptr;
+        CFP_CUDA(cudaMalloc(&c->scan_bsum, sizeof(int) * std::max<int64_t>(nb, 1)));
+        c->scan_cap = nb;
+    }
+    if (nb > 0) {
+        k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(f, n, c->scan_bsum);
+        k_scan_blocks<<<1, kScanThreads, 0, c->stream>>>(c->scan_bsum, (int)nb, dtotal);
+        k_scan_scatter<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(f, sink, n, c->scan_bsum);
+    } else {
+        CFP_CUDA(cudaMemsetAsync(dtotal, 0, sizeof(long long), c->stream));
+    }
+    CFP_CUDA(cudaGetLastError());
+    CFP_CUDA(cudaMemcpyAsync(htotal, dtotal, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    CFP_CUDA(cudaStreamSynchronize(c->stream));
+    return CFP_OK;
+}
+
+// ------------------------------------------------------------------ IBIs
+struct IrrArgs {
+    const uint8_t* type;
+    const int32_t* slot;
+    const int32_t* irr_lin;
+    int64_t n_irr;
+    int n[3];
+};
+
+__device__ __forceinline__ int solid_axis_mask(const uint8_t* type, int64_t l, const int64_t st[3]) {
+    int m = 0;
+#pragma unroll
+    for (int dir = 0; dir < 6; ++dir) {
+        const int64_t nb = l + ((dir & 1) ? st[dir >> 1] : -st[dir >> 1]);
+        if (type[nb] == CFP_SOLID) m |= 1 << dir;
+    }
+    return m;
+}
+
+__global__ void k_ibi_count(IrrArgs a, int* cnt) {
+    const int64_t st[3] = {1, a.n[0], (int64_t)a.n[0] * a.n[1]};
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < a.n_irr;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        cnt[s] = __popc(solid_axis_mask(a.type, a.irr_lin[s], st));
+    }
+}
+
+// Root of phi on the edge from fluid node A (t = 0) to solid node B (t = 1):
+// scan t = 1/8 .. 7/8 for the first sign change seen from A, then 60
+// bisection steps; the solid end of the last bracket is returned.
+__device__ double ibi_root(const GeoArgs& g, int d, const double pa[3], double xb) {
+    double q[3] = {pa[0], pa[1], pa[2]};
+    double lo = 0.0, hi = 1.0;
+    for (int s = 1; s < 8; ++s) {
+        const double ts = (double)s / 8.0;
+        q[d] = edge_pos(pa[d], xb, ts);
+        if (union_phi(g.bodies, g.nb, g.inside, q[0], q[1], q[2]) <= 0.0) {
+            hi = ts;
+            break;
+        }
+        lo = ts;
+    }
+    for (int it = 0; it < 60; ++it) {
+        const double mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
+        q[d] = edge_pos(pa[d], xb, mid);
+        if (union_phi(g.bodies, g.nb, g.inside, q[0], q[1], q[2]) > 0.0) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
+__global__ void k_ibi_roots(IrrArgs a, GeoArgs g, const int32_t* ibi_off, double* xyz) {
+    const int nx = a.n[0], ny = a.n[1];
+    const int64_t st[3] = {1, nx, (int64_t)nx * ny};
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < a.n_irr;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = a.irr_lin[s];
+        const int idx[3] = {(int)(l % nx), (int)((l / nx) % ny), (int)(l / ((int64_t)nx * ny))};
+        const int mask = solid_axis_mask(a.type, l, st);
+        int m = ibi_off[s];
+        const double pa[3] = {g.X[0][idx[0]], g.X[1][idx[1]], g.X[2][idx[2]]};
+        for (int dir = 0; dir < 6; ++dir) {
+            if (!(mask & (1 << dir))) continue;
+            const int d = dir >> 1, sg = (dir & 1) ? 1 : -1;
+            const double xb = g.X[d][idx[d] + sg];
+            const double t = ibi_root(g, d, pa, xb);
+            xyz[3 * (int64_t)m + 0] = pa[0];
+            xyz[3 * (int64_t)m + 1] = pa[1];
+            xyz[3 * (int64_t)m + 2] = pa[2];
+            xyz[3 * (int64_t)m + d] = edge_pos(pa[d], xb, t);
+            ++m;
+        }
+    }
+}
+
+// ------------------------------------------------------------- side list
+constexpr int kMaxCorr = 192;
+constexpr int kMaxBib = 64;
+
+struct CorrAcc {
+    int n;
+    int off[kMaxCorr];
+    double val[kMaxCorr];
+    __device__ bool add(int o, double v) {
+        for (int q = 0; q < n; ++q)
+            if (off[q] == o) {
+                val[q] += v;
+                return true;
+            }
+        if (n == kMaxCorr) return false;
+        off[n] = o;
+        val[n] = v;
+        ++n;
+        return true;
+    }
+};
+
+struct BibAcc {
+    int n;
+    int idx[kMaxBib];
+    double val[kMaxBib];
+    __device__ bool add(int i, double v) {
+        if (n == kMaxBib) return false;
+        idx[n] = i;
+        val[n] = v;
+        ++n;
+        return true;
+    }
+};
+
+struct SideArgs {
+    IrrArgs a;
+    Axis<double> ax[3];
+    const double* X[3];
+    const int32_t* ibi_off;
+    const double* ibi_xyz;
+};
+
+__device__ __forceinline__ double Lc(const Axis<double>& A, int m, int o) {
+    return o < 0 ? A.a[m] : (o == 0 ? 1.0 : A.c[m]);
+}
+__device__ __forceinline__ double Rc(const Axis<double>& A, int m, int o) {
+    return o < 0 ? A.ar[m] : (o == 0 ? A.br[m] : A.cr[m]);
+}
+
+// IBI index of the edge from interior fluid node l in direction dir
+// (-x,+x,-y,+y,-z,+z), or -1 if that neighbour is not solid.
+__device__ int ibi_index(const SideArgs& S, int64_t l, int dir) {
+    const int64_t st[3] = {1, S.a.n[0], (int64_t)S.a.n[0] * S.a.n[1]};
+    const int s = S.a.slot[l];
+    if (s < 0) return -1;
+    const int mask = solid_axis_mask(S.a.type, l, st);
+    if (!(mask & (1 << dir))) return -1;
+    return S.ibi_off[s] + __popc(mask & ((1 << dir) - 1));
+}
+
+// Moment matching of Eqs. mat1-mat4 (matrix M of Eq. M): c_n with
+// sum_n c_n (xi_n - xe)^m = sum_s L_s m(m-1) (xs_s - xe)^(m-2), m < M,
+// lengths scaled by hs, Gaussian elimination with partial pivoting.
+__device__ bool moment_solve(int M, const double* xi, double xe, int ns, const double* xs,
+                             const double* Ls, double hs, double* c) {
+    double A[6][7];
+    for (int m = 0; m < M; ++m) {
+        for (int q = 0; q < M; ++q) {
+            const double e = (xi[q] - xe) / hs;
+            double p = 1.0;
+            for (int r = 0; r < m; ++r) p *= e;
+            A[m][q] = p;
+        }
+        double r = 0.0;
+        if (m >= 2)
+            for (int s = 0; s < ns; ++s) {
+                const double e = (xs[s] - xe) / hs;
+                double p = 1.0;
+                for (int q = 0; q < m - 2; ++q) p *= e;
+                r += Ls[s] * (double)(m * (m - 1)) * p;
+            }
+        A[m][M] = r / (hs * hs);
+    }
+    for (int col = 0; col < M; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < M; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (A[piv][col] == 0.0) return false;
+        if (piv != col)
+            for (int q = 0; q <= M; ++q) {
+                const double t = A[col][q];
+                A[col][q] = A[piv][q];
+                A[piv][q] = t;
+            }
+        for (int r = col + 1; r < M; ++r) {
+            const double f = A[r][col] / A[col][col];
+            for (int q = col; q <= M; ++q) A[r][q] -= f * A[col][q];
+        }
+    }
+    for (int r = M - 1; r >= 0; --r) {
+        double s = A[r][M];
+        for (int q = r + 1; q < M; ++q) s -= A[r][q] * c[q];
+        c[r] = s / A[r][r];
+    }
+    return true;
+}
+
+struct RowCtx {
+    int idx[3];
+    int64_t lin;
+    int64_t st[3];
+    CorrAcc* corr;
+    BibAcc* bib;
+    int ndeg;
+    int err;
+};
+
+// One modified operator along axis d of the line with centre index vector
+// base (base[d] = the irregular point's index along d).  The expansion node
+// is at offset e; the operator is bounded on side -sg by a solid node whose
+// IBI it uses and walks e, e+sg, ... over up to G grid nodes (5 for the
+// six-point operators of Eqs. mod1-mod4, 4 for the five-point operators of
+// Eqs. mod2_case2 / mod2_case22).  If the walk meets a solid node first,
+// that edge's IBI closes the set; if it leaves the grid, the set ends at the
+// box (fewer points, counted as degenerate).
+__device__ void modified_op(const SideArgs& S, RowCtx& R, const int base[3], int d, double w, int e,
+                            int sg, int G, int ns, const int* surv, const double* Ls) {
+    if (R.err) return;
+    const int nd = S.a.n[d];
+    double xi[7], xs[3], cc[7];
+    int offs[6];
+    int ib[2];
+    int ng = 0, nib = 0;
+    int f[3] = {base[0], base[1], base[2]};
+    f[d] += e;
+    const int64_t fl = lin3(f[0], f[1], f[2], S.a.n[0], S.a.n[1]);
+    const uint8_t ft = S.a.type[fl];
+    if (ft != CFP_REGULAR && ft != CFP_IRREGULAR) { R.err = DETAIL_BOXIBI; return; }
+    ib[nib] = ibi_index(S, fl, 2 * d + (sg > 0 ? 0 : 1));
+    if (ib[nib] < 0) { R.err = DETAIL_MISSINGIBI; return; }
+    ++nib;
+    for (int q = 0; q < G; ++q) {
+        int p[3] = {f[0], f[1], f[2]};
+        p[d] += q * sg;
+        if (p[d] < 0 || p[d] >= nd) break;
+        const int64_t l = lin3(p[0], p[1], p[2], S.a.n[0], S.a.n[1]);
+        if (S.a.type[l] == CFP_SOLID) {
+            const int64_t pl = l - sg * R.st[d];
+            const uint8_t pt = S.a.type[pl];
+            if (pt != CFP_REGULAR && pt != CFP_IRREGULAR) { R.err = DETAIL_BOXIBI; return; }
+            ib[nib] = ibi_index(S, pl, 2 * d + (sg > 0 ? 1 : 0));
+            if (ib[nib] < 0) { R.err = DETAIL_MISSINGIBI; return; }
+            ++nib;
+            break;
+        }
+        xi[ng] = S.X[d][p[d]];
+        offs[ng] = (int)(l - R.lin);
+        ++ng;
+    }
+    const int M = ng + nib;
+    if (M < 3) { R.err = DETAIL_FEWPOINTS; return; }
+    if (ng < G || nib > 1) R.ndeg++;
+    for (int q = 0; q < nib; ++q) xi[ng + q] = S.ibi_xyz[3 * (int64_t)ib[q] + d];
+    const double xe = S.X[d][f[d]];
+    for (int s = 0; s < ns; ++s) xs[s] = S.X[d][base[d] + surv[s]];
+    double hs = 0.0;
+    for (int q = 1; q < M; ++q) hs = fmax(hs, fabs(xi[q] - xe));
+    if (!moment_solve(M, xi, xe, ns, xs, Ls, hs, cc)) { R.err = DETAIL_SINGULAR; return; }
+    for (int q = 0; q < ng; ++q)
+        if (!R.corr->add(offs[q], w * cc[q])) { R.err = DETAIL_OVERFLOW; return; }
+    for (int q = 0; q < nib; ++q)
+        if (!R.bib->add(ib[q], w * cc[ng + q])) { R.err = DETAIL_OVERFLOW; return; }
+}
+
+// Corrections that turn the regular 27-point row at an irregular point into
+// its modified row: for each of the 27 lines (Eq. lhsrhs_xxyyzz_mod) with a
+// solid node, minus the regular R operator at its fluid nodes, plus the
+// modified operator(s); IBI weights go to bib (script B of Eq. bc).
+__device__ void build_row(const SideArgs& S, RowCtx& R) {
+    for (int d = 0; d < 3; ++d) {
+        const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+        const int m = R.idx[d];
+        const Axis<double>& A = S.ax[d];
+        const double a = A.a[m], c = A.c[m];
+        for (int o1 = -1; o1 <= 1; ++o1)
+            for (int o2 = -1; o2 <= 1; ++o2) {
+                const double w = Lc(S.ax[t1], R.idx[t1], o1) * Lc(S.ax[t2], R.idx[t2], o2);
+                int base[3] = {R.idx[0], R.idx[1], R.idx[2]};
+                base[t1] += o1;
+                base[t2] += o2;
+                const int64_t bl = lin3(base[0], base[1], base[2], S.a.n[0], S.a.n[1]);
+                int sol[3];
+                for (int s = -1; s <= 1; ++s) sol[s + 1] = S.a.type[bl + s * R.st[d]] == CFP_SOLID;
+                const int mask = (sol[0] << 2) | (sol[1] << 1) | sol[2];
+                if (mask == 0 || mask == 7) continue;  // regular or dropped line
+                for (int s = -1; s <= 1; ++s)
+                    if (!sol[s + 1])
+                        if (!R.corr->add((int)(bl + s * R.st[d] - R.lin), -w * Rc(A, m, s))) {
+                            R.err = DETAIL_OVERFLOW;
+                            return;
+                        }
+                switch (mask) {
+                case 1: {  // +1 solid (Eqs. mod1_top, mod1, mat1)
+                    const int sv[2] = {-1, 0};
+                    const double Ls[2] = {a, 1.0};
+                    modified_op(S, R, base, d, w, 0, -1, 5, 2, sv, Ls);
+                } break;
+                case 4: {  // -1 solid (Eqs. mod3_top, mod3, mat3)
+                    const int sv[2] = {0, 1};
+                    const double Ls[2] = {1.0, c};
+                    modified_op(S, R, base, d, w, 0, +1, 5, 2, sv, Ls);
+                } break;
+                case 3: {  // 0 and +1 solid (Eqs. mod2_top, mod2, mat2)
+                    const int sv[1] = {-1};
+                    const double Ls[1] = {a};
+                    modified_op(S, R, base, d, w, -1, -1, 5, 1, sv, Ls);
+                } break;
+                case 6: {  // -1 and 0 solid (Eqs. mod4_top, mod4, mat4)
+                    const int sv[1] = {1};
+                    const double Ls[1] = {c};
+                    modified_op(S, R, base, d, w, 1, +1, 5, 1, sv, Ls);
+                } break;
+                case 2: {  // middle solid: Eqs. mod2_case2 and mod2_case22
+                    const int svm[1] = {-1};
+                    const double Lsm[1] = {a};
+                    modified_op(S, R, base, d, w, -1, -1, 4, 1, svm, Lsm);
+                    const int svp[1] = {1};
+                    const double Lsp[1] = {c};
+                    modified_op(S, R, base, d, w, 1, +1, 4, 1, svp, Lsp);
+                } break;
+                default: {  // 5: fluid node between two solid nodes
+                    const int sv[1] = {0};
+                    const double Ls[1] = {1.0};
+                    modified_op(S, R, base, d, w, 0, -1, 5, 1, sv, Ls);
+                } break;
+                }
+                if (R.err) return;
+            }
+    }
+}
+
+__device__ void record_error(DevError* e, int code, int lin, int detail) {
+    if (atomicCAS(&e->code, 0, code) == 0) {
+        e->lin = lin;
+        e->detail = detail;
+    }
+}
+
+// mode 0: count entries; mode 1: write them (and the K rows)
+template <int MODE>
+__global__ void __launch_bounds__(64) k_side(SideArgs S, int* ccount, int* bcount,
+                                             const int32_t* corr_ptr, int32_t* corr_off,
+                                             double* corr_val, const int32_t* bib_ptr,
+                                             int32_t* bib_idx, double* bib_val, double* krow,
+                                             unsigned long long* ndeg, DevError* err) {
+    const int nx = S.a.n[0], ny = S.a.n[1];
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S.a.n_irr;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        CorrAcc corr;
+        BibAcc bib;
+        corr.n = 0;
+        bib.n = 0;
+        RowCtx R;
+        R.lin = S.a.irr_lin[s];
+        R.idx[0] = (int)(R.lin % nx);
+        R.idx[1] = (int)((R.lin / nx) % ny);
+        R.idx[2] = (int)(R.lin / ((int64_t)nx * ny));
+        R.st[0] = 1;
+        R.st[1] = nx;
+        R.st[2] = (int64_t)nx * ny;
+        R.corr = &corr;
+        R.bib = &bib;
+        R.ndeg = 0;
+        R.err = 0;
+        build_row(S, R);
+        if (R.err) {
+            record_error(err, CFP_EGEOM, (int)R.lin, R.err);
+            if (MODE == 0) {
+                ccount[s] = 0;
+                bcount[s] = 0;
+            }
+            continue;
+        }
+        if (MODE == 0) {
+            ccount[s] = corr.n;
+            bcount[s] = bib.n;
+            if (R.ndeg) atomicAdd(ndeg, (unsigned long long)R.ndeg);
+            continue;
+        }
+        const int c0 = corr_ptr[s];
+        for (int q = 0; q < corr.n; ++q) {
+            corr_off[c0 + q] = corr.off[q];
+            corr_val[c0 + q] = corr.val[q];
+        }
+        const int b0 = bib_ptr[s];
+        for (int q = 0; q < bib.n; ++q) {
+            bib_idx[b0 + q] = bib.idx[q];
+            bib_val[b0 + q] = bib.val[q];
+        }
+        // Shortley-Weller row of K (Eqs. 2ndorder_coef_mod, A7_mod): the IBI
+        // distance replaces the spacing on a solid side, whose term is dropped.
+        double kr[7];
+        kr[0] = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const int m = R.idx[d];
+            const double xm = S.X[d][m];
+            double fw = S.X[d][m + 1] - xm;
+            double bw = xm - S.X[d][m - 1];
+            const int im = ibi_index(S, R.lin, 2 * d);
+            const int ip = ibi_index(S, R.lin, 2 * d + 1);
+            if (im >= 0) bw = xm - S.ibi_xyz[3 * (int64_t)im + d];
+            if (ip >= 0) fw = S.ibi_xyz[3 * (int64_t)ip + d] - xm;
+            const double ca = 2.0 / (bw * (fw + bw));
+            const double cb = -2.0 / (bw * fw);
+            const double cc = 2.0 / (fw * (fw + bw));
+            kr[0] += cb;
+            kr[1 + 2 * d] = im >= 0 ? 0.0 : ca;
+            kr[2 + 2 * d] = ip >= 0 ? 0.0 : cc;
+        }
+        for (int q = 0; q < 7; ++q) krow[7 * s + q] = kr[q];
+    }
+}
+
+__global__ void k_to_float(const double* in, float* out, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = (float)in[q];
+}
+
+template <class T>
+void free_ptr(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+unsigned grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
+}
+
+}  // namespace
+
+cfp_status classify(cfp_ctx* c) {
+    const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
+    const int64_t N = c->N;
+    c->classified = false;
+    free_ptr(c->irr_lin);
+    free_ptr(c->ibi_off);
+    free_ptr(c->ibi_xyz);
+    free_ptr(c->corr_ptr);
+    free_ptr(c->corr_off);
+    free_ptr(c->corr_val);
+    free_ptr(c->corr_val32);
+    free_ptr(c->bib_ptr);
+    free_ptr(c->bib_idx);
+    free_ptr(c->bib_val);
+    free_ptr(c->krow);
+    free_ptr(c->krow32);
+    c->gsweeps[0] = c->gsweeps[1] = -1;  // side data changes: rebuild graphs
+
+    GeoArgs g;
+    for (int d = 0; d < 3; ++d) {
+        g.X[d] = c->dX[d];
+        g.n[d] = c->n[d];
+    }
+    g.bodies = c->dbodies;
+    g.nb = (int)c->bodies.size();
+    g.inside = c->fluid_inside;
+
+    k_classify_solid<<<grid_for(N, 256), 256, 0, c->stream>>>(g, c->type, N);
+    k_classify_irregular<<<grid_for((int64_t)(nx - 2) * (ny - 2) * (nz - 2), 256), 256, 0, c->stream>>>(
+        c->type, nx, ny, nz);
+    CFP_CUDA(cudaGetLastError());
+
+    long long h = 0;
+    // compaction of the irregular points (slot map and list), ascending index
+    {
+        // size the list first with a counting pass
+        long long nirr = 0;
+        const int64_t nb = (N + kScanChunk - 1) / kScanChunk;
+        if (nb > c->scan_cap) {
+            free_ptr(c->scan_bsum);
+            CFP_CUDA(cudaMalloc(&c->scan_bsum, sizeof(int) * nb));
+            c->scan_cap = nb;
+        }
+        k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(FlagIrregular{c->type}, N, c->scan_bsum);
+        k_scan_blocks<<<1, kScanThreads, 0, c->stream>>>(c->scan_bsum, (int)nb, c->dtotal);
+        CFP_CUDA(cudaGetLastError());
+        CFP_CUDA(cudaMemcpyAsync(&nirr, c->dtotal, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+        CFP_CUDA(cudaStreamSynchronize(c->stream));
+        c->n_irr = nirr;
+        CFP_CUDA(cudaMalloc(&c->irr_lin, sizeof(int32_t) * std::max<long long>(nirr, 1)));
+        k_scan_scatter<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(FlagIrregular{c->type},
+                                                                      SinkSlots{c->slot, c->irr_lin}, N,
+                                                                      c->scan_bsum);
+        CFP_CUDA(cudaGetLastError());
+    }
+    const int64_t nirr = c->n_irr;
+
+    IrrArgs ia;
+    ia.type = c->type;
+    ia.slot = c->slot;
+    ia.irr_lin = c->irr_lin;
+    ia.n_irr = nirr;
+    for (int d = 0; d < 3; ++d) ia.n[d] = c->n[d];
+
+    // IBI list: per irregular point, one IBI per solid axis neighbour
+    int* cnt = nullptr;
+    int* cnt2 = nullptr;
+    CFP_CUDA(cudaMalloc(&cnt, sizeof(int) * (nirr + 1)));
+    CFP_CUDA(cudaMalloc(&cnt2, sizeof(int) * (nirr + 1)));
+    CFP_CUDA(cudaMalloc(&c->ibi_off, sizeof(int32_t) * (nirr + 1)));
+    if (nirr) k_ibi_count<<<grid_for(nirr, 256), 256, 0, c->stream>>>(ia, cnt);
+    CFP_TRY(scan(c, FetchInt{cnt}, SinkOffsets{c->ibi_off}, nirr, c->dtotal, &h));
+    c->n_ibi = h;
+    CFP_CUDA(cudaMemcpyAsync(c->ibi_off + nirr, c->dtotal, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+    CFP_CUDA(cudaMalloc(&c->ibi_xyz, sizeof(double) * 3 * std::max<int64_t>(c->n_ibi, 1)));
+    if (nirr) k_ibi_roots<<<grid_for(nirr, 128), 128, 0, c->stream>>>(ia, g, c->ibi_off, c->ibi_xyz);
+    CFP_CUDA(cudaGetLastError());
+
+    // side list: count, scan, fill
+    SideArgs S;
+    S.a = ia;
+    const Grid<double> gv = grid_view<double>(c);
+    for (int d = 0; d < 3; ++d) {
+        S.ax[d] = gv.ax[d];
+        S.X[d] = c->dX[d];
+    }
+    S.ibi_off = c->ibi_off;
+    S.ibi_xyz = c->ibi_xyz;
+    CFP_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(DevError), c->stream));
+    CFP_CUDA(cudaMemsetAsync(c->dtotal + 4, 0, sizeof(long long), c->stream));
+    unsigned long long* ndeg = reinterpret_cast<unsigned long long*>(c->dtotal + 4);
+    if (nirr)
+        k_side<0><<<grid_for(nirr, 64), 64, 0, c->stream>>>(S, cnt, cnt2, nullptr, nullptr, nullptr, nullptr,
+                                                           nullptr, nullptr, nullptr, ndeg, c->derr);
+    CFP_CUDA(cudaGetLastError());
+    DevError he;
+    long long hdeg = 0;
+    CFP_CUDA(cudaMemcpyAsync(&he, c->derr, sizeof(DevError), cudaMemcpyDeviceToHost, c->stream));
+    CFP_CUDA(cudaMemcpyAsync(&hdeg, c->dtotal + 4, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    CFP_CUDA(cudaStreamSynchronize(c->stream));
+    c->n_deg = hdeg;
+    if (he.code) {
+        cudaFree(cnt);
+        cudaFree(cnt2);
+        const int i = he.lin % nx, j = (he.lin / nx) % ny, k = he.lin / (nx * ny);
+        const char* why = he.detail == DETAIL_BOXIBI ? "a modified stencil needs an IBI at a box node"
+                        : he.detail == DETAIL_FEWPOINTS ? "fewer than three points for a modified operator"
+                        : he.detail == DETAIL_SINGULAR ? "singular moment matrix"
+                        : he.detail == DETAIL_OVERFLOW ? "too many stencil entries"
+                        : "missing IBI";
+        c->class_status = CFP_EGEOM;
+        return fail(CFP_EGEOM, std::string("unsupported geometry at irregular point (") + std::to_string(i) + "," +
+                                   std::to_string(j) + "," + std::to_string(k) + "): " + why);
+    }
+    CFP_CUDA(cudaMalloc(&c->corr_ptr, sizeof(int32_t) * (nirr + 1)));
+    CFP_CUDA(cudaMalloc(&c->bib_ptr, sizeof(int32_t) * (nirr + 1)));
+    CFP_TRY(scan(c, FetchInt{cnt}, SinkOffsets{c->corr_ptr}, nirr, c->dtotal, &h));
+    c->n_corr = h;
+    CFP_CUDA(cudaMemcpyAsync(c->corr_ptr + nirr, c->dtotal, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+    CFP_TRY(scan(c, FetchInt{cnt2}, SinkOffsets{c->bib_ptr}, nirr, c->dtotal, &h));
+    c->n_bib = h;
+    CFP_CUDA(cudaMemcpyAsync(c->bib_ptr + nirr, c->dtotal, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+    CFP_CUDA(cudaMalloc(&c->corr_off, sizeof(int32_t) * std::max<int64_t>(c->n_corr, 1)));
+    CFP_CUDA(cudaMalloc(&c->corr_val, sizeof(double) * std::max<int64_t>(c->n_corr, 1)));
+    CFP_CUDA(cudaMalloc(&c->corr_val32, sizeof(float) * std::max<int64_t>(c->n_corr, 1)));
+    CFP_CUDA(cudaMalloc(&c->bib_idx, sizeof(int32_t) * std::max<int64_t>(c->n_bib, 1)));
+    CFP_CUDA(cudaMalloc(&c->bib_val, sizeof(double) * std::max<int64_t>(c->n_bib, 1)));
+    CFP_CUDA(cudaMalloc(&c->krow, sizeof(double) * 7 * std::max<int64_t>(nirr, 1)));
+    CFP_CUDA(cudaMalloc(&c->krow32, sizeof(float) * 7 * std::max<int64_t>(nirr, 1)));
+    if (nirr)
+        k_side<1><<<grid_for(nirr, 64), 64, 0, c->stream>>>(S, nullptr, nullptr, c->corr_ptr, c->corr_off,
+                                                           c->corr_val, c->bib_ptr, c->bib_idx, c->bib_val,
+                                                           c->krow, ndeg, c->derr);
+    if (c->n_corr)
+        k_to_float<<<grid_for(c->n_corr, 256), 256, 0, c->stream>>>(c->corr_val, c->corr_val32, c->n_corr);
+    if (nirr) k_to_float<<<grid_for(7 * nirr, 256), 256, 0, c->stream>>>(c->krow, c->krow32, 7 * nirr);
+    CFP_CUDA(cudaGetLastError());
+    CFP_CUDA(cudaStreamSynchronize(c->stream));
+    cudaFree(cnt);
+    cudaFree(cnt2);
+    c->classified = true;
+    c->class_status = CFP_OK;
+    return CFP_OK;
+}
+
+}  // namespace cfp

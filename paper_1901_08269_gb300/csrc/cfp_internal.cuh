@@ -1,0 +1,202 @@
+// Internal declarations of the CUDA library behind include/cfp.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cfp.h"
+
+namespace cfp {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+cfp_status fail(cfp_status st, const std::string& msg);
+cfp_status cuda_fail(cudaError_t e, const char* what);
+
+#define CFP_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return ::cfp::cuda_fail(e_, #call); \
+    } while (0)
+
+#define CFP_TRY(call)                          \
+    do {                                       \
+        cfp_status s_ = (call);                \
+        if (s_ != CFP_OK) return s_;           \
+    } while (0)
+
+// ------------------------------------------------------------ device types
+// Per-axis 1D grid metrics.  Compact (Eq. app_xxx): a, c, ar, br, cr with
+// b = 1; second order (Eq. 2ndorder_coef): ka, kb, kc.  Entries 0 and n-1
+// are zero.
+template <class T>
+struct Axis {
+    const T* a;
+    const T* c;
+    const T* ar;
+    const T* br;
+    const T* cr;
+    const T* ka;
+    const T* kb;
+    const T* kc;
+};
+
+template <class T>
+struct Grid {
+    Axis<T> ax[3];
+    int nx, ny, nz;
+};
+
+// Irregular-point side data, indexed by the slot of the irregular point
+// (its rank in ascending linear index).
+template <class T>
+struct Side {
+    const int32_t* slot;      // N: slot of an irregular node, -1 otherwise
+    const int32_t* corr_ptr;  // n_irr + 1: correction entries per slot
+    const int32_t* corr_off;  // linear-index offsets of the entries
+    const T* corr_val;        // coefficients added to the regular row
+    const T* krow;            // 7 per slot: K diag, -x, +x, -y, +y, -z, +z
+};
+
+// Device-resident scalars of one BiCGSTAB run (Algorithm 1).
+struct KState {
+    double rho, alpha, omega, beta;
+    double sigma, ts, tt, rr, rho_new;
+    double bnorm2;     // ||b||^2 of the system being solved
+    double stop2;      // stop when rr <= stop2
+    int iter, maxit;
+    int flag;          // FLAG_*
+    int execs;         // executed iteration bodies
+};
+
+enum { FLAG_RUN = 0, FLAG_CONV = 1, FLAG_BREAK = 2, FLAG_NAN = 3, FLAG_MAXIT = 4 };
+
+// First device error of the set-up kernels.
+struct DevError {
+    int code;    // cfp_status, 0 = none
+    int lin;     // node where it happened
+    int detail;  // kernel-specific
+    int pad;
+};
+
+enum { DETAIL_OFFGRID = 1, DETAIL_FEWPOINTS = 2, DETAIL_SINGULAR = 3, DETAIL_BOXIBI = 4,
+       DETAIL_OVERFLOW = 5, DETAIL_MISSINGIBI = 6 };
+
+constexpr int kApplyTX = 32;
+constexpr int kApplyTY = 8;
+constexpr int kApplyKC = 32;
+constexpr int kUpdBlocks = 152 * 8;   // grid of the vector-update kernels
+constexpr int kUpdThreads = 256;
+
+}  // namespace cfp
+
+// ------------------------------------------------------------------ context
+struct cfp_ctx {
+    int n[3] = {0, 0, 0};
+    int64_t N = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<double> X[3];
+    std::vector<cfp_body> bodies;
+    int fluid_inside = 0;
+
+    // grid metrics (device)
+    double* dX[3] = {nullptr, nullptr, nullptr};
+    double* dcoef64 = nullptr;  // 8 arrays per axis, n[d] each
+    float* dcoef32 = nullptr;
+    cfp_body* dbodies = nullptr;
+
+    // classification and side data
+    bool classified = false;
+    cfp_status class_status = CFP_OK;
+    uint8_t* type = nullptr;
+    int32_t* slot = nullptr;
+    int32_t* irr_lin = nullptr;
+    int64_t n_irr = 0, n_ibi = 0, n_deg = 0, n_corr = 0, n_bib = 0;
+    int32_t* ibi_off = nullptr;
+    double* ibi_xyz = nullptr;
+    int32_t* corr_ptr = nullptr;
+    int32_t* corr_off = nullptr;
+    double* corr_val = nullptr;
+    float* corr_val32 = nullptr;
+    int32_t* bib_ptr = nullptr;
+    int32_t* bib_idx = nullptr;
+    double* bib_val = nullptr;
+    double* krow = nullptr;
+    float* krow32 = nullptr;
+
+    // scan scratch
+    int* scan_bsum = nullptr;
+    int64_t scan_cap = 0;
+    long long* dtotal = nullptr;   // device counters (8)
+    cfp::DevError* derr = nullptr;
+
+    // Krylov work space
+    double* v64 = nullptr;    // kNV64 fields
+    float* v32 = nullptr;     // kNV32 fields
+    double* partial = nullptr;
+    int64_t partial_cap = 0;
+    cfp::KState* kst = nullptr;   // [0]: FP64 run, [1]: FP32 run
+    cfp::KState* hkst = nullptr;  // pinned host mirror
+
+    // host-buffer solve
+    double* hs_f = nullptr;
+    double* hs_g = nullptr;
+    double* hs_u = nullptr;
+    double* hs_gi = nullptr;
+    int64_t hs_gi_cap = 0;
+
+    // kernels enqueued since the counter was last reset
+    int64_t launches = 0;
+
+    // graphs: [precision][sweeps-config]
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int gsweeps[2] = {-1, -1};
+};
+
+namespace cfp {
+
+constexpr int kNV64 = 12;  // x r rh p ph v s sh t rhs tmp tmp2
+constexpr int kNV32 = 9;   // x r rh p ph v s sh t
+enum { V_X = 0, V_R, V_RH, V_P, V_PH, V_V, V_S, V_SH, V_T, V_RHS, V_TMP, V_TMP2 };
+
+// geometry (cfp_geometry.cu)
+cfp_status classify(cfp_ctx* c);
+
+// stencils (cfp_stencil.cu)
+template <class T>
+Grid<T> grid_view(cfp_ctx* c);
+template <>
+Grid<double> grid_view<double>(cfp_ctx* c);
+template <>
+Grid<float> grid_view<float>(cfp_ctx* c);
+template <class T>
+Side<T> side_view(cfp_ctx* c);
+template <>
+Side<double> side_view<double>(cfp_ctx* c);
+template <>
+Side<float> side_view<float>(cfp_ctx* c);
+template <class T>
+void launch_apply(cfp_ctx* c, const T* x, T* y, const T* d0, int dotmode, double* partial,
+                  cudaStream_t s, int* nblocks_out);
+template <class T>
+void launch_precond(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s);
+template <class T>
+void launch_rbgs_half(cfp_ctx* c, const T* rho, T* phi, int colour, bool first, cudaStream_t s);
+inline int precond_kernels(int sweeps) { return sweeps <= 0 ? 1 : 2 * sweeps; }
+void launch_qf(cfp_ctx* c, const double* f, double* out, cudaStream_t s);
+void launch_rhs_finish(cfp_ctx* c, const double* qf, const double* bg, const double* g_ibi,
+                       double* rhs, cudaStream_t s);
+void launch_boundary_lift(cfp_ctx* c, const double* g, double* gb, cudaStream_t s);
+void launch_finish_solution(cfp_ctx* c, const double* x, const double* g, double* u, cudaStream_t s);
+void launch_mask_unknowns(cfp_ctx* c, const double* in, double* out, cudaStream_t s);
+int apply_blocks(cfp_ctx* c);
+
+// Krylov (cfp_krylov.cu)
+cfp_status ensure_work(cfp_ctx* c, bool need32);
+cfp_status time_kernel(cfp_ctx* c, int kernel, int prec, int reps, double* ms, double* bytes);
+
+}  // namespace cfp

@@ -1,0 +1,567 @@
+// Preconditioned BiCGSTAB (Algorithm 1, Sec. 3.2), with the preconditioner
+// of Sec. 3.3 applied on the right: p_hat = P p, s_hat = P s and the update
+// u += alpha p_hat + omega s_hat.  All scalars live on the device; the
+// iteration body is captured once per (precision, sweeps) into a CUDA graph
+// whose while-node condition is set by the last scalar kernel, so a whole
+// solve runs without returning to the host.  The iteration cap bounds the
+// loop.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "cfp_internal.cuh"
+
+namespace cfp {
+namespace {
+
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+    __shared__ double sa[32], sb[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        sa[wid] = a;
+        sb[wid] = b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        a = lane < nw ? sa[lane] : 0.0;
+        b = lane < nw ? sb[lane] : 0.0;
+        for (int o = 16; o; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+    }
+    __syncthreads();
+}
+
+// fixed-order sum of nb pairs of block partials (one block of 256 threads)
+__device__ void sum_partials(const double* partial, int nb, double& a, double& b) {
+    a = 0.0;
+    b = 0.0;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+        a += partial[2 * q];
+        b += partial[2 * q + 1];
+    }
+    block_sum2(a, b);
+}
+
+#define GRID_STRIDE(l, N) \
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < (N); l += (int64_t)gridDim.x * blockDim.x)
+
+// r = b - v, r_hat0 = r, p = r; partial (r, r)
+template <class T>
+__global__ void k_init_r(const T* __restrict__ b, const T* __restrict__ v, T* __restrict__ r, T* __restrict__ rh,
+                         T* __restrict__ p, double* __restrict__ partial, int64_t N) {
+    double a = 0.0, z = 0.0;
+    GRID_STRIDE(l, N) {
+        const T x = b[l] - v[l];
+        r[l] = x;
+        rh[l] = x;
+        p[l] = x;
+        a += (double)x * (double)x;
+    }
+    block_sum2(a, z);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+// Algorithm 1, line 7: s = r - alpha v
+template <class T>
+__global__ void k_axpy_s(const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ s,
+                         const KState* __restrict__ st, int64_t N) {
+    if (st->flag != FLAG_RUN) return;
+    const T alpha = (T)st->alpha;
+    GRID_STRIDE(l, N) s[l] = r[l] - alpha * v[l];
+}
+
+// Algorithm 1, lines 11-12 with the preconditioned directions:
+// u += alpha p_hat + omega s_hat; r = s - omega t; partials (r_hat0, r), (r, r)
+template <class T>
+__global__ void k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ ph,
+                            const T* __restrict__ sh, const T* __restrict__ s, const T* __restrict__ t,
+                            const T* __restrict__ rh, const KState* __restrict__ st,
+                            double* __restrict__ partial, int64_t N) {
+    if (st->flag != FLAG_RUN) return;
+    const T alpha = (T)st->alpha, omega = (T)st->omega;
+    double a = 0.0, b = 0.0;
+    GRID_STRIDE(l, N) {
+        x[l] += alpha * ph[l] + omega * sh[l];
+        const T rn = s[l] - omega * t[l];
+        r[l] = rn;
+        a += (double)rh[l] * (double)rn;
+        b += (double)rn * (double)rn;
+    }
+    block_sum2(a, b);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// Algorithm 1, line 14: p = r + beta (p - omega v)
+template <class T>
+__global__ void k_update_p(T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ v,
+                           const KState* __restrict__ st, int64_t N) {
+    if (st->flag != FLAG_RUN) return;
+    const T beta = (T)st->beta, omega = (T)st->omega;
+    GRID_STRIDE(l, N) p[l] = r[l] + beta * (p[l] - omega * v[l]);
+}
+
+__global__ void k_fin_init(KState* st, const double* partial, int nb) {
+    double rr, z;
+    sum_partials(partial, nb, rr, z);
+    if (threadIdx.x == 0) {
+        st->rr = rr;
+        st->rho = rr;  // r_hat0 = r0
+        st->iter = 0;
+        st->flag = !isfinite(rr) ? FLAG_NAN : (rr <= st->stop2 ? FLAG_CONV : FLAG_RUN);
+    }
+}
+
+// line 6: alpha = (r_hat0, r) / (r_hat0, v)
+__global__ void k_fin_alpha(KState* st, const double* partial, int nb) {
+    if (st->flag != FLAG_RUN) return;
+    double sigma, z;
+    sum_partials(partial, nb, sigma, z);
+    if (threadIdx.x == 0) {
+        st->sigma = sigma;
+        if (!isfinite(sigma)) st->flag = FLAG_NAN;
+        else if (sigma == 0.0) st->flag = FLAG_BREAK;
+        else st->alpha = st->rho / sigma;
+    }
+}
+
+// line 10: omega = (t, s) / (t, t)
+__global__ void k_fin_omega(KState* st, const double* partial, int nb) {
+    if (st->flag != FLAG_RUN) return;
+    double ts, tt;
+    sum_partials(partial, nb, ts, tt);
+    if (threadIdx.x == 0) {
+        st->ts = ts;
+        st->tt = tt;
+        if (!isfinite(tt) || !isfinite(ts)) st->flag = FLAG_NAN;
+        else st->omega = tt > 0.0 ? ts / tt : 0.0;
+    }
+}
+
+// line 13 and the stopping test; sets the graph's while condition
+__global__ void k_fin_beta(KState* st, const double* partial, int nb, cudaGraphConditionalHandle h, int use_cond) {
+    if (threadIdx.x == 0) st->execs += 1;
+    if (st->flag == FLAG_RUN) {
+        double rho_new, rr;
+        sum_partials(partial, nb, rho_new, rr);
+        if (threadIdx.x == 0) {
+            st->iter += 1;
+            st->rr = rr;
+            st->rho_new = rho_new;
+            if (!isfinite(rr)) st->flag = FLAG_NAN;
+            else if (rr <= st->stop2) st->flag = FLAG_CONV;
+            else if (st->omega == 0.0 || st->rho == 0.0) st->flag = FLAG_BREAK;
+            else if (st->iter >= st->maxit) st->flag = FLAG_MAXIT;
+            else {
+                st->beta = (rho_new / st->rho) * (st->alpha / st->omega);
+                st->rho = rho_new;
+            }
+        }
+    }
+    __syncthreads();
+    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(h, st->flag == FLAG_RUN ? 1u : 0u);
+}
+
+// out = b - y at every node; partial (out, out)
+__global__ void k_resid(const double* __restrict__ b, const double* __restrict__ y, double* __restrict__ out,
+                        double* __restrict__ partial, int64_t N) {
+    double a = 0.0, z = 0.0;
+    GRID_STRIDE(l, N) {
+        const double v = b[l] - y[l];
+        out[l] = v;
+        a += v * v;
+    }
+    block_sum2(a, z);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+__global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ partial,
+                      int64_t N) {
+    double s = 0.0, z = 0.0;
+    GRID_STRIDE(l, N) s += a[l] * b[l];
+    block_sum2(s, z);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = s;
+        partial[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+__global__ void k_fin_store(const double* partial, int nb, double* out) {
+    double a, b;
+    sum_partials(partial, nb, a, b);
+    if (threadIdx.x == 0) out[0] = a;
+}
+
+__global__ void k_to32(const double* __restrict__ in, float* __restrict__ out, double scale, int64_t N) {
+    GRID_STRIDE(l, N) out[l] = (float)(in[l] * scale);
+}
+
+__global__ void k_add32(double* __restrict__ x, const float* __restrict__ e, double scale, int64_t N) {
+    GRID_STRIDE(l, N) x[l] += (double)e[l] * scale;
+}
+
+template <class T>
+__global__ void k_zero(T* __restrict__ x, int64_t N) {
+    GRID_STRIDE(l, N) x[l] = T(0);
+}
+
+// --------------------------------------------------------------- host side
+template <class T>
+struct Vecs {
+    T *x, *r, *rh, *p, *ph, *v, *s, *sh, *t;
+};
+
+Vecs<double> vecs64(cfp_ctx* c) {
+    double* b = c->v64;
+    const int64_t N = c->N;
+    return Vecs<double>{b + V_X * N, b + V_R * N, b + V_RH * N, b + V_P * N, b + V_PH * N,
+                        b + V_V * N, b + V_S * N, b + V_SH * N, b + V_T * N};
+}
+Vecs<float> vecs32(cfp_ctx* c) {
+    float* b = c->v32;
+    const int64_t N = c->N;
+    return Vecs<float>{b + 0 * N, b + 1 * N, b + 2 * N, b + 3 * N, b + 4 * N, b + 5 * N, b + 6 * N, b + 7 * N, b + 8 * N};
+}
+template <class T>
+Vecs<T> vecs(cfp_ctx* c);
+template <>
+Vecs<double> vecs<double>(cfp_ctx* c) { return vecs64(c); }
+template <>
+Vecs<float> vecs<float>(cfp_ctx* c) { return vecs32(c); }
+
+// One iteration of Algorithm 1 (lines 4-14) on stream s.
+template <class T>
+void enqueue_body(cfp_ctx* c, int prec, int sweeps, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+    Vecs<T> V = vecs<T>(c);
+    KState* st = c->kst + prec;
+    const int64_t N = c->N;
+    int nb = 0;
+    launch_precond<T>(c, sweeps, V.p, V.ph, s);                       // line 4
+    launch_apply<T>(c, V.ph, V.v, V.rh, 1, c->partial, s, &nb);        // line 5 (+ (r_hat0, v))
+    k_fin_alpha<<<1, 256, 0, s>>>(st, c->partial, nb);                // line 6
+    k_axpy_s<T><<<kUpdBlocks, kUpdThreads, 0, s>>>(V.r, V.v, V.s, st, N);  // line 7
+    launch_precond<T>(c, sweeps, V.s, V.sh, s);                       // line 8
+    launch_apply<T>(c, V.sh, V.t, V.s, 2, c->partial, s, &nb);         // line 9 (+ (t, s), (t, t))
+    k_fin_omega<<<1, 256, 0, s>>>(st, c->partial, nb);                // line 10
+    k_update_xr<T><<<kUpdBlocks, kUpdThreads, 0, s>>>(V.x, V.r, V.ph, V.sh, V.s, V.t, V.rh, st, c->partial, N);
+    k_fin_beta<<<1, 256, 0, s>>>(st, c->partial, kUpdBlocks, h, use_cond);  // line 13 + stop test
+    k_update_p<T><<<kUpdBlocks, kUpdThreads, 0, s>>>(V.p, V.r, V.v, st, N);  // line 14
+    c->launches += 6;
+}
+
+int body_kernels(int sweeps) { return 2 * precond_kernels(sweeps) + 2 + 6; }
+
+template <class T>
+cfp_status build_graph(cfp_ctx* c, int prec, int sweeps) {
+    if (c->gexec[prec] && c->gsweeps[prec] == sweeps) return CFP_OK;
+    if (c->gexec[prec]) {
+        cudaGraphExecDestroy(c->gexec[prec]);
+        c->gexec[prec] = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    CFP_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    CFP_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CFP_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    CFP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        const int64_t saved = c->launches;
+        enqueue_body<T>(c, prec, sweeps, cs, h, 1);
+        c->launches = saved;
+        cudaGraph_t out = nullptr;
+        e = cudaStreamEndCapture(cs, &out);
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(e, "capturing the BiCGSTAB body");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    c->gexec[prec] = exec;
+    c->gsweeps[prec] = sweeps;
+    return CFP_OK;
+}
+
+// Solve B x = b (b and x zero off the unknowns) until ||r||^2 <= stop2 or
+// maxit iterations; x holds the initial guess.  Returns the final flag.
+template <class T>
+cfp_status run_bicgstab(cfp_ctx* c, int prec, const T* b, double stop2, int maxit, int sweeps, bool use_graph,
+                        int* flag, int* used, double* rr) {
+    Vecs<T> V = vecs<T>(c);
+    KState* st = c->kst + prec;
+    KState* hs = c->hkst + prec;
+    const int64_t N = c->N;
+    memset(hs, 0, sizeof(KState));
+    hs->stop2 = stop2;
+    hs->maxit = std::max(1, maxit);
+    CFP_CUDA(cudaMemcpyAsync(st, hs, sizeof(KState), cudaMemcpyHostToDevice, c->stream));
+    launch_apply<T>(c, V.x, V.v, nullptr, 0, nullptr, c->stream, nullptr);
+    k_init_r<T><<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(b, V.v, V.r, V.rh, V.p, c->partial, N);
+    k_fin_init<<<1, 256, 0, c->stream>>>(st, c->partial, kUpdBlocks);
+    c->launches += 2;
+    CFP_CUDA(cudaGetLastError());
+    if (use_graph) {
+        CFP_TRY(build_graph<T>(c, prec, sweeps));
+        CFP_CUDA(cudaGraphLaunch(c->gexec[prec], c->stream));
+    } else {
+        for (int it = 0; it < maxit;) {
+            const int chunk = std::min(16, maxit - it);
+            for (int q = 0; q < chunk; ++q) enqueue_body<T>(c, prec, sweeps, c->stream, 0, 0);
+            it += chunk;
+            CFP_CUDA(cudaGetLastError());
+            CFP_CUDA(cudaMemcpyAsync(hs, st, sizeof(KState), cudaMemcpyDeviceToHost, c->stream));
+            CFP_CUDA(cudaStreamSynchronize(c->stream));
+            if (hs->flag != FLAG_RUN) break;
+        }
+    }
+    CFP_CUDA(cudaMemcpyAsync(hs, st, sizeof(KState), cudaMemcpyDeviceToHost, c->stream));
+    CFP_CUDA(cudaStreamSynchronize(c->stream));
+    if (use_graph) c->launches += (int64_t)hs->execs * body_kernels(sweeps);
+    *flag = hs->flag == FLAG_RUN ? FLAG_MAXIT : hs->flag;
+    *used = hs->iter;
+    *rr = hs->rr;
+    return CFP_OK;
+}
+
+double* scalar_slot(cfp_ctx* c, int q) { return reinterpret_cast<double*>(c->dtotal) + q; }
+
+// ||b - B x||^2 with out = b - B x (FP64)
+cfp_status true_residual(cfp_ctx* c, const double* b, const double* x, double* out, double* r2) {
+    double* tmp = c->v64 + V_TMP2 * c->N;
+    launch_apply<double>(c, x, tmp, nullptr, 0, nullptr, c->stream, nullptr);
+    k_resid<<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(b, tmp, out, c->partial, c->N);
+    k_fin_store<<<1, 256, 0, c->stream>>>(c->partial, kUpdBlocks, scalar_slot(c, 6));
+    c->launches += 2;
+    CFP_CUDA(cudaGetLastError());
+    CFP_CUDA(cudaMemcpyAsync(r2, scalar_slot(c, 6), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CFP_CUDA(cudaStreamSynchronize(c->stream));
+    return CFP_OK;
+}
+
+cfp_status dot_host(cfp_ctx* c, const double* a, const double* b, double* out) {
+    k_dot<<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(a, b, c->partial, c->N);
+    k_fin_store<<<1, 256, 0, c->stream>>>(c->partial, kUpdBlocks, scalar_slot(c, 7));
+    c->launches += 2;
+    CFP_CUDA(cudaGetLastError());
+    CFP_CUDA(cudaMemcpyAsync(out, scalar_slot(c, 7), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CFP_CUDA(cudaStreamSynchronize(c->stream));
+    return CFP_OK;
+}
+
+cfp_status status_of(int flag) {
+    return flag == FLAG_NAN ? CFP_ENAN : flag == FLAG_BREAK ? CFP_EBREAKDOWN : CFP_ENOCONV;
+}
+
+}  // namespace
+
+cfp_status ensure_work(cfp_ctx* c, bool need32) {
+    const int64_t N = c->N;
+    if (!c->v64) {
+        CFP_CUDA(cudaMalloc(&c->v64, sizeof(double) * N * kNV64));
+        CFP_CUDA(cudaMemsetAsync(c->v64, 0, sizeof(double) * N * kNV64, c->stream));
+    }
+    if (need32 && !c->v32) {
+        CFP_CUDA(cudaMalloc(&c->v32, sizeof(float) * N * (kNV32 + 1)));
+        CFP_CUDA(cudaMemsetAsync(c->v32, 0, sizeof(float) * N * (kNV32 + 1), c->stream));
+    }
+    const int64_t need = 2 * (int64_t)std::max(apply_blocks(c), kUpdBlocks);
+    if (c->partial_cap < need) {
+        if (c->partial) cudaFree(c->partial);
+        c->partial = nullptr;
+        CFP_CUDA(cudaMalloc(&c->partial, sizeof(double) * need));
+        c->partial_cap = need;
+    }
+    return CFP_OK;
+}
+
+namespace {
+template <class T>
+cfp_status time_kernel_t(cfp_ctx* c, int prec, int kernel, int reps, double* ms, double* bytes) {
+    Vecs<T> V = vecs<T>(c);
+    KState* st = c->kst + prec;
+    KState* hs = c->hkst + prec;
+    memset(hs, 0, sizeof(KState));
+    hs->flag = FLAG_RUN;  // alpha = omega = 0: the update leaves x unchanged
+    CFP_CUDA(cudaMemcpyAsync(st, hs, sizeof(KState), cudaMemcpyHostToDevice, c->stream));
+    const int64_t nint = (int64_t)(c->n[0] - 2) * (c->n[1] - 2) * (c->n[2] - 2);
+    auto launch = [&]() {
+        if (kernel == CFP_KERNEL_APPLY) launch_apply<T>(c, V.ph, V.v, V.rh, 1, c->partial, c->stream, nullptr);
+        else if (kernel == CFP_KERNEL_RBGS) launch_rbgs_half<T>(c, V.p, V.ph, 0, false, c->stream);
+        else
+            k_update_xr<T><<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(V.x, V.r, V.ph, V.sh, V.s, V.t, V.rh, st,
+                                                                      c->partial, c->N);
+    };
+    for (int q = 0; q < 2; ++q) launch();
+    cudaEvent_t e0, e1;
+    CFP_CUDA(cudaEventCreate(&e0));
+    CFP_CUDA(cudaEventCreate(&e1));
+    CFP_CUDA(cudaEventRecord(e0, c->stream));
+    for (int q = 0; q < reps; ++q) launch();
+    CFP_CUDA(cudaEventRecord(e1, c->stream));
+    CFP_CUDA(cudaGetLastError());
+    CFP_CUDA(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CFP_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = (double)t / reps;
+    const double w = (double)sizeof(T);
+    if (bytes)
+        *bytes = kernel == CFP_KERNEL_APPLY ? 3.0 * w * nint
+               : kernel == CFP_KERNEL_RBGS ? 1.5 * w * nint
+                                           : 8.0 * w * (double)c->N;
+    return CFP_OK;
+}
+}  // namespace
+
+cfp_status time_kernel(cfp_ctx* c, int kernel, int prec, int reps, double* ms, double* bytes) {
+    if (kernel < CFP_KERNEL_APPLY || kernel > CFP_KERNEL_UPDATE || reps < 1 || !ms)
+        return fail(CFP_EINVAL, "bad kernel id, reps or output pointer");
+    CFP_TRY(ensure_work(c, prec == CFP_PREC_MIXED));
+    return prec == CFP_PREC_MIXED ? time_kernel_t<float>(c, 1, kernel, reps, ms, bytes)
+                                  : time_kernel_t<double>(c, 0, kernel, reps, ms, bytes);
+}
+
+cfp_status solve_impl(cfp_ctx* c, const double* f, const double* g, const double* gi, double* u, double tol,
+                      const cfp_opts* opts, cfp_info* info);
+
+}  // namespace cfp
+
+using namespace cfp;
+
+// The FP64 and mixed-precision drivers.
+cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const double* gi, double* u, double tol,
+                           const cfp_opts* o, cfp_info* info) {
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    cfp_opts opts;
+    cfp_default_opts(&opts);
+    if (o) opts = *o;
+    if (!(tol > 0.0) || opts.maxit < 1 || opts.sweeps < 0) return fail(CFP_EINVAL, "bad tol, maxit or sweeps");
+    c->launches = 0;
+    if (!c->classified) CFP_TRY(classify(c));
+    const bool mixed = opts.precision == CFP_PREC_MIXED;
+    CFP_TRY(ensure_work(c, mixed));
+    const int64_t N = c->N;
+    double* rhs = c->v64 + V_RHS * N;
+    double* tmp = c->v64 + V_TMP * N;
+    double* X = c->v64 + V_X * N;
+    const auto t1 = clk::now();
+    cfp_status st = cfp_assemble_rhs(c, f, g, gi, rhs);
+    if (st) return st;
+    launch_mask_unknowns(c, u, X, c->stream);
+    double b2 = 0.0;
+    CFP_TRY(dot_host(c, rhs, rhs, &b2));
+    const auto t2 = clk::now();
+    int total = 0, restarts = 0, refinements = 0;
+    double rel = 0.0;
+    cfp_status status = CFP_OK;
+    if (!isfinite(b2)) {
+        status = CFP_ENAN;
+        rel = NAN;
+    } else if (b2 == 0.0) {
+        CFP_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * N, c->stream));
+    } else if (!mixed) {
+        for (;;) {
+            int flag = 0, used = 0;
+            double rr = 0.0;
+            CFP_TRY(run_bicgstab<double>(c, 0, rhs, tol * tol * b2, opts.maxit - total, opts.sweeps,
+                                         opts.use_graph != 0, &flag, &used, &rr));
+            total += used;
+            double r2 = 0.0;
+            CFP_TRY(true_residual(c, rhs, X, tmp, &r2));
+            rel = sqrt(r2 / b2);
+            if (flag == FLAG_NAN || !isfinite(rel)) { status = CFP_ENAN; break; }
+            if (rel <= tol) { status = CFP_OK; break; }
+            if (total >= opts.maxit) { status = CFP_ENOCONV; break; }
+            if (restarts >= opts.max_restarts) { status = status_of(flag); break; }
+            ++restarts;
+        }
+    } else {
+        // Iterative refinement: FP64 residual (with the FP64 irregular rows),
+        // FP32 correction solve, FP64 update.
+        float* b32 = c->v32 + kNV32 * N;
+        float* e32 = c->v32;  // the x vector of the FP32 run
+        double r2 = 0.0;
+        CFP_TRY(true_residual(c, rhs, X, tmp, &r2));
+        rel = sqrt(r2 / b2);
+        double prev = INFINITY;
+        int stall = 0;
+        while (rel > tol && isfinite(rel)) {
+            if (refinements >= opts.max_refine || total >= opts.maxit) { status = CFP_ENOCONV; break; }
+            const double scale = 1.0 / sqrt(r2);
+            k_to32<<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(tmp, b32, scale, N);
+            k_zero<float><<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(e32, N);
+            c->launches += 2;
+            int flag = 0, used = 0;
+            double rr = 0.0;
+            const double it2 = opts.inner_tol * opts.inner_tol;
+            CFP_TRY(run_bicgstab<float>(c, 1, b32, it2, opts.maxit - total, opts.sweeps, opts.use_graph != 0, &flag,
+                                        &used, &rr));
+            total += used;
+            ++refinements;
+            if (flag == FLAG_NAN) { status = CFP_ENAN; break; }
+            k_add32<<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(X, e32, 1.0 / scale, N);
+            c->launches += 1;
+            CFP_TRY(true_residual(c, rhs, X, tmp, &r2));
+            rel = sqrt(r2 / b2);
+            if (!(rel < 0.9 * prev)) {
+                if (++stall > opts.max_restarts) { status = status_of(flag); break; }
+            }
+            prev = std::min(prev, rel);
+        }
+        if (!isfinite(rel)) status = CFP_ENAN;
+        restarts = 0;
+    }
+    launch_finish_solution(c, X, g, u, c->stream);
+    CFP_CUDA(cudaGetLastError());
+    CFP_CUDA(cudaStreamSynchronize(c->stream));
+    const auto t3 = clk::now();
+    if (info) {
+        info->status = status;
+        info->iterations = total;
+        info->restarts = restarts;
+        info->refinements = refinements;
+        info->rel_residual = rel;
+        info->n_irregular = c->n_irr;
+        info->n_ibi = c->n_ibi;
+        info->n_degenerate = c->n_deg;
+        info->ms_setup = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        info->ms_rhs = std::chrono::duration<double, std::milli>(t2 - t1).count();
+        info->ms_solve = std::chrono::duration<double, std::milli>(t3 - t2).count();
+        info->launches = c->launches;
+    }
+    if (status != CFP_OK)
+        return fail(status, status == CFP_ENAN ? "non-finite value in the solve"
+                            : status == CFP_EBREAKDOWN ? "BiCGSTAB breakdown after restarts"
+                                                       : "no convergence within the iteration cap");
+    return CFP_OK;
+}

@@ -1,0 +1,393 @@
+// Matrix-free operators on the grid:
+//  - B x (Eq. Bdec): the regular 27-point compact stencil of Eqs. A27/As_qs
+//    rebuilt on the fly from the 1D metrics, sum-factorised as
+//      A x = sum_r Lz[r] (sum_q Ly[q] XR + Ry[q] XL) + Rz[r] (sum_q Ly[q] XL),
+//      XR = sum_p Rx[p] x,  XL = sum_p Lx[p] x,
+//    with the x-pass of each z-plane staged in shared memory and the y-pass
+//    results of three planes kept in registers while a CTA marches in z;
+//    rows of irregular points get their modified-stencil corrections from the
+//    side list in the same pass; solid rows are zero.
+//  - red-black Gauss-Seidel half-sweeps on K (Eqs. A7 / A7_mod, Sec. 3.3).
+//  - the source term of Eq. q with solid weights dropped, and helpers of the
+//    right-hand side of Eq. Bu=q.
+#include <algorithm>
+
+#include "cfp_internal.cuh"
+
+namespace cfp {
+
+template <>
+Grid<double> grid_view<double>(cfp_ctx* c) {
+    Grid<double> g;
+    int64_t off = 0;
+    for (int d = 0; d < 3; ++d) {
+        const int n = c->n[d];
+        double* b = c->dcoef64 + off;
+        g.ax[d] = Axis<double>{b, b + n, b + 2 * n, b + 3 * n, b + 4 * n, b + 5 * n, b + 6 * n, b + 7 * n};
+        off += 8 * (int64_t)n;
+    }
+    g.nx = c->n[0];
+    g.ny = c->n[1];
+    g.nz = c->n[2];
+    return g;
+}
+
+template <>
+Grid<float> grid_view<float>(cfp_ctx* c) {
+    Grid<float> g;
+    int64_t off = 0;
+    for (int d = 0; d < 3; ++d) {
+        const int n = c->n[d];
+        float* b = c->dcoef32 + off;
+        g.ax[d] = Axis<float>{b, b + n, b + 2 * n, b + 3 * n, b + 4 * n, b + 5 * n, b + 6 * n, b + 7 * n};
+        off += 8 * (int64_t)n;
+    }
+    g.nx = c->n[0];
+    g.ny = c->n[1];
+    g.nz = c->n[2];
+    return g;
+}
+
+template <>
+Side<double> side_view<double>(cfp_ctx* c) {
+    return Side<double>{c->slot, c->corr_ptr, c->corr_off, c->corr_val, c->krow};
+}
+
+template <>
+Side<float> side_view<float>(cfp_ctx* c) {
+    return Side<float>{c->slot, c->corr_ptr, c->corr_off, c->corr_val32, c->krow32};
+}
+
+namespace {
+
+__device__ __forceinline__ void block_reduce2(double& a, double& b) {
+    __shared__ double sa[32], sb[32];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        sa[wid] = a;
+        sb[wid] = b;
+    }
+    __syncthreads();
+    const int nw = (blockDim.x * blockDim.y) >> 5;
+    if (wid == 0) {
+        a = lane < nw ? sa[lane] : 0.0;
+        b = lane < nw ? sb[lane] : 0.0;
+        for (int o = 16; o; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+    }
+}
+
+// DOT = 0: y only; 1: partial (d0, y); 2: partials (d0, y) and (y, y)
+template <class T, int DOT>
+__global__ void __launch_bounds__(kApplyTX* kApplyTY)
+    k_apply(Grid<T> G, Side<T> S, const uint8_t* __restrict__ type, const T* __restrict__ x,
+            T* __restrict__ y, const T* __restrict__ d0, double* __restrict__ partial) {
+    __shared__ T sR[kApplyTY + 2][kApplyTX];
+    __shared__ T sL[kApplyTY + 2][kApplyTX];
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = 1 + blockIdx.x * kApplyTX + tx;
+    const int j0 = 1 + blockIdx.y * kApplyTY;
+    const int j = j0 + ty;
+    const int k0 = 1 + blockIdx.z * kApplyKC;
+    const int k1 = min(k0 + kApplyKC, nz - 1);
+    const bool iin = i <= nx - 2;
+    const bool jin = j <= ny - 2;
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+
+    T ax = 0, cx = 0, arx = 0, brx = 0, crx = 0;
+    if (iin) {
+        ax = G.ax[0].a[i];
+        cx = G.ax[0].c[i];
+        arx = G.ax[0].ar[i];
+        brx = G.ax[0].br[i];
+        crx = G.ax[0].cr[i];
+    }
+    T ay = 0, cy = 0, ary = 0, bry = 0, cry = 0;
+    if (jin) {
+        ay = G.ax[1].a[j];
+        cy = G.ax[1].c[j];
+        ary = G.ax[1].ar[j];
+        bry = G.ax[1].br[j];
+        cry = G.ax[1].cr[j];
+    }
+    T Pm = 0, P0 = 0, Pp = 0, Qm = 0, Q0 = 0, Qp = 0;
+    double acc0 = 0.0, acc1 = 0.0;
+
+    for (int kk = k0 - 1; kk <= k1; ++kk) {
+        for (int r = ty; r < kApplyTY + 2; r += kApplyTY) {
+            const int J = j0 - 1 + r;
+            T vr = 0, vl = 0;
+            if (iin && J <= ny - 1) {
+                const T* row = x + (int64_t)kk * sz + (int64_t)J * sy + i;
+                const T xm = row[-1], xc = row[0], xp = row[1];
+                vr = arx * xm + brx * xc + crx * xp;
+                vl = ax * xm + xc + cx * xp;
+            }
+            sR[r][tx] = vr;
+            sL[r][tx] = vl;
+        }
+        __syncthreads();
+        const T P = ay * sR[ty][tx] + sR[ty + 1][tx] + cy * sR[ty + 2][tx] + ary * sL[ty][tx] +
+                    bry * sL[ty + 1][tx] + cry * sL[ty + 2][tx];
+        const T Q = ay * sL[ty][tx] + sL[ty + 1][tx] + cy * sL[ty + 2][tx];
+        __syncthreads();
+        Pm = P0;
+        P0 = Pp;
+        Pp = P;
+        Qm = Q0;
+        Q0 = Qp;
+        Qp = Q;
+        if (kk >= k0 + 1 && iin && jin) {
+            const int k = kk - 1;
+            const T az = G.ax[2].a[k], cz = G.ax[2].c[k];
+            const T arz = G.ax[2].ar[k], brz = G.ax[2].br[k], crz = G.ax[2].cr[k];
+            T v = az * Pm + P0 + cz * Pp + (arz * Qm + brz * Q0 + crz * Qp);
+            const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
+            const uint8_t t = type[l];
+            if (t == CFP_SOLID) {
+                v = 0;
+            } else if (t == CFP_IRREGULAR) {
+                const int s = S.slot[l];
+                const int e1 = S.corr_ptr[s + 1];
+                for (int e = S.corr_ptr[s]; e < e1; ++e) v += S.corr_val[e] * x[l + S.corr_off[e]];
+            }
+            y[l] = v;
+            if (DOT >= 1) acc0 += (double)d0[l] * (double)v;
+            if (DOT == 2) acc1 += (double)v * (double)v;
+        }
+    }
+    if (DOT) {
+        block_reduce2(acc0, acc1);
+        if (tx == 0 && ty == 0) {
+            const int64_t b = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+            partial[2 * b] = acc0;
+            partial[2 * b + 1] = acc1;
+        }
+    }
+}
+
+// One red-black Gauss-Seidel half-sweep on K phi = rho over the points of
+// one colour ((i+j+k) % 2 == colour).  FIRST: phi = 0 on entry, so the
+// neighbour sum vanishes.  Only unknowns are written; phi must be zero at
+// box and solid nodes.
+template <class T, bool FIRST>
+__global__ void __launch_bounds__(256)
+    k_rbgs(Grid<T> G, Side<T> S, const uint8_t* __restrict__ type, const T* __restrict__ rho,
+           T* __restrict__ phi, int colour) {
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const int nh = (nx - 1) / 2;
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    const int64_t total = (int64_t)nh * (ny - 2) * (nz - 2);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(q % nh);
+        const int j = 1 + (int)((q / nh) % (ny - 2));
+        const int k = 1 + (int)(q / ((int64_t)nh * (ny - 2)));
+        const int i = 1 + ((1 + j + k + colour) & 1) + 2 * m;
+        if (i > nx - 2) continue;
+        const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
+        const uint8_t t = type[l];
+        if (t != CFP_REGULAR && t != CFP_IRREGULAR) continue;
+        T dg, cxm, cxp, cym, cyp, czm, czp;
+        if (t == CFP_IRREGULAR) {
+            const T* kr = S.krow + 7 * (int64_t)S.slot[l];
+            dg = kr[0];
+            cxm = kr[1];
+            cxp = kr[2];
+            cym = kr[3];
+            cyp = kr[4];
+            czm = kr[5];
+            czp = kr[6];
+        } else {
+            dg = G.ax[0].kb[i] + G.ax[1].kb[j] + G.ax[2].kb[k];
+            cxm = G.ax[0].ka[i];
+            cxp = G.ax[0].kc[i];
+            cym = G.ax[1].ka[j];
+            cyp = G.ax[1].kc[j];
+            czm = G.ax[2].ka[k];
+            czp = G.ax[2].kc[k];
+        }
+        T v = rho[l];
+        if (!FIRST)
+            v -= (cxm * phi[l - 1] + cxp * phi[l + 1]) + (cym * phi[l - sy] + cyp * phi[l + sy]) +
+                 (czm * phi[l - sz] + czp * phi[l + sz]);
+        phi[l] = v / dg;
+    }
+}
+
+template <class T>
+__global__ void k_mask_copy(const uint8_t* __restrict__ type, const T* __restrict__ in, T* __restrict__ out,
+                            int64_t N) {
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < N; l += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t t = type[l];
+        out[l] = (t == CFP_REGULAR || t == CFP_IRREGULAR) ? in[l] : T(0);
+    }
+}
+
+// Eq. q with the weights of solid points set to zero (Q-bar): one thread
+// per interior node, plain 27-term sum.
+__global__ void k_qf(Grid<double> G, const uint8_t* __restrict__ type, const double* __restrict__ f,
+                     double* __restrict__ out) {
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    const int64_t nin = (int64_t)(nx - 2) * (ny - 2) * (nz - 2);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nin;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = 1 + (int)(q % (nx - 2));
+        const int j = 1 + (int)((q / (nx - 2)) % (ny - 2));
+        const int k = 1 + (int)(q / ((int64_t)(nx - 2) * (ny - 2)));
+        const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
+        const uint8_t t = type[l];
+        if (t != CFP_REGULAR && t != CFP_IRREGULAR) {
+            out[l] = 0.0;
+            continue;
+        }
+        const double Lx[3] = {G.ax[0].a[i], 1.0, G.ax[0].c[i]};
+        const double Ly[3] = {G.ax[1].a[j], 1.0, G.ax[1].c[j]};
+        const double Lz[3] = {G.ax[2].a[k], 1.0, G.ax[2].c[k]};
+        double s = 0.0;
+        for (int r = 0; r < 3; ++r)
+            for (int p = 0; p < 3; ++p)
+                for (int o = 0; o < 3; ++o) {
+                    const int64_t c = l + (o - 1) + (p - 1) * sy + (r - 1) * sz;
+                    if (type[c] == CFP_SOLID) continue;
+                    s += Lx[o] * Ly[p] * Lz[r] * f[c];
+                }
+        out[l] = s;
+    }
+}
+
+__global__ void k_rhs_finish(const uint8_t* __restrict__ type, const int32_t* __restrict__ slot,
+                             const int32_t* __restrict__ bib_ptr, const int32_t* __restrict__ bib_idx,
+                             const double* __restrict__ bib_val, const double* __restrict__ qf,
+                             const double* __restrict__ bg, const double* __restrict__ g_ibi,
+                             double* __restrict__ rhs, int64_t N) {
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < N; l += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t t = type[l];
+        double v = 0.0;
+        if (t == CFP_REGULAR || t == CFP_IRREGULAR) {
+            v = qf[l] - bg[l];
+            if (t == CFP_IRREGULAR) {
+                const int s = slot[l];
+                for (int e = bib_ptr[s]; e < bib_ptr[s + 1]; ++e) v -= bib_val[e] * g_ibi[bib_idx[e]];
+            }
+        }
+        rhs[l] = v;
+    }
+}
+
+__global__ void k_boundary_lift(const uint8_t* __restrict__ type, const double* __restrict__ g,
+                                double* __restrict__ gb, int64_t N) {
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < N; l += (int64_t)gridDim.x * blockDim.x)
+        gb[l] = type[l] == CFP_BOUNDARY ? g[l] : 0.0;
+}
+
+__global__ void k_finish_solution(const uint8_t* __restrict__ type, const double* __restrict__ x,
+                                  const double* __restrict__ g, double* __restrict__ u, int64_t N) {
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < N; l += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t t = type[l];
+        u[l] = t == CFP_BOUNDARY ? g[l] : (t == CFP_SOLID ? 0.0 : x[l]);
+    }
+}
+
+unsigned flat_grid(int64_t n) {
+    const int64_t b = (n + 255) / 256;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+dim3 apply_grid(const cfp_ctx* c) {
+    return dim3((unsigned)((c->n[0] - 2 + kApplyTX - 1) / kApplyTX), (unsigned)((c->n[1] - 2 + kApplyTY - 1) / kApplyTY),
+                (unsigned)((c->n[2] - 2 + kApplyKC - 1) / kApplyKC));
+}
+
+}  // namespace
+
+int apply_blocks(cfp_ctx* c) {
+    const dim3 g = apply_grid(c);
+    return (int)(g.x * g.y * g.z);
+}
+
+template <class T>
+void launch_apply(cfp_ctx* c, const T* x, T* y, const T* d0, int dotmode, double* partial, cudaStream_t s,
+                  int* nblocks_out) {
+    const dim3 grid = apply_grid(c);
+    const dim3 block(kApplyTX, kApplyTY);
+    const Grid<T> G = grid_view<T>(c);
+    const Side<T> S = side_view<T>(c);
+    if (dotmode == 0) k_apply<T, 0><<<grid, block, 0, s>>>(G, S, c->type, x, y, d0, partial);
+    else if (dotmode == 1) k_apply<T, 1><<<grid, block, 0, s>>>(G, S, c->type, x, y, d0, partial);
+    else k_apply<T, 2><<<grid, block, 0, s>>>(G, S, c->type, x, y, d0, partial);
+    c->launches += 1;
+    if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+}
+
+template <class T>
+void launch_precond(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s) {
+    const Grid<T> G = grid_view<T>(c);
+    const Side<T> S = side_view<T>(c);
+    c->launches += precond_kernels(sweeps);
+    if (sweeps <= 0) {
+        k_mask_copy<T><<<flat_grid(c->N), 256, 0, s>>>(c->type, rho, phi, c->N);
+        return;
+    }
+    const int64_t half = (int64_t)((c->n[0] - 1) / 2) * (c->n[1] - 2) * (c->n[2] - 2);
+    const unsigned nb = flat_grid(half);
+    for (int sw = 0; sw < sweeps; ++sw) {
+        if (sw == 0) k_rbgs<T, true><<<nb, 256, 0, s>>>(G, S, c->type, rho, phi, 0);
+        else k_rbgs<T, false><<<nb, 256, 0, s>>>(G, S, c->type, rho, phi, 0);
+        k_rbgs<T, false><<<nb, 256, 0, s>>>(G, S, c->type, rho, phi, 1);
+    }
+}
+
+template <class T>
+void launch_rbgs_half(cfp_ctx* c, const T* rho, T* phi, int colour, bool first, cudaStream_t s) {
+    const int64_t half = (int64_t)((c->n[0] - 1) / 2) * (c->n[1] - 2) * (c->n[2] - 2);
+    if (first) k_rbgs<T, true><<<flat_grid(half), 256, 0, s>>>(grid_view<T>(c), side_view<T>(c), c->type, rho, phi, colour);
+    else k_rbgs<T, false><<<flat_grid(half), 256, 0, s>>>(grid_view<T>(c), side_view<T>(c), c->type, rho, phi, colour);
+    c->launches += 1;
+}
+
+template void launch_rbgs_half<double>(cfp_ctx*, const double*, double*, int, bool, cudaStream_t);
+template void launch_rbgs_half<float>(cfp_ctx*, const float*, float*, int, bool, cudaStream_t);
+template void launch_apply<double>(cfp_ctx*, const double*, double*, const double*, int, double*, cudaStream_t,
+                                   int*);
+template void launch_apply<float>(cfp_ctx*, const float*, float*, const float*, int, double*, cudaStream_t, int*);
+template void launch_precond<double>(cfp_ctx*, int, const double*, double*, cudaStream_t);
+template void launch_precond<float>(cfp_ctx*, int, const float*, float*, cudaStream_t);
+
+void launch_qf(cfp_ctx* c, const double* f, double* out, cudaStream_t s) {
+    c->launches += 1;
+    k_qf<<<flat_grid(c->N), 256, 0, s>>>(grid_view<double>(c), c->type, f, out);
+}
+
+void launch_rhs_finish(cfp_ctx* c, const double* qf, const double* bg, const double* g_ibi, double* rhs,
+                       cudaStream_t s) {
+    c->launches += 1;
+    k_rhs_finish<<<flat_grid(c->N), 256, 0, s>>>(c->type, c->slot, c->bib_ptr, c->bib_idx, c->bib_val, qf, bg, g_ibi,
+                                                 rhs, c->N);
+}
+
+void launch_boundary_lift(cfp_ctx* c, const double* g, double* gb, cudaStream_t s) {
+    c->launches += 1;
+    k_boundary_lift<<<flat_grid(c->N), 256, 0, s>>>(c->type, g, gb, c->N);
+}
+
+void launch_finish_solution(cfp_ctx* c, const double* x, const double* g, double* u, cudaStream_t s) {
+    c->launches += 1;
+    k_finish_solution<<<flat_grid(c->N), 256, 0, s>>>(c->type, x, g, u, c->N);
+}
+
+void launch_mask_unknowns(cfp_ctx* c, const double* in, double* out, cudaStream_t s) {
+    c->launches += 1;
+    k_mask_copy<double><<<flat_grid(c->N), 256, 0, s>>>(c->type, in, out, c->N);
+}
+
+}  // namespace cfp

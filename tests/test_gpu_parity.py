@@ -1,0 +1,222 @@
+"""GPU path versus the CPU oracle, through the C ABI.
+
+Bars: classification and IBI order bit-exact; IBI coordinates and the
+operators within rounding (scaled by the sum of absolute terms); FP64
+solutions within 1e-10 relative max-norm; fourth-order convergence; the
+mixed-precision solve reaching the FP64 discretisation error."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import pyoracle as O  # noqa: E402
+from paper_1901_08269_gb300 import cfp  # noqa: E402
+from paper_1901_08269_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def ragged(n=37):
+    # deliberately uneven sizes: several apply tiles plus a ragged tail in x,
+    # y and z chunks
+    return (W.tanh_grid(-1, 1, n, 1.1), W.tanh_grid(-1, 1, n + 12, 0.7), W.uniform_grid(-1, 1, n - 6))
+
+
+CASES = {
+    "c1-17": lambda: W.config1(17),
+    "c2-33": lambda: W.config2(33),
+    "ragged-sphere": lambda: W.Workload("ragged", *ragged(), [W.sphere((0.05, -0.03, 0.02), 0.33)], W._c2_u, W._c2_f),
+    "ragged-torus": lambda: W.Workload("ragged-torus", *ragged(41),
+                                       [W.torus((0.02, 0.01, -0.03), 0.45, 0.16, W.rot_euler(0.1, 0.5, 0.3))],
+                                       W._c3_u, W._c3_f),
+    "c3-bodies-65": lambda: W.Workload("c3b", W.tanh_grid(-1, 1, 65, 1.0), W.tanh_grid(-1, 1, 65, 0.6),
+                                       W.tanh_grid(-1, 1, 65, 0.6), W.config3_bodies(), W._c3_u, W._c3_f),
+    "random-3": lambda: W.random_problem(3, sizes=(33, 49)),
+    "random-8": lambda: W.random_problem(8, sizes=(33, 49)),
+}
+
+
+class Pair:
+    def __init__(self, w):
+        self.w = w
+        self.ctx = cfp.Context(w.x, w.y, w.z, w.bodies, w.fluid_inside)
+        self.type = torch.empty(w.N, dtype=torch.uint8, device="cuda")
+        self.ctx.classify_points(self.type)
+        self.xyz = self.ctx.ibi_points()
+        self.P = O.Problem(w.x, w.y, w.z, w.bodies, w.fluid_inside)
+        self.otype = self.P.classify()
+        self.okey, self.ot, self.oxyz = self.P.ibi()
+        self.P.assemble()
+        self.unk = np.flatnonzero((self.otype == O.REGULAR) | (self.otype == O.IRREGULAR))
+
+    def rand_field(self, seed, zero_off=True):
+        rng = np.random.default_rng(seed)
+        x = rng.standard_normal(self.w.N)
+        if zero_off:
+            m = np.zeros(self.w.N, bool)
+            m[self.unk] = True
+            x[~m] = 0.0
+        else:
+            x[self.otype == O.SOLID] = 0.0
+        return x
+
+
+_pairs = {}
+
+
+def pair(name):
+    if name not in _pairs:
+        _pairs[name] = Pair(CASES[name]())
+    return _pairs[name]
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_classification_bit_exact(name):
+    p = pair(name)
+    np.testing.assert_array_equal(p.type.cpu().numpy(), p.otype)
+    assert p.ctx.n_irregular == p.P.n_irr and p.ctx.n_ibi == p.P.n_ibi
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_ibi_points(name):
+    p = pair(name)
+    g = p.xyz.cpu().numpy()
+    assert g.shape == p.oxyz.shape
+    # same bisection on bit-identical level-set values: equal coordinates
+    np.testing.assert_array_equal(g, p.oxyz)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("zero_off", [True, False])
+def test_apply_parity(name, zero_off):
+    p = pair(name)
+    x = p.rand_field(1, zero_off)
+    y = torch.zeros(p.w.N, dtype=torch.float64, device="cuda")
+    p.ctx.apply(dev(x), y)
+    yo = p.P.apply_B(x)
+    scale = p.P.apply_B(x, absval=True)
+    err = np.abs(y.cpu().numpy() - yo)
+    assert np.all(err <= 1e-13 * scale + 1e-300), np.max(err / (scale + 1e-300))
+    nonunk = np.ones(p.w.N, bool)
+    nonunk[p.unk] = False
+    assert np.all(y.cpu().numpy()[nonunk] == 0.0)
+
+
+@pytest.mark.parametrize("name", ["c2-33", "ragged-torus", "random-3"])
+@pytest.mark.parametrize("sweeps", [0, 1, 8])
+def test_preconditioner_parity(name, sweeps):
+    p = pair(name)
+    rho = p.rand_field(2)
+    phi = torch.zeros(p.w.N, dtype=torch.float64, device="cuda")
+    p.ctx.precondition(dev(rho), phi, sweeps)
+    po = p.P.precond(rho, sweeps)
+    err = np.max(np.abs(phi.cpu().numpy() - po))
+    assert err <= 1e-12 * np.max(np.abs(po)), err
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_parity(name):
+    p = pair(name)
+    f, g = p.w.fields()
+    gi = p.w.g_at(p.oxyz)
+    rhs = torch.zeros(p.w.N, dtype=torch.float64, device="cuda")
+    p.ctx.assemble_rhs(dev(f), dev(g), dev(gi), rhs)
+    ro = p.P.rhs(f, g, gi)
+    X, Y, Z = p.w.mesh()
+    u = p.w.u(X, Y, Z, np).reshape(-1)
+    u[p.otype == O.SOLID] = 0.0
+    scale = p.P.apply_B(u, absval=True) + np.abs(ro) + 1.0
+    err = np.abs(rhs.cpu().numpy() - ro)
+    assert np.all(err <= 1e-12 * scale), np.max(err / scale)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("graph", [1, 0])
+def test_solve_parity_fp64(name, graph):
+    p = pair(name)
+    f, g = p.w.fields()
+    gi = p.w.g_at(p.oxyz)
+    tol = 1e-13
+    uo, st, it, rel = p.P.solve(f, g, gi, tol=tol)
+    assert st == 0
+    u = torch.zeros(p.w.N, dtype=torch.float64, device="cuda")
+    info = p.ctx.solve(dev(f), dev(g), dev(gi), u, tol=tol, use_graph=graph)
+    assert info.status == 0 and info.rel_residual <= tol
+    ug = u.cpu().numpy()
+    assert np.max(np.abs(ug - uo)) <= 1e-10 * np.max(np.abs(uo))
+    assert np.all(ug[p.otype == O.SOLID] == 0.0)
+    bd = p.otype == O.BOUNDARY
+    np.testing.assert_array_equal(ug[bd], g[bd])
+    assert abs(info.iterations - it) <= max(3, it // 5)
+
+
+def test_solve_fourth_order_gpu():
+    errs, ns = [], (33, 65, 129)
+    for n in ns:
+        w = W.config2(n)
+        ctx = cfp.Context(w.x, w.y, w.z, w.bodies)
+        t = torch.empty(w.N, dtype=torch.uint8, device="cuda")
+        ctx.classify_points(t)
+        xyz = ctx.ibi_points()
+        f, g = w.fields(torch, "cuda")
+        u = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+        ctx.solve(f, g, w.g_at(xyz, torch), u, tol=1e-13)
+        X, Y, Z = w.mesh(torch, "cuda")
+        ue = w.u(X, Y, Z, torch).reshape(-1)
+        m = t != cfp.SOLID
+        errs.append(float((u - ue).abs()[m].max()))
+    p = [np.log(errs[q] / errs[q + 1]) / np.log((ns[q + 1] - 1) / (ns[q] - 1)) for q in range(2)]
+    assert 3.7 < p[0] < 4.3 and 3.8 < p[1] < 4.2, (errs, p)
+
+
+@pytest.mark.parametrize("name", ["c2-33", "ragged-torus", "c3-bodies-65"])
+def test_mixed_precision_reaches_fp64_error(name):
+    p = pair(name)
+    f, g = p.w.fields()
+    gi = p.w.g_at(p.oxyz)
+    X, Y, Z = p.w.mesh()
+    ue = p.w.u(X, Y, Z, np).reshape(-1)
+    m = p.otype != O.SOLID
+    u64 = torch.zeros(p.w.N, dtype=torch.float64, device="cuda")
+    p.ctx.solve(dev(f), dev(g), dev(gi), u64, tol=1e-12)
+    u32 = torch.zeros(p.w.N, dtype=torch.float64, device="cuda")
+    info = p.ctx.solve(dev(f), dev(g), dev(gi), u32, tol=1e-12, precision=cfp.PREC_MIXED)
+    assert info.status == 0 and info.refinements >= 1
+    e64 = np.max(np.abs(u64.cpu().numpy() - ue)[m])
+    e32 = np.max(np.abs(u32.cpu().numpy() - ue)[m])
+    assert e32 <= 1.02 * e64 + 1e-14, (e32, e64)
+    assert np.max(np.abs(u32.cpu().numpy() - u64.cpu().numpy())) <= 1e-9 * np.max(np.abs(ue))
+
+
+def test_errors_are_reported_not_raised_on_device():
+    w = W.config1(17)
+    ctx = cfp.Context(w.x, w.y, w.z, [W.sphere((0.5, 0.5, 0.97), 0.2)])  # body through the box
+    with pytest.raises(cfp.CfpError) as e:
+        ctx.classify_points()
+    assert e.value.status == cfp.EGEOM
+    ctx2 = cfp.Context(w.x, w.y, w.z)
+    ctx2.classify_points()
+    f, g = w.fields(torch, "cuda")
+    f[100] = float("nan")
+    u = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+    info = ctx2.solve(f, g, None, u, tol=1e-12, check=False)
+    assert info.status == cfp.ENAN
+    wq = W.quartic_workload(w.x, w.y, w.z, seed=2)
+    f2, g2 = wq.fields(torch, "cuda")
+    u.zero_()
+    info = ctx2.solve(f2, g2, None, u, tol=1e-15, maxit=3, max_restarts=0, check=False)
+    assert info.status == cfp.ENOCONV and info.iterations == 3
+    u.zero_()
+    info = ctx2.solve(f2, g2, None, u, tol=1e-12)
+    assert info.status == 0
