@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Benchmark of the compact-stencil immersed-body Poisson solve on GB300.
+
+Workload: the 513^3 stretched grid of [-1,1]^3 (tanh factors 2.0, 1.2, 1.2)
+with an ellipsoid (0.4, 0.25, 0.2) rotated 30 degrees about z and a torus
+(R 0.3, r 0.1) at (0.5, 0.4, -0.3); u = sin(2x) cosh(y) exp(-z^2).  One step
+= the whole hot path: grid metrics, point classification, IBI location,
+modified stencils, right-hand side, preconditioned BiCGSTAB to the
+tolerance (mixed FP32/FP64 by default).  Inputs (f, g on the nodes, g at the
+IBI points) are resident in HBM before the timed region; every field is
+1.08 GB, far above the 129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead (bounded sample, extrapolated), see `reference_arm`.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s/solve at 513³ to equal max-norm error, plain FP64 vs mixed/learned; HBM GB/s"
+UNIT = "s/solve"
+FALLBACK_HBM_GBS = 6800.0
+# FP64 iterations of the 513^3 workload, measured by the GPU path (used by
+# the reference arm, which cannot run the 513^3 solve itself)
+FP64_ITERS_513 = 400
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=513)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--sweeps", type=int, default=8)
+    ap.add_argument("--no-fp64-check", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--oracle-n", type=int, default=129)
+    ap.add_argument("--oracle-iters", type=int, default=10)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return d, "measured"
+        except Exception:
+            pass
+    return {}, "fallback"
+
+
+def hbm_peak():
+    d, src = peaks()
+    for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+        if k in d:
+            v = d[k]
+            if isinstance(v, dict):
+                v = v.get("value", v.get("gbs"))
+            try:
+                return float(v), "measured"
+            except (TypeError, ValueError):
+                pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------- CPU baseline
+def oracle_sample(n_sample, iters, n_full, iters_full):
+    """Time the CPU oracle on a bounded sample of the workload: the same
+    geometry and solution on an n_sample^3 grid, set-up (classification, IBI,
+    explicit CSR assembly, right-hand side) plus `iters` BiCGSTAB iterations.
+    Extrapolated to an n_full^3 solve of `iters_full` iterations by the node
+    count ratio."""
+    import numpy as np
+
+    from oracle import pyoracle as O
+    from paper_1901_08269_gb300 import workloads as W
+    w = W.config3(n_sample)
+    f, g = w.fields()
+    t0 = time.perf_counter()
+    P = O.Problem(w.x, w.y, w.z, w.bodies)
+    P.classify()
+    key, tt, xyz = P.ibi()
+    P.assemble()
+    rhs = P.rhs(f, g, w.g_at(xyz))
+    t1 = time.perf_counter()
+    x, st, it, rel = P.bicgstab(rhs, tol=1e-30, maxit=iters, sweeps=8)
+    t2 = time.perf_counter()
+    ratio = (n_full / n_sample) ** 3
+    t_iter = (t2 - t1) / max(it, 1)
+    est = ((t1 - t0) + t_iter * iters_full) * ratio
+    return {"est_s_per_solve": est, "setup_s": t1 - t0, "iter_s": t_iter, "iters": it, "cores": O.threads(),
+            "wall_s": t2 - t0}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    vals = []
+    for s in range(args.warmup + args.steps):
+        r = oracle_sample(args.oracle_n, args.oracle_iters, args.n, FP64_ITERS_513)
+        if s >= args.warmup:
+            vals.append(r["est_s_per_solve"])
+    v = statistics.mean(vals)
+    sample = ("oracle (plain C, FP64, CSR) on config-3 geometry at %d^3: set-up + %d BiCGSTAB iterations, "
+              "extrapolated to a %d^3 solve of %d iterations by the node-count ratio" %
+              (args.oracle_n, r["iters"], args.n, FP64_ITERS_513))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "config3-%d^3-ellipsoid+torus" % args.n, "n": args.n, "precision": "fp64"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_1901_08269_gb300 import cfp
+    from paper_1901_08269_gb300 import workloads as W
+
+    w = W.config3(args.n)
+    stream = torch.cuda.current_stream()
+    ctx = cfp.Context(w.x, w.y, w.z, w.bodies, stream=stream)
+    t_type = torch.empty(w.N, dtype=torch.uint8, device="cuda")
+    ctx.classify_points(t_type)
+    xyz = ctx.ibi_points()
+    f, g = w.fields(torch, "cuda")
+    gi = w.g_at(xyz, torch).contiguous()
+    u = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+    prec = cfp.PREC_MIXED if args.precision == "mixed" else cfp.PREC_FP64
+    opts = cfp.default_opts(precision=prec, sweeps=args.sweeps, inner_tol=args.inner_tol)
+
+    def step():
+        ctx.classify_points()
+        u.zero_()
+        return ctx.solve(f, g, gi, u, tol=args.tol, opts=opts)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    infos = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = ctx.launch_count() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = ms / 1000.0 / (args.steps * world)
+
+    X, Y, Z = w.mesh(torch, "cuda")
+    ue = w.u(X, Y, Z, torch).reshape(-1)
+    fluid = t_type != cfp.SOLID
+    err = float((u - ue).abs()[fluid].max())
+    info = infos[-1]
+    result = {"max_err": err, "iterations": info.iterations, "refinements": info.refinements,
+              "rel_residual": info.rel_residual, "n_irregular": info.n_irregular, "n_ibi": info.n_ibi,
+              "n_degenerate": info.n_degenerate}
+    del X, Y, Z
+
+    fp64 = None
+    if not args.no_fp64_check:
+        u64 = torch.zeros_like(u)
+        ctx.classify_points()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        i64 = ctx.solve(f, g, gi, u64, tol=args.tol, precision=cfp.PREC_FP64, sweeps=args.sweeps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e64 = float((u64 - ue).abs()[fluid].max())
+        fp64 = {"s_per_solve": a.elapsed_time(b) / 1000.0, "max_err": e64, "iterations": i64.iterations,
+                "err_ratio_vs_fp64": err / e64 if e64 > 0 else None, "equal_error": err <= 1.02 * e64,
+                "max_diff_vs_fp64": float((u - u64).abs().max())}
+        del u64
+
+    # roofline of the dominant kernel: a red-black half-sweep of the
+    # preconditioner, in the precision of the inner solve
+    kprec = prec
+    kern = {}
+    for name, kid in (("rbgs_half", cfp.KERNEL_RBGS), ("apply", cfp.KERNEL_APPLY), ("update", cfp.KERNEL_UPDATE)):
+        kms, kbytes = ctx.time_kernel(kid, kprec, reps=20)
+        kern[name] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6}
+    peak, psrc = hbm_peak()
+    dom = kern["rbgs_half"]
+    roofline = {"bound": "hbm", "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": dom["gbs"] / peak, "traffic": None, "kernel": "k_rbgs<%s> half-sweep" %
+                ("float" if kprec == cfp.PREC_MIXED else "double"), "peak_source": psrc}
+    tr = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr):
+        try:
+            d = json.load(open(tr)).get(roofline["kernel"])
+            if d and d.get("stencil_sha") == _src_hash():
+                roofline["traffic"] = d["bytes_per_interior_node"] * (args.n - 2) ** 3
+        except Exception:
+            pass
+
+    e2e = None
+    if not args.no_e2e:
+        hf = f.cpu().pin_memory()
+        hg = g.cpu().pin_memory()
+        hgi = gi.cpu().pin_memory()
+        hu = torch.zeros(w.N, dtype=torch.float64).pin_memory()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        ctx.classify_points()
+        hu.zero_()
+        ctx.solve_host(hf, hg, hgi, hu, tol=args.tol, opts=opts)
+        b.record(stream)
+        torch.cuda.synchronize()
+        es = a.elapsed_time(b) / 1000.0
+        h2d = (hf.numel() + hg.numel() + hu.numel() + hgi.numel()) * 8
+        e2e = {"value": es / world, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": hu.numel() * 8}
+        del hf, hg, hgi, hu
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        iters_full = fp64["iterations"] if fp64 else FP64_ITERS_513
+        r = oracle_sample(args.oracle_n, args.oracle_iters, args.n, iters_full)
+        cpu = {"value": r["est_s_per_solve"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+               "sample": "oracle (plain C, FP64, CSR, OpenMP) on the same geometry at %d^3: set-up + %d "
+                         "BiCGSTAB iterations (%.1f s wall), extrapolated to a %d^3 FP64 solve of %d iterations "
+                         "by the node-count ratio" % (args.oracle_n, r["iters"], r["wall_s"], args.n, iters_full)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if prec == cfp.PREC_MIXED else "f64", "data": "synthetic",
+                "config": {"workload": "config3-%d^3-ellipsoid+torus" % args.n, "n": args.n,
+                           "grid": "tanh (2.0, 1.2, 1.2) on [-1,1]^3", "precision": args.precision,
+                           "tol": args.tol, "inner_tol": args.inner_tol, "sweeps": args.sweeps,
+                           "l2": "no flush: every field (1.08 GB at 513^3) exceeds the 129 MB L2",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "result": result, "fp64": fp64, "kernels": kern, "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _src_hash():
+    import hashlib
+    p = os.path.join(ROOT, "paper_1901_08269_gb300", "csrc", "cfp_stencil.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

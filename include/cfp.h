@@ -208,6 +208,10 @@ cfp_status cfp_solve_host(cfp_ctx* ctx, const double* f_host,
                           double* u_host, double tol, const cfp_opts* opts,
                           cfp_info* info);
 
+/* Kernels this context has launched since it was created (graph bodies
+ * counted once per executed iteration).  0 for NULL. */
+int64_t cfp_launch_count(const cfp_ctx* ctx);
+
 enum { CFP_KERNEL_APPLY = 0,   /* B x with the fused (r_hat0, v) dot, as in
                                   Algorithm 1 line 5                         */
        CFP_KERNEL_RBGS = 1,    /* one red-black Gauss-Seidel half-sweep      */

@@ -49,7 +49,7 @@ _D = C.POINTER(C.c_double)
 
 EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_destroy", "cfp_classify_points",
            "cfp_ibi_points", "cfp_assemble_rhs", "cfp_apply", "cfp_precondition", "cfp_solve", "cfp_solve_host",
-           "cfp_time_kernel"]
+           "cfp_time_kernel", "cfp_launch_count"]
 KERNEL_APPLY, KERNEL_RBGS, KERNEL_UPDATE = 0, 1, 2
 
 
@@ -78,8 +78,10 @@ def lib(build_if_missing=True):
         L.cfp_solve.argtypes = [_P, _P, _P, _P, _P, C.c_double, C.POINTER(Opts), C.POINTER(Info)]
         L.cfp_solve_host.argtypes = [_P, _P, _P, _P, _P, C.c_double, C.POINTER(Opts), C.POINTER(Info)]
         L.cfp_time_kernel.argtypes = [_P, C.c_int, C.c_int, C.c_int, _D, _D]
+        L.cfp_launch_count.argtypes = [_P]
+        L.cfp_launch_count.restype = C.c_int64
         for name in EXPORTS[2:]:
-            if name != "cfp_ctx_destroy":
+            if name not in ("cfp_ctx_destroy", "cfp_launch_count"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -210,6 +212,9 @@ class Context:
         if check:
             _check(st, "cfp_solve")
         return info
+
+    def launch_count(self):
+        return lib().cfp_launch_count(self._h)
 
     def time_kernel(self, kernel, precision=PREC_FP64, reps=20):
         """Mean device time (ms) of one launch and its algorithmic bytes."""

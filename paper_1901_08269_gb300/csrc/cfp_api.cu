@@ -29,31 +29,6 @@ cfp_status solve_impl(cfp_ctx* c, const double* f, const double* g, const double
 
 namespace {
 
-// Eq. app_xxx (compact, b = 1) and Eq. 2ndorder_coef at interior nodes;
-// layout per axis: a, c, ar, br, cr, ka, kb, kc (n each), zero at the ends.
-__global__ void k_metrics(const double* __restrict__ x, int n, double* __restrict__ out, float* __restrict__ out32) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (i > 0 && i < n - 1) {
-            const double f = x[i + 1] - x[i];
-            const double b = x[i] - x[i - 1];
-            const double D = f * f * f + 4.0 * f * f * b + 4.0 * f * b * b + b * b * b;
-            v[0] = f * (b * b + b * f - f * f) / D;
-            v[1] = b * (f * f + b * f - b * b) / D;
-            v[2] = 12.0 * f / D;
-            v[3] = -12.0 / (f * f + 3.0 * f * b + b * b);
-            v[4] = 12.0 * b / D;
-            v[5] = 2.0 / (b * (f + b));
-            v[6] = -2.0 / (b * f);
-            v[7] = 2.0 / (f * (f + b));
-        }
-        for (int q = 0; q < 8; ++q) {
-            out[(int64_t)q * n + i] = v[q];
-            out32[(int64_t)q * n + i] = (float)v[q];
-        }
-    }
-}
-
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -145,13 +120,10 @@ cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny, cons
     chk(cudaMalloc(&c->kst, sizeof(KState) * 2), "cudaMalloc");
     chk(cudaMallocHost(&c->hkst, sizeof(KState) * 2), "cudaMallocHost");
     if (st == CFP_OK) {
-        int64_t off = 0;
-        for (int d = 0; d < 3; ++d) {
+        for (int d = 0; d < 3; ++d)
             chk(cudaMemcpyAsync(c->dX[d], src[d], sizeof(double) * n[d], cudaMemcpyHostToDevice, c->stream),
                 "cudaMemcpyAsync");
-            k_metrics<<<(n[d] + 255) / 256, 256, 0, c->stream>>>(c->dX[d], n[d], c->dcoef64 + off, c->dcoef32 + off);
-            off += 8 * (int64_t)n[d];
-        }
+        launch_metrics(c);
         if (nbodies)
             chk(cudaMemcpyAsync(c->dbodies, bodies, sizeof(cfp_body) * nbodies, cudaMemcpyHostToDevice, c->stream),
                 "cudaMemcpyAsync");
@@ -286,6 +258,8 @@ cfp_status cfp_solve_host(cfp_ctx* c, const double* f, const double* g, const do
     if (st != CFP_OK) g_last_error = msg;
     return st;
 }
+
+int64_t cfp_launch_count(const cfp_ctx* c) { return c ? c->launches : 0; }
 
 cfp_status cfp_time_kernel(cfp_ctx* c, int kernel, int precision, int reps, double* ms, double* bytes) {
     CFP_TRY(need_classified(c));

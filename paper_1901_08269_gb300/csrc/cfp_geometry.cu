@@ -227,6 +227,7 @@ cfp_status scan(cfp_ctx* c, F f, S sink, int64_t n, long long* dtotal, long long
         k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(f, n, c->scan_bsum);
         k_scan_blocks<<<1, kScanThreads, 0, c->stream>>>(c->scan_bsum, (int)nb, dtotal);
         k_scan_scatter<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(f, sink, n, c->scan_bsum);
+        c->launches += 3;
     } else {
         CFP_CUDA(cudaMemsetAsync(dtotal, 0, sizeof(long long), c->stream));
     }
@@ -681,7 +682,9 @@ cfp_status classify(cfp_ctx* c) {
     g.nb = (int)c->bodies.size();
     g.inside = c->fluid_inside;
 
+    launch_metrics(c);  // the 1D grid metrics are rebuilt with every classification
     k_classify_solid<<<grid_for(N, 256), 256, 0, c->stream>>>(g, c->type, N);
+    c->launches += 2;
     k_classify_irregular<<<grid_for((int64_t)(nx - 2) * (ny - 2) * (nz - 2), 256), 256, 0, c->stream>>>(
         c->type, nx, ny, nz);
     CFP_CUDA(cudaGetLastError());
@@ -699,6 +702,7 @@ cfp_status classify(cfp_ctx* c) {
         }
         k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(FlagIrregular{c->type}, N, c->scan_bsum);
         k_scan_blocks<<<1, kScanThreads, 0, c->stream>>>(c->scan_bsum, (int)nb, c->dtotal);
+        c->launches += 3;  // with the scatter below
         CFP_CUDA(cudaGetLastError());
         CFP_CUDA(cudaMemcpyAsync(&nirr, c->dtotal, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
         CFP_CUDA(cudaStreamSynchronize(c->stream));
@@ -725,11 +729,13 @@ cfp_status classify(cfp_ctx* c) {
     CFP_CUDA(cudaMalloc(&cnt2, sizeof(int) * (nirr + 1)));
     CFP_CUDA(cudaMalloc(&c->ibi_off, sizeof(int32_t) * (nirr + 1)));
     if (nirr) k_ibi_count<<<grid_for(nirr, 256), 256, 0, c->stream>>>(ia, cnt);
+    if (nirr) c->launches += 1;
     CFP_TRY(scan(c, FetchInt{cnt}, SinkOffsets{c->ibi_off}, nirr, c->dtotal, &h));
     c->n_ibi = h;
     CFP_CUDA(cudaMemcpyAsync(c->ibi_off + nirr, c->dtotal, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
     CFP_CUDA(cudaMalloc(&c->ibi_xyz, sizeof(double) * 3 * std::max<int64_t>(c->n_ibi, 1)));
     if (nirr) k_ibi_roots<<<grid_for(nirr, 128), 128, 0, c->stream>>>(ia, g, c->ibi_off, c->ibi_xyz);
+    if (nirr) c->launches += 1;
     CFP_CUDA(cudaGetLastError());
 
     // side list: count, scan, fill
@@ -748,6 +754,7 @@ cfp_status classify(cfp_ctx* c) {
     if (nirr)
         k_side<0><<<grid_for(nirr, 64), 64, 0, c->stream>>>(S, cnt, cnt2, nullptr, nullptr, nullptr, nullptr,
                                                            nullptr, nullptr, nullptr, ndeg, c->derr);
+    if (nirr) c->launches += 1;
     CFP_CUDA(cudaGetLastError());
     DevError he;
     long long hdeg = 0;
@@ -790,6 +797,7 @@ cfp_status classify(cfp_ctx* c) {
     if (c->n_corr)
         k_to_float<<<grid_for(c->n_corr, 256), 256, 0, c->stream>>>(c->corr_val, c->corr_val32, c->n_corr);
     if (nirr) k_to_float<<<grid_for(7 * nirr, 256), 256, 0, c->stream>>>(c->krow, c->krow32, 7 * nirr);
+    c->launches += (nirr ? 2 : 0) + (c->n_corr ? 1 : 0);
     CFP_CUDA(cudaGetLastError());
     CFP_CUDA(cudaStreamSynchronize(c->stream));
     cudaFree(cnt);

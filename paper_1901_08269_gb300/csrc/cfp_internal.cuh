@@ -194,6 +194,7 @@ void launch_boundary_lift(cfp_ctx* c, const double* g, double* gb, cudaStream_t 
 void launch_finish_solution(cfp_ctx* c, const double* x, const double* g, double* u, cudaStream_t s);
 void launch_mask_unknowns(cfp_ctx* c, const double* in, double* out, cudaStream_t s);
 int apply_blocks(cfp_ctx* c);
+void launch_metrics(cfp_ctx* c);  // Eq. app_xxx and Eq. 2ndorder_coef per axis
 
 // Krylov (cfp_krylov.cu)
 cfp_status ensure_work(cfp_ctx* c, bool need32);

@@ -466,7 +466,7 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
     cfp_default_opts(&opts);
     if (o) opts = *o;
     if (!(tol > 0.0) || opts.maxit < 1 || opts.sweeps < 0) return fail(CFP_EINVAL, "bad tol, maxit or sweeps");
-    c->launches = 0;
+    const int64_t launches0 = c->launches;
     if (!c->classified) CFP_TRY(classify(c));
     const bool mixed = opts.precision == CFP_PREC_MIXED;
     CFP_TRY(ensure_work(c, mixed));
@@ -557,7 +557,7 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
         info->ms_setup = std::chrono::duration<double, std::milli>(t1 - t0).count();
         info->ms_rhs = std::chrono::duration<double, std::milli>(t2 - t1).count();
         info->ms_solve = std::chrono::duration<double, std::milli>(t3 - t2).count();
-        info->launches = c->launches;
+        info->launches = c->launches - launches0;
     }
     if (status != CFP_OK)
         return fail(status, status == CFP_ENAN ? "non-finite value in the solve"

@@ -298,6 +298,31 @@ __global__ void k_finish_solution(const uint8_t* __restrict__ type, const double
     }
 }
 
+// Eq. app_xxx (compact, b = 1) and Eq. 2ndorder_coef at interior nodes;
+// layout per axis: a, c, ar, br, cr, ka, kb, kc (n each), zero at the ends.
+__global__ void k_metrics(const double* __restrict__ x, int n, double* __restrict__ out, float* __restrict__ out32) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (i > 0 && i < n - 1) {
+            const double f = x[i + 1] - x[i];
+            const double b = x[i] - x[i - 1];
+            const double D = f * f * f + 4.0 * f * f * b + 4.0 * f * b * b + b * b * b;
+            v[0] = f * (b * b + b * f - f * f) / D;
+            v[1] = b * (f * f + b * f - b * b) / D;
+            v[2] = 12.0 * f / D;
+            v[3] = -12.0 / (f * f + 3.0 * f * b + b * b);
+            v[4] = 12.0 * b / D;
+            v[5] = 2.0 / (b * (f + b));
+            v[6] = -2.0 / (b * f);
+            v[7] = 2.0 / (f * (f + b));
+        }
+        for (int q = 0; q < 8; ++q) {
+            out[(int64_t)q * n + i] = v[q];
+            out32[(int64_t)q * n + i] = (float)v[q];
+        }
+    }
+}
+
 unsigned flat_grid(int64_t n) {
     const int64_t b = (n + 255) / 256;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
@@ -309,6 +334,16 @@ dim3 apply_grid(const cfp_ctx* c) {
 }
 
 }  // namespace
+
+void launch_metrics(cfp_ctx* c) {
+    int64_t off = 0;
+    for (int d = 0; d < 3; ++d) {
+        const int n = c->n[d];
+        k_metrics<<<(n + 255) / 256, 256, 0, c->stream>>>(c->dX[d], n, c->dcoef64 + off, c->dcoef32 + off);
+        off += 8 * (int64_t)n;
+    }
+    c->launches += 3;
+}
 
 int apply_blocks(cfp_ctx* c) {
     const dim3 g = apply_grid(c);
