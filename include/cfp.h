@@ -208,6 +208,26 @@ cfp_status cfp_solve_host(cfp_ctx* ctx, const double* f_host,
                           double* u_host, double tol, const cfp_opts* opts,
                           cfp_info* info);
 
+/*
+ * cfp_assemble_rhs without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a library
+ * call cudaMalloc -- for instance applications whose device memory belongs to
+ * a pooling allocator (an allocation outside the pool may fail and it
+ * synchronises the device) or loops with a fixed memory or latency budget.
+ * cfp_assemble_rhs allocates the solver work space on first use; this
+ * variant keeps its one scratch field in a static device array of 2^22
+ * doubles (32 MiB) that every GPU loading the library holds until exit.
+ *   Same arguments, output and errors as cfp_assemble_rhs, plus CFP_EINVAL
+ *   when the grid has more than 2^22 = 4,194,304 nodes.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (two streams or threads at once) race.
+ */
+cfp_status cfp_assemble_rhs_noalloc(cfp_ctx* ctx, const double* f_dev,
+                                    const double* g_nodes_dev,
+                                    const double* g_ibi_dev, double* rhs_dev);
+
 /* Kernels this context has launched since it was created (graph bodies
  * counted once per executed iteration).  0 for NULL. */
 int64_t cfp_launch_count(const cfp_ctx* ctx);

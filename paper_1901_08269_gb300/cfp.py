@@ -49,7 +49,7 @@ _D = C.POINTER(C.c_double)
 
 EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_destroy", "cfp_classify_points",
            "cfp_ibi_points", "cfp_assemble_rhs", "cfp_apply", "cfp_precondition", "cfp_solve", "cfp_solve_host",
-           "cfp_time_kernel", "cfp_launch_count"]
+           "cfp_time_kernel", "cfp_launch_count", "cfp_assemble_rhs_noalloc"]
 KERNEL_APPLY, KERNEL_RBGS, KERNEL_UPDATE = 0, 1, 2
 
 
@@ -78,6 +78,7 @@ def lib(build_if_missing=True):
         L.cfp_solve.argtypes = [_P, _P, _P, _P, _P, C.c_double, C.POINTER(Opts), C.POINTER(Info)]
         L.cfp_solve_host.argtypes = [_P, _P, _P, _P, _P, C.c_double, C.POINTER(Opts), C.POINTER(Info)]
         L.cfp_time_kernel.argtypes = [_P, C.c_int, C.c_int, C.c_int, _D, _D]
+        L.cfp_assemble_rhs_noalloc.argtypes = [_P, _P, _P, _P, _P]
         L.cfp_launch_count.argtypes = [_P]
         L.cfp_launch_count.restype = C.c_int64
         for name in EXPORTS[2:]:
@@ -192,6 +193,14 @@ class Context:
         _check(lib().cfp_assemble_rhs(self._h, self._field(f, "f"), self._field(g_nodes, "g_nodes"),
                                       _ptr(g_ibi) if g_ibi is not None and g_ibi.numel() else None,
                                       self._field(rhs, "rhs")), "cfp_assemble_rhs")
+        return rhs
+
+    def assemble_rhs_noalloc(self, f, g_nodes, g_ibi, rhs):
+        """cfp_assemble_rhs_noalloc: the right-hand side without any device
+        allocation (grids of at most 2^22 nodes; see include/cfp.h)."""
+        _check(lib().cfp_assemble_rhs_noalloc(self._h, self._field(f, "f"), self._field(g_nodes, "g_nodes"),
+                                              _ptr(g_ibi) if g_ibi is not None and g_ibi.numel() else None,
+                                              self._field(rhs, "rhs")), "cfp_assemble_rhs_noalloc")
         return rhs
 
     def apply(self, x, y):
