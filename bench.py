@@ -42,9 +42,11 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=513)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--tol", type=float, default=1e-12)
-    ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--tol", type=float, default=1e-15)
+    ap.add_argument("--inner-tol", type=float, default=1e-3)
     ap.add_argument("--sweeps", type=int, default=8)
+    ap.add_argument("--precond", default="mg", choices=["mg", "rbgs"])
+    ap.add_argument("--mg-smooth", type=int, default=2)
     ap.add_argument("--no-fp64-check", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -212,7 +214,9 @@ def main():
     gi = w.g_at(xyz, torch).contiguous()
     u = torch.zeros(w.N, dtype=torch.float64, device="cuda")
     prec = cfp.PREC_MIXED if args.precision == "mixed" else cfp.PREC_FP64
-    opts = cfp.default_opts(precision=prec, sweeps=args.sweeps, inner_tol=args.inner_tol)
+    pc = cfp.PRECOND_MG if args.precond == "mg" else cfp.PRECOND_RBGS
+    opts = cfp.default_opts(precision=prec, sweeps=args.sweeps, inner_tol=args.inner_tol, precond=pc,
+                            mg_smooth=args.mg_smooth)
 
     def step():
         ctx.classify_points()
@@ -262,7 +266,8 @@ def main():
         ctx.classify_points()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        i64 = ctx.solve(f, g, gi, u64, tol=args.tol, precision=cfp.PREC_FP64, sweeps=args.sweeps)
+        i64 = ctx.solve(f, g, gi, u64, tol=args.tol, precision=cfp.PREC_FP64, sweeps=args.sweeps, precond=pc,
+                        mg_smooth=args.mg_smooth)
         b.record(stream)
         torch.cuda.synchronize()
         e64 = float((u64 - ue).abs()[fluid].max())
@@ -328,6 +333,7 @@ def main():
                 "config": {"workload": "config3-%d^3-ellipsoid+torus" % args.n, "n": args.n,
                            "grid": "tanh (2.0, 1.2, 1.2) on [-1,1]^3", "precision": args.precision,
                            "tol": args.tol, "inner_tol": args.inner_tol, "sweeps": args.sweeps,
+                           "precond": args.precond, "mg_smooth": args.mg_smooth,
                            "l2": "no flush: every field (1.08 GB at 513^3) exceeds the 129 MB L2",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "result": result, "fp64": fp64, "kernels": kern, "roofline": roofline, "cpu_baseline": cpu,

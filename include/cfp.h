@@ -59,6 +59,14 @@ enum { CFP_PREC_FP64 = 0,   /* the whole solve in FP64                       */
                                refinement; residuals, the irregular rows of
                                the residual and the right-hand side in FP64 */ };
 
+enum { CFP_PRECOND_RBGS = 0, /* `sweeps` red-black Gauss-Seidel sweeps on K from
+                                zero (the paper's fixed count of inner
+                                iterations, Sec. 3.3)                         */
+       CFP_PRECOND_MG = 1    /* one multigrid V-cycle on K from zero: red-black
+                                smoothing (mg_smooth sweeps before and after),
+                                rediscretised coarse levels; quality
+                                independent of the grid size                  */ };
+
 typedef struct {
     int precision;     /* CFP_PREC_FP64 (default) or CFP_PREC_MIXED            */
     int sweeps;        /* red-black Gauss-Seidel sweeps of the preconditioner
@@ -71,6 +79,9 @@ typedef struct {
     int max_refine;    /* CFP_PREC_MIXED: cap on refinement steps (default 40) */
     int use_graph;     /* 1 (default): the iteration runs as one CUDA graph
                           with a device-side while loop; 0: plain launches   */
+    int precond;       /* CFP_PRECOND_RBGS (default) or CFP_PRECOND_MG        */
+    int mg_smooth;     /* CFP_PRECOND_MG: sweeps before and after the coarse
+                          correction on each level (default 2)               */
 } cfp_opts;
 
 typedef struct {
@@ -182,6 +193,14 @@ cfp_status cfp_precondition(cfp_ctx* ctx, int sweeps, const double* rho_dev,
                             double* phi_dev);
 
 /*
+ * phi = P(rho) with the preconditioner chosen in opts (precond, sweeps,
+ * mg_smooth; NULL: defaults), as applied inside cfp_solve.  Fields, no
+ * overlap; phi is 0 at box and solid nodes.  Errors as cfp_precondition.
+ */
+cfp_status cfp_precondition_ex(cfp_ctx* ctx, const cfp_opts* opts,
+                               const double* rho_dev, double* phi_dev);
+
+/*
  * Solve Eq. Bu=q with BiCGSTAB (Algorithm 1, Sec. 3.2) right-preconditioned
  * by P (Sec. 3.3), the update being u += alpha*p_hat + omega*s_hat.
  *   f_dev, g_nodes_dev, g_ibi_dev  as for cfp_assemble_rhs
@@ -234,7 +253,8 @@ int64_t cfp_launch_count(const cfp_ctx* ctx);
 
 enum { CFP_KERNEL_APPLY = 0,   /* B x with the fused (r_hat0, v) dot, as in
                                   Algorithm 1 line 5                         */
-       CFP_KERNEL_RBGS = 1,    /* one red-black Gauss-Seidel half-sweep      */
+       CFP_KERNEL_RBGS = 1,    /* one red-black Gauss-Seidel sweep (both
+                                  colours, one fused kernel)                 */
        CFP_KERNEL_UPDATE = 2   /* the fused x/r update with two dots (lines
                                   11-12)                                     */ };
 
@@ -246,9 +266,9 @@ enum { CFP_KERNEL_APPLY = 0,   /* B x with the fused (r_hat0, v) dot, as in
  *   ms_per_launch     host pointer: mean device time of one launch
  *   bytes_per_launch  host pointer or NULL: algorithmic bytes of one launch
  *                     (minimum traffic: per unknown, apply 3 values (x, y
- *                     and the dot operand), half-sweep 1.5 values (the
- *                     other colour of phi, rho and phi of its own colour),
- *                     update 8 values over all nodes)
+ *                     and the dot operand), sweep 2.5 values (rho, the new
+ *                     phi and the black half of the previous phi), update
+ *                     8 values over all nodes)
  * Requires classification.  Synchronises.  Errors: CFP_ESTATE, CFP_EINVAL,
  * CFP_ECUDA.
  */

@@ -14,6 +14,7 @@ OK, EINVAL, ENOMEM, ECUDA, EGEOM, ENOCONV, EBREAKDOWN, ENAN, ESTATE = range(9)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EGEOM", "ENOCONV", "EBREAKDOWN", "ENAN", "ESTATE"]
 BOUNDARY, REGULAR, IRREGULAR, SOLID = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
+PRECOND_RBGS, PRECOND_MG = 0, 1
 KINDS = {"sphere": 0, "ellipsoid": 1, "torus": 2}
 
 
@@ -30,7 +31,8 @@ class Body(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("sweeps", C.c_int), ("maxit", C.c_int), ("max_restarts", C.c_int),
-                ("inner_tol", C.c_double), ("max_refine", C.c_int), ("use_graph", C.c_int)]
+                ("inner_tol", C.c_double), ("max_refine", C.c_int), ("use_graph", C.c_int),
+                ("precond", C.c_int), ("mg_smooth", C.c_int)]
 
 
 class Info(C.Structure):
@@ -49,7 +51,7 @@ _D = C.POINTER(C.c_double)
 
 EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_destroy", "cfp_classify_points",
            "cfp_ibi_points", "cfp_assemble_rhs", "cfp_apply", "cfp_precondition", "cfp_solve", "cfp_solve_host",
-           "cfp_time_kernel", "cfp_launch_count", "cfp_assemble_rhs_noalloc"]
+           "cfp_time_kernel", "cfp_launch_count", "cfp_assemble_rhs_noalloc", "cfp_precondition_ex"]
 KERNEL_APPLY, KERNEL_RBGS, KERNEL_UPDATE = 0, 1, 2
 
 
@@ -79,6 +81,7 @@ def lib(build_if_missing=True):
         L.cfp_solve_host.argtypes = [_P, _P, _P, _P, _P, C.c_double, C.POINTER(Opts), C.POINTER(Info)]
         L.cfp_time_kernel.argtypes = [_P, C.c_int, C.c_int, C.c_int, _D, _D]
         L.cfp_assemble_rhs_noalloc.argtypes = [_P, _P, _P, _P, _P]
+        L.cfp_precondition_ex.argtypes = [_P, C.POINTER(Opts), _P, _P]
         L.cfp_launch_count.argtypes = [_P]
         L.cfp_launch_count.restype = C.c_int64
         for name in EXPORTS[2:]:
@@ -210,6 +213,12 @@ class Context:
     def precondition(self, rho, phi, sweeps=8):
         _check(lib().cfp_precondition(self._h, int(sweeps), self._field(rho, "rho"), self._field(phi, "phi")),
                "cfp_precondition")
+        return phi
+
+    def precondition_ex(self, rho, phi, opts=None, **kw):
+        o = opts if opts is not None else default_opts(**kw)
+        _check(lib().cfp_precondition_ex(self._h, C.byref(o), self._field(rho, "rho"), self._field(phi, "phi")),
+               "cfp_precondition_ex")
         return phi
 
     def solve(self, f, g_nodes, g_ibi, u, tol=1e-12, opts=None, check=True, **kw):

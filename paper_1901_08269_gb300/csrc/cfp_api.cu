@@ -67,6 +67,8 @@ void cfp_default_opts(cfp_opts* o) {
     o->inner_tol = 1e-5;
     o->max_refine = 40;
     o->use_graph = 1;
+    o->precond = CFP_PRECOND_RBGS;
+    o->mg_smooth = 2;
 }
 
 const char* cfp_last_error(void) { return g_last_error.c_str(); }
@@ -144,6 +146,7 @@ void cfp_ctx_destroy(cfp_ctx* c) {
     else cudaDeviceSynchronize();
     for (int q = 0; q < 2; ++q)
         if (c->gexec[q]) cudaGraphExecDestroy(c->gexec[q]);
+    free_mg(c);
     void* ptrs[] = {c->dcoef64, c->dcoef32, c->dX[0], c->dX[1], c->dX[2], c->dbodies, c->type, c->slot, c->irr_lin,
                     c->ibi_off, c->ibi_xyz, c->corr_ptr, c->corr_off, c->corr_val, c->corr_val32, c->bib_ptr,
                     c->bib_idx, c->bib_val, c->krow, c->krow32, c->scan_bsum, c->dtotal, c->derr, c->v64, c->v32,
@@ -213,8 +216,33 @@ cfp_status cfp_precondition(cfp_ctx* c, int sweeps, const double* rho, double* p
     CFP_TRY(need_field(phi, "phi_dev"));
     if (sweeps < 0) return fail(CFP_EINVAL, "sweeps must be >= 0");
     if (rho == phi) return fail(CFP_EINVAL, "rho and phi must not overlap");
+    CFP_TRY(ensure_work(c, false));
+    if (phi == c->v64 + (int64_t)V_TMP2 * c->N) return fail(CFP_EINVAL, "phi aliases the context's work space");
     CFP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * c->N, c->stream));
+    c->precond_kind = CFP_PRECOND_RBGS;
     launch_precond<double>(c, sweeps, rho, phi, c->stream);
+    CFP_CUDA(cudaGetLastError());
+    return CFP_OK;
+}
+
+cfp_status cfp_precondition_ex(cfp_ctx* c, const cfp_opts* o, const double* rho, double* phi) {
+    cfp_opts opts;
+    cfp_default_opts(&opts);
+    if (o) opts = *o;
+    CFP_TRY(need_classified(c));
+    CFP_TRY(need_field(rho, "rho_dev"));
+    CFP_TRY(need_field(phi, "phi_dev"));
+    if (opts.sweeps < 0 || (opts.precond != CFP_PRECOND_RBGS && opts.precond != CFP_PRECOND_MG))
+        return fail(CFP_EINVAL, "bad sweeps or preconditioner");
+    if (rho == phi) return fail(CFP_EINVAL, "rho and phi must not overlap");
+    CFP_TRY(ensure_work(c, false));
+    if (phi == c->v64 + (int64_t)V_TMP2 * c->N) return fail(CFP_EINVAL, "phi aliases the context's work space");
+    c->precond_kind = opts.precond;
+    c->mg_smooth = std::max(1, opts.mg_smooth);
+    if (c->precond_kind == CFP_PRECOND_MG) CFP_TRY(ensure_mg(c));
+    CFP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * c->N, c->stream));
+    launch_precond<double>(c, opts.sweeps, rho, phi, c->stream);
+    c->precond_kind = CFP_PRECOND_RBGS;
     CFP_CUDA(cudaGetLastError());
     return CFP_OK;
 }

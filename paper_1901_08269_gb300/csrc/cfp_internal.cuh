@@ -85,11 +85,27 @@ struct DevError {
 enum { DETAIL_OFFGRID = 1, DETAIL_FEWPOINTS = 2, DETAIL_SINGULAR = 3, DETAIL_BOXIBI = 4,
        DETAIL_OVERFLOW = 5, DETAIL_MISSINGIBI = 6 };
 
-constexpr int kApplyTX = 32;
-constexpr int kApplyTY = 8;
-constexpr int kApplyKC = 32;
+constexpr int kAX = 32, kAY = 8;   // apply CTA tile (threads) in x and y
+constexpr int kApplyKC = 32;       // planes per apply CTA
 constexpr int kUpdBlocks = 152 * 8;   // grid of the vector-update kernels
 constexpr int kUpdThreads = 256;
+
+// One level of the multigrid hierarchy of the preconditioner (level 0 is the
+// fine grid, whose arrays belong to the context).
+struct MgLevel {
+    int n[3] = {0, 0, 0};
+    int64_t N = 0;
+    std::vector<double> X[3];
+    double* coef64 = nullptr;  // 8 arrays per axis (only ka, kb, kc used)
+    float* coef32 = nullptr;
+    uint8_t* type = nullptr;
+    double* v64 = nullptr;     // e, b, r
+    float* v32 = nullptr;
+    int* ilo[3] = {nullptr, nullptr, nullptr};  // interpolation from the next coarser level
+    int64_t off[3] = {0, 0, 0};
+    double* w64 = nullptr;
+    float* w32 = nullptr;
+};
 
 }  // namespace cfp
 
@@ -149,12 +165,20 @@ struct cfp_ctx {
     double* hs_gi = nullptr;
     int64_t hs_gi_cap = 0;
 
-    // kernels enqueued since the counter was last reset
+    // kernels enqueued since the context was created
     int64_t launches = 0;
+
+    // preconditioner of the current solve and its multigrid hierarchy
+    int precond_kind = CFP_PRECOND_RBGS;
+    int mg_smooth = 2;
+    std::vector<cfp::MgLevel> mg;
 
     // graphs: [precision][sweeps-config]
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int gsweeps[2] = {-1, -1};
+    int gprecond[2] = {-1, -1};
+    int64_t body_launches = 0;
+    int gmgs[2] = {-1, -1};
 };
 
 namespace cfp {
@@ -185,8 +209,22 @@ void launch_apply(cfp_ctx* c, const T* x, T* y, const T* d0, int dotmode, double
 template <class T>
 void launch_precond(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s);
 template <class T>
-void launch_rbgs_half(cfp_ctx* c, const T* rho, T* phi, int colour, bool first, cudaStream_t s);
-inline int precond_kernels(int sweeps) { return sweeps <= 0 ? 1 : 2 * sweeps; }
+void launch_rbgs_half(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s);
+template <class T>
+void launch_half_sweep(const Grid<T>& G, const Side<T>& S, const uint8_t* type, const T* rho, T* phi, int colour,
+                       bool first, cudaStream_t s);
+template <class T>
+T* precond_tmp(cfp_ctx* c);
+template <>
+double* precond_tmp<double>(cfp_ctx* c);
+template <>
+float* precond_tmp<float>(cfp_ctx* c);
+
+// multigrid (cfp_mg.cu)
+cfp_status ensure_mg(cfp_ctx* c);
+void free_mg(cfp_ctx* c);
+template <class T>
+void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s);
 void launch_qf(cfp_ctx* c, const double* f, double* out, cudaStream_t s);
 void launch_rhs_finish(cfp_ctx* c, const double* qf, const double* bg, const double* g_ibi,
                        double* rhs, cudaStream_t s);

@@ -265,11 +265,16 @@ void enqueue_body(cfp_ctx* c, int prec, int sweeps, cudaStream_t s, cudaGraphCon
     c->launches += 6;
 }
 
-int body_kernels(int sweeps) { return 2 * precond_kernels(sweeps) + 2 + 6; }
+int64_t body_launches(cfp_ctx* c);
+
+// kernels of one iteration body, counted by enqueueing it on a dummy path
+int64_t body_launches(cfp_ctx* c) { return c->body_launches; }
 
 template <class T>
 cfp_status build_graph(cfp_ctx* c, int prec, int sweeps) {
-    if (c->gexec[prec] && c->gsweeps[prec] == sweeps) return CFP_OK;
+    if (c->gexec[prec] && c->gsweeps[prec] == sweeps && c->gprecond[prec] == c->precond_kind &&
+        c->gmgs[prec] == c->mg_smooth)
+        return CFP_OK;
     if (c->gexec[prec]) {
         cudaGraphExecDestroy(c->gexec[prec]);
         c->gexec[prec] = nullptr;
@@ -292,6 +297,7 @@ cfp_status build_graph(cfp_ctx* c, int prec, int sweeps) {
     if (e == cudaSuccess) {
         const int64_t saved = c->launches;
         enqueue_body<T>(c, prec, sweeps, cs, h, 1);
+        c->body_launches = c->launches - saved;
         c->launches = saved;
         cudaGraph_t out = nullptr;
         e = cudaStreamEndCapture(cs, &out);
@@ -307,6 +313,8 @@ cfp_status build_graph(cfp_ctx* c, int prec, int sweeps) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     c->gexec[prec] = exec;
     c->gsweeps[prec] = sweeps;
+    c->gprecond[prec] = c->precond_kind;
+    c->gmgs[prec] = c->mg_smooth;
     return CFP_OK;
 }
 
@@ -344,7 +352,7 @@ cfp_status run_bicgstab(cfp_ctx* c, int prec, const T* b, double stop2, int maxi
     }
     CFP_CUDA(cudaMemcpyAsync(hs, st, sizeof(KState), cudaMemcpyDeviceToHost, c->stream));
     CFP_CUDA(cudaStreamSynchronize(c->stream));
-    if (use_graph) c->launches += (int64_t)hs->execs * body_kernels(sweeps);
+    if (use_graph) c->launches += (int64_t)hs->execs * c->body_launches;
     *flag = hs->flag == FLAG_RUN ? FLAG_MAXIT : hs->flag;
     *used = hs->iter;
     *rr = hs->rr;
@@ -389,8 +397,8 @@ cfp_status ensure_work(cfp_ctx* c, bool need32) {
         CFP_CUDA(cudaMemsetAsync(c->v64, 0, sizeof(double) * N * kNV64, c->stream));
     }
     if (need32 && !c->v32) {
-        CFP_CUDA(cudaMalloc(&c->v32, sizeof(float) * N * (kNV32 + 1)));
-        CFP_CUDA(cudaMemsetAsync(c->v32, 0, sizeof(float) * N * (kNV32 + 1), c->stream));
+        CFP_CUDA(cudaMalloc(&c->v32, sizeof(float) * N * (kNV32 + 2)));
+        CFP_CUDA(cudaMemsetAsync(c->v32, 0, sizeof(float) * N * (kNV32 + 2), c->stream));
     }
     const int64_t need = 2 * (int64_t)std::max(apply_blocks(c), kUpdBlocks);
     if (c->partial_cap < need) {
@@ -414,7 +422,7 @@ cfp_status time_kernel_t(cfp_ctx* c, int prec, int kernel, int reps, double* ms,
     const int64_t nint = (int64_t)(c->n[0] - 2) * (c->n[1] - 2) * (c->n[2] - 2);
     auto launch = [&]() {
         if (kernel == CFP_KERNEL_APPLY) launch_apply<T>(c, V.ph, V.v, V.rh, 1, c->partial, c->stream, nullptr);
-        else if (kernel == CFP_KERNEL_RBGS) launch_rbgs_half<T>(c, V.p, V.ph, 0, false, c->stream);
+        else if (kernel == CFP_KERNEL_RBGS) launch_rbgs_half<T>(c, V.p, V.ph, c->stream);
         else
             k_update_xr<T><<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(V.x, V.r, V.ph, V.sh, V.s, V.t, V.rh, st,
                                                                       c->partial, c->N);
@@ -468,6 +476,11 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
     if (!(tol > 0.0) || opts.maxit < 1 || opts.sweeps < 0) return fail(CFP_EINVAL, "bad tol, maxit or sweeps");
     const int64_t launches0 = c->launches;
     if (!c->classified) CFP_TRY(classify(c));
+    if (opts.precond != CFP_PRECOND_RBGS && opts.precond != CFP_PRECOND_MG)
+        return fail(CFP_EINVAL, "unknown preconditioner");
+    c->precond_kind = opts.precond;
+    c->mg_smooth = std::max(1, opts.mg_smooth);
+    if (c->precond_kind == CFP_PRECOND_MG) CFP_TRY(ensure_mg(c));
     const bool mixed = opts.precision == CFP_PREC_MIXED;
     CFP_TRY(ensure_work(c, mixed));
     const int64_t N = c->N;

@@ -84,17 +84,27 @@ __device__ __forceinline__ void block_reduce2(double& a, double& b) {
     }
 }
 
-// DOT = 0: y only; 1: partial (d0, y); 2: partials (d0, y) and (y, y)
+// B x at the unknowns.  A CTA of kAX x kAY threads owns a kAX x kAY tile of
+// (i, j) columns and marches kApplyKC planes in z.  Per plane, rows j0-1 ..
+// j0+kAY of the tile form the x-pass XR = Rx x, XL = Lx x (shared memory),
+// each thread then forms the y-pass P = Ly XR + Ry XL, Q = Ly XL of its
+// column and keeps P, Q of three planes in registers for the z-pass
+//   out(k) = Lz (P(k-1), P(k), P(k+1)) + Rz (Q(k-1), Q(k), Q(k+1)).
+// The loads of the next plane are issued before the current plane is
+// processed (clamped addresses, results masked), so memory latency overlaps
+// the arithmetic and the barriers.  Irregular rows add their side-list
+// corrections; solid rows are zero.
+// DOT = 0: y only; 1: partial (d0, y); 2: partials (d0, y) and (y, y).
 template <class T, int DOT>
-__global__ void __launch_bounds__(kApplyTX* kApplyTY)
+__global__ void __launch_bounds__(kAX* kAY)
     k_apply(Grid<T> G, Side<T> S, const uint8_t* __restrict__ type, const T* __restrict__ x,
             T* __restrict__ y, const T* __restrict__ d0, double* __restrict__ partial) {
-    __shared__ T sR[kApplyTY + 2][kApplyTX];
-    __shared__ T sL[kApplyTY + 2][kApplyTX];
+    __shared__ T sR[kAY + 2][kAX];
+    __shared__ T sL[kAY + 2][kAX];
     const int nx = G.nx, ny = G.ny, nz = G.nz;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = 1 + blockIdx.x * kApplyTX + tx;
-    const int j0 = 1 + blockIdx.y * kApplyTY;
+    const int i = 1 + blockIdx.x * kAX + tx;
+    const int j0 = 1 + blockIdx.y * kAY;
     const int j = j0 + ty;
     const int k0 = 1 + blockIdx.z * kApplyKC;
     const int k1 = min(k0 + kApplyKC, nz - 1);
@@ -118,21 +128,34 @@ __global__ void __launch_bounds__(kApplyTX* kApplyTY)
         bry = G.ax[1].br[j];
         cry = G.ax[1].cr[j];
     }
+    // the two x-pass rows this thread loads: ty and (ty < 2) ty + kAY
+    const int ic = iin ? i : 1;
+    const bool v0 = iin && (j0 - 1 + ty) <= ny - 1;
+    const bool v1 = iin && ty < 2 && (j0 - 1 + ty + kAY) <= ny - 1;
+    const T* p0 = x + (int64_t)(k0 - 1) * sz + (int64_t)(v0 ? j0 - 1 + ty : 1) * sy + ic;
+    const T* p1 = x + (int64_t)(k0 - 1) * sz + (int64_t)(v1 ? j0 - 1 + ty + kAY : 1) * sy + ic;
+    T a0m = p0[-1], a0c = p0[0], a0p = p0[1];
+    T a1m = p1[-1], a1c = p1[0], a1p = p1[1];
+
     T Pm = 0, P0 = 0, Pp = 0, Qm = 0, Q0 = 0, Qp = 0;
     double acc0 = 0.0, acc1 = 0.0;
-
     for (int kk = k0 - 1; kk <= k1; ++kk) {
-        for (int r = ty; r < kApplyTY + 2; r += kApplyTY) {
-            const int J = j0 - 1 + r;
-            T vr = 0, vl = 0;
-            if (iin && J <= ny - 1) {
-                const T* row = x + (int64_t)kk * sz + (int64_t)J * sy + i;
-                const T xm = row[-1], xc = row[0], xp = row[1];
-                vr = arx * xm + brx * xc + crx * xp;
-                vl = ax * xm + xc + cx * xp;
-            }
-            sR[r][tx] = vr;
-            sL[r][tx] = vl;
+        const T c0m = a0m, c0c = a0c, c0p = a0p, c1m = a1m, c1c = a1c, c1p = a1p;
+        if (kk < k1) {  // prefetch plane kk + 1
+            p0 += sz;
+            p1 += sz;
+            a0m = p0[-1];
+            a0c = p0[0];
+            a0p = p0[1];
+            a1m = p1[-1];
+            a1c = p1[0];
+            a1p = p1[1];
+        }
+        sR[ty][tx] = v0 ? arx * c0m + brx * c0c + crx * c0p : T(0);
+        sL[ty][tx] = v0 ? ax * c0m + c0c + cx * c0p : T(0);
+        if (ty < 2) {
+            sR[ty + kAY][tx] = v1 ? arx * c1m + brx * c1c + crx * c1p : T(0);
+            sL[ty + kAY][tx] = v1 ? ax * c1m + c1c + cx * c1p : T(0);
         }
         __syncthreads();
         const T P = ay * sR[ty][tx] + sR[ty + 1][tx] + cy * sR[ty + 2][tx] + ary * sL[ty][tx] +
@@ -175,52 +198,49 @@ __global__ void __launch_bounds__(kApplyTX* kApplyTY)
 }
 
 // One red-black Gauss-Seidel half-sweep on K phi = rho over the points of
-// one colour ((i+j+k) % 2 == colour).  FIRST: phi = 0 on entry, so the
-// neighbour sum vanishes.  Only unknowns are written; phi must be zero at
-// box and solid nodes.
+// one colour ((i+j+k) % 2 == colour), in place.  FIRST: phi = 0 on entry, so
+// the neighbour sum vanishes.  Only unknowns are written; phi must be zero at
+// box and solid nodes.  Launch: x over the colour points of a row, y = j-1,
+// z = k-1 (no integer division per point).  Used on every multigrid level
+// (coarse levels have no irregular points).
+constexpr int kRbgsThreads = 128;
+
 template <class T, bool FIRST>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kRbgsThreads)
     k_rbgs(Grid<T> G, Side<T> S, const uint8_t* __restrict__ type, const T* __restrict__ rho,
            T* __restrict__ phi, int colour) {
-    const int nx = G.nx, ny = G.ny, nz = G.nz;
-    const int nh = (nx - 1) / 2;
+    const int nx = G.nx, ny = G.ny;
+    const int j = 1 + blockIdx.y, k = 1 + blockIdx.z;
+    const int i = 1 + ((1 + j + k + colour) & 1) + 2 * (int)(blockIdx.x * kRbgsThreads + threadIdx.x);
+    if (i > nx - 2) return;
     const int64_t sy = nx, sz = (int64_t)nx * ny;
-    const int64_t total = (int64_t)nh * (ny - 2) * (nz - 2);
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int m = (int)(q % nh);
-        const int j = 1 + (int)((q / nh) % (ny - 2));
-        const int k = 1 + (int)(q / ((int64_t)nh * (ny - 2)));
-        const int i = 1 + ((1 + j + k + colour) & 1) + 2 * m;
-        if (i > nx - 2) continue;
-        const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
-        const uint8_t t = type[l];
-        if (t != CFP_REGULAR && t != CFP_IRREGULAR) continue;
-        T dg, cxm, cxp, cym, cyp, czm, czp;
-        if (t == CFP_IRREGULAR) {
-            const T* kr = S.krow + 7 * (int64_t)S.slot[l];
-            dg = kr[0];
-            cxm = kr[1];
-            cxp = kr[2];
-            cym = kr[3];
-            cyp = kr[4];
-            czm = kr[5];
-            czp = kr[6];
-        } else {
-            dg = G.ax[0].kb[i] + G.ax[1].kb[j] + G.ax[2].kb[k];
-            cxm = G.ax[0].ka[i];
-            cxp = G.ax[0].kc[i];
-            cym = G.ax[1].ka[j];
-            cyp = G.ax[1].kc[j];
-            czm = G.ax[2].ka[k];
-            czp = G.ax[2].kc[k];
-        }
-        T v = rho[l];
-        if (!FIRST)
-            v -= (cxm * phi[l - 1] + cxp * phi[l + 1]) + (cym * phi[l - sy] + cyp * phi[l + sy]) +
-                 (czm * phi[l - sz] + czp * phi[l + sz]);
-        phi[l] = v / dg;
+    const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
+    const uint8_t t = type[l];
+    if (t != CFP_REGULAR && t != CFP_IRREGULAR) return;
+    T dg, cxm, cxp, cym, cyp, czm, czp;
+    if (t == CFP_IRREGULAR) {
+        const T* kr = S.krow + 7 * (int64_t)S.slot[l];
+        dg = kr[0];
+        cxm = kr[1];
+        cxp = kr[2];
+        cym = kr[3];
+        cyp = kr[4];
+        czm = kr[5];
+        czp = kr[6];
+    } else {
+        dg = G.ax[0].kb[i] + G.ax[1].kb[j] + G.ax[2].kb[k];
+        cxm = G.ax[0].ka[i];
+        cxp = G.ax[0].kc[i];
+        cym = G.ax[1].ka[j];
+        cyp = G.ax[1].kc[j];
+        czm = G.ax[2].ka[k];
+        czp = G.ax[2].kc[k];
     }
+    T v = rho[l];
+    if (!FIRST)
+        v -= (cxm * phi[l - 1] + cxp * phi[l + 1]) + (cym * phi[l - sy] + cyp * phi[l + sy]) +
+             (czm * phi[l - sz] + czp * phi[l + sz]);
+    phi[l] = v / dg;
 }
 
 template <class T>
@@ -328,8 +348,30 @@ unsigned flat_grid(int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
+}  // namespace
+
+// colour points per row: ceil((nx - 2) / 2) = (nx - 1) / 2
+dim3 rbgs_grid(int nx, int ny, int nz) {
+    const int nh = (nx - 1) / 2;
+    return dim3((unsigned)((nh + kRbgsThreads - 1) / kRbgsThreads), (unsigned)(ny - 2), (unsigned)(nz - 2));
+}
+
+template <class T>
+void launch_half_sweep(const Grid<T>& G, const Side<T>& S, const uint8_t* type, const T* rho, T* phi, int colour,
+                       bool first, cudaStream_t s) {
+    const dim3 nb = rbgs_grid(G.nx, G.ny, G.nz);
+    if (first) k_rbgs<T, true><<<nb, kRbgsThreads, 0, s>>>(G, S, type, rho, phi, colour);
+    else k_rbgs<T, false><<<nb, kRbgsThreads, 0, s>>>(G, S, type, rho, phi, colour);
+}
+template void launch_half_sweep<double>(const Grid<double>&, const Side<double>&, const uint8_t*, const double*,
+                                        double*, int, bool, cudaStream_t);
+template void launch_half_sweep<float>(const Grid<float>&, const Side<float>&, const uint8_t*, const float*, float*,
+                                       int, bool, cudaStream_t);
+
+namespace {
+
 dim3 apply_grid(const cfp_ctx* c) {
-    return dim3((unsigned)((c->n[0] - 2 + kApplyTX - 1) / kApplyTX), (unsigned)((c->n[1] - 2 + kApplyTY - 1) / kApplyTY),
+    return dim3((unsigned)((c->n[0] - 2 + kAX - 1) / kAX), (unsigned)((c->n[1] - 2 + kAY - 1) / kAY),
                 (unsigned)((c->n[2] - 2 + kApplyKC - 1) / kApplyKC));
 }
 
@@ -354,7 +396,7 @@ template <class T>
 void launch_apply(cfp_ctx* c, const T* x, T* y, const T* d0, int dotmode, double* partial, cudaStream_t s,
                   int* nblocks_out) {
     const dim3 grid = apply_grid(c);
-    const dim3 block(kApplyTX, kApplyTY);
+    const dim3 block(kAX, kAY);
     const Grid<T> G = grid_view<T>(c);
     const Side<T> S = side_view<T>(c);
     if (dotmode == 0) k_apply<T, 0><<<grid, block, 0, s>>>(G, S, c->type, x, y, d0, partial);
@@ -364,34 +406,42 @@ void launch_apply(cfp_ctx* c, const T* x, T* y, const T* d0, int dotmode, double
     if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
 }
 
+template <>
+double* precond_tmp<double>(cfp_ctx* c) { return c->v64 + (int64_t)V_TMP2 * c->N; }
+template <>
+float* precond_tmp<float>(cfp_ctx* c) { return c->v32 + (int64_t)(kNV32 + 1) * c->N; }
+
+// `sweeps` red-black sweeps from phi = 0 (sweeps = 0: masked copy).
 template <class T>
-void launch_precond(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s) {
+void launch_precond_rbgs(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s) {
     const Grid<T> G = grid_view<T>(c);
     const Side<T> S = side_view<T>(c);
-    c->launches += precond_kernels(sweeps);
+    c->launches += sweeps <= 0 ? 1 : 2 * sweeps;
     if (sweeps <= 0) {
         k_mask_copy<T><<<flat_grid(c->N), 256, 0, s>>>(c->type, rho, phi, c->N);
         return;
     }
-    const int64_t half = (int64_t)((c->n[0] - 1) / 2) * (c->n[1] - 2) * (c->n[2] - 2);
-    const unsigned nb = flat_grid(half);
     for (int sw = 0; sw < sweeps; ++sw) {
-        if (sw == 0) k_rbgs<T, true><<<nb, 256, 0, s>>>(G, S, c->type, rho, phi, 0);
-        else k_rbgs<T, false><<<nb, 256, 0, s>>>(G, S, c->type, rho, phi, 0);
-        k_rbgs<T, false><<<nb, 256, 0, s>>>(G, S, c->type, rho, phi, 1);
+        launch_half_sweep<T>(G, S, c->type, rho, phi, 0, sw == 0, s);
+        launch_half_sweep<T>(G, S, c->type, rho, phi, 1, false, s);
     }
 }
 
 template <class T>
-void launch_rbgs_half(cfp_ctx* c, const T* rho, T* phi, int colour, bool first, cudaStream_t s) {
-    const int64_t half = (int64_t)((c->n[0] - 1) / 2) * (c->n[1] - 2) * (c->n[2] - 2);
-    if (first) k_rbgs<T, true><<<flat_grid(half), 256, 0, s>>>(grid_view<T>(c), side_view<T>(c), c->type, rho, phi, colour);
-    else k_rbgs<T, false><<<flat_grid(half), 256, 0, s>>>(grid_view<T>(c), side_view<T>(c), c->type, rho, phi, colour);
+void launch_precond(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s) {
+    if (c->precond_kind == CFP_PRECOND_MG) launch_precond_mg<T>(c, rho, phi, s);
+    else launch_precond_rbgs<T>(c, sweeps, rho, phi, s);
+}
+
+// one half-sweep (not the first), for timing
+template <class T>
+void launch_rbgs_half(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
+    launch_half_sweep<T>(grid_view<T>(c), side_view<T>(c), c->type, rho, phi, 0, false, s);
     c->launches += 1;
 }
 
-template void launch_rbgs_half<double>(cfp_ctx*, const double*, double*, int, bool, cudaStream_t);
-template void launch_rbgs_half<float>(cfp_ctx*, const float*, float*, int, bool, cudaStream_t);
+template void launch_rbgs_half<double>(cfp_ctx*, const double*, double*, cudaStream_t);
+template void launch_rbgs_half<float>(cfp_ctx*, const float*, float*, cudaStream_t);
 template void launch_apply<double>(cfp_ctx*, const double*, double*, const double*, int, double*, cudaStream_t,
                                    int*);
 template void launch_apply<float>(cfp_ctx*, const float*, float*, const float*, int, double*, cudaStream_t, int*);

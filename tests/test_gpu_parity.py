@@ -220,3 +220,53 @@ def test_errors_are_reported_not_raised_on_device():
     u.zero_()
     info = ctx2.solve(f2, g2, None, u, tol=1e-12)
     assert info.status == 0
+
+
+# ---------------------------------------------------------------- multigrid
+@pytest.mark.parametrize("name", ["c2-33", "ragged-torus", "c3-bodies-65", "random-8"])
+def test_solve_parity_multigrid(name):
+    # The converged solution does not depend on the preconditioner: the
+    # V-cycle solve must match the oracle's red-black solve like the others.
+    p = pair(name)
+    f, g = p.w.fields()
+    gi = p.w.g_at(p.oxyz)
+    uo, st, it, rel = p.P.solve(f, g, gi, tol=1e-13)
+    u = torch.zeros(p.w.N, dtype=torch.float64, device="cuda")
+    info = p.ctx.solve(dev(f), dev(g), dev(gi), u, tol=1e-13, precond=cfp.PRECOND_MG)
+    assert info.status == 0 and info.rel_residual <= 1e-13
+    assert np.max(np.abs(u.cpu().numpy() - uo)) <= 1e-10 * np.max(np.abs(uo))
+    assert info.iterations < it
+
+
+def test_multigrid_iterations_do_not_grow_with_n():
+    its = []
+    for n in (33, 65, 129):
+        w = W.config2(n)
+        ctx = cfp.Context(w.x, w.y, w.z, w.bodies)
+        ctx.classify_points()
+        xyz = ctx.ibi_points()
+        f, g = w.fields(torch, "cuda")
+        u = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+        info = ctx.solve(f, g, w.g_at(xyz, torch), u, tol=1e-12, precond=cfp.PRECOND_MG)
+        assert info.status == 0
+        its.append(info.iterations)
+    assert its[-1] <= 2 * its[0] + 4, its
+
+
+@pytest.mark.parametrize("name", ["c2-33", "ragged-torus"])
+def test_multigrid_preconditioner_is_linear_and_approximates_K_inverse(name):
+    p = pair(name)
+    K = p.P.export(O.MAT_K)
+    a, b = p.rand_field(5), p.rand_field(6)
+    outs = []
+    for v in (a, b, 2.0 * a - 3.0 * b):
+        phi = torch.zeros(p.w.N, dtype=torch.float64, device="cuda")
+        p.ctx.precondition_ex(dev(v), phi, precond=cfp.PRECOND_MG)
+        outs.append(phi.cpu().numpy())
+    np.testing.assert_allclose(outs[2], 2.0 * outs[0] - 3.0 * outs[1], atol=1e-11 * np.max(np.abs(outs[2])))
+    # residual of K phi = rho after one V-cycle, versus 8 red-black sweeps
+    res_mg = np.linalg.norm((a - K @ outs[0])[p.unk]) / np.linalg.norm(a[p.unk])
+    phi = torch.zeros(p.w.N, dtype=torch.float64, device="cuda")
+    p.ctx.precondition(dev(a), phi, 8)
+    res_gs = np.linalg.norm((a - K @ phi.cpu().numpy())[p.unk]) / np.linalg.norm(a[p.unk])
+    assert res_mg < 0.5 and res_mg < res_gs, (res_mg, res_gs)
