@@ -29,9 +29,11 @@ sys.path.insert(0, ROOT)
 METRIC = "s/solve at 513³ to equal max-norm error, plain FP64 vs mixed/learned; HBM GB/s"
 UNIT = "s/solve"
 FALLBACK_HBM_GBS = 6800.0
-# FP64 iterations of the 513^3 workload, measured by the GPU path (used by
-# the reference arm, which cannot run the 513^3 solve itself)
-FP64_ITERS_513 = 400
+# BiCGSTAB iterations of the 513^3 workload in FP64 with the oracle's own
+# preconditioner (8 red-black sweeps) to tol 1e-15, measured by the GPU path
+# with the same preconditioner; the CPU baselines extrapolate with it since
+# the oracle cannot run the 513^3 solve itself.
+FP64_RBGS_ITERS_513 = 650
 
 
 def parse():
@@ -47,6 +49,9 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=8)
     ap.add_argument("--precond", default="mg", choices=["mg", "rbgs"])
     ap.add_argument("--mg-smooth", type=int, default=2)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="plain launches instead of the CUDA graph (ncu cannot profile kernel nodes of graphs "
+                         "with conditional nodes)")
     ap.add_argument("--no-fp64-check", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -168,13 +173,13 @@ def reference_arm(args):
         return 0
     vals = []
     for s in range(args.warmup + args.steps):
-        r = oracle_sample(args.oracle_n, args.oracle_iters, args.n, FP64_ITERS_513)
+        r = oracle_sample(args.oracle_n, args.oracle_iters, args.n, FP64_RBGS_ITERS_513)
         if s >= args.warmup:
             vals.append(r["est_s_per_solve"])
     v = statistics.mean(vals)
     sample = ("oracle (plain C, FP64, CSR) on config-3 geometry at %d^3: set-up + %d BiCGSTAB iterations, "
               "extrapolated to a %d^3 solve of %d iterations by the node-count ratio" %
-              (args.oracle_n, r["iters"], args.n, FP64_ITERS_513))
+              (args.oracle_n, r["iters"], args.n, FP64_RBGS_ITERS_513))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -216,7 +221,7 @@ def main():
     prec = cfp.PREC_MIXED if args.precision == "mixed" else cfp.PREC_FP64
     pc = cfp.PRECOND_MG if args.precond == "mg" else cfp.PRECOND_RBGS
     opts = cfp.default_opts(precision=prec, sweeps=args.sweeps, inner_tol=args.inner_tol, precond=pc,
-                            mg_smooth=args.mg_smooth)
+                            mg_smooth=args.mg_smooth, use_graph=0 if args.no_graph else 1)
 
     def step():
         ctx.classify_points()
@@ -226,6 +231,16 @@ def main():
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
+    # phase split of one step (outside the timed region)
+    a, b, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    a.record(stream)
+    ctx.classify_points()
+    b.record(stream)
+    u.zero_()
+    ctx.solve(f, g, gi, u, tol=args.tol, opts=opts)
+    c2.record(stream)
+    torch.cuda.synchronize()
+    phases = {"setup_ms": a.elapsed_time(b), "rhs_and_solve_ms": b.elapsed_time(c2)}
     if dist:
         dist.barrier()
     clocks = ClockSampler(local)
@@ -318,11 +333,12 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        iters_full = fp64["iterations"] if fp64 else FP64_ITERS_513
+        iters_full = FP64_RBGS_ITERS_513
         r = oracle_sample(args.oracle_n, args.oracle_iters, args.n, iters_full)
         cpu = {"value": r["est_s_per_solve"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                "sample": "oracle (plain C, FP64, CSR, OpenMP) on the same geometry at %d^3: set-up + %d "
-                         "BiCGSTAB iterations (%.1f s wall), extrapolated to a %d^3 FP64 solve of %d iterations "
+                         "BiCGSTAB iterations with its 8-sweep red-black preconditioner (%.1f s wall), extrapolated "
+                         "to a %d^3 FP64 solve of %d iterations (the count the same preconditioner needs on the GPU) "
                          "by the node-count ratio" % (args.oracle_n, r["iters"], r["wall_s"], args.n, iters_full)}
 
     if rank == 0:
@@ -335,8 +351,9 @@ def main():
                            "tol": args.tol, "inner_tol": args.inner_tol, "sweeps": args.sweeps,
                            "precond": args.precond, "mg_smooth": args.mg_smooth,
                            "l2": "no flush: every field (1.08 GB at 513^3) exceeds the 129 MB L2",
-                           "parallelism": "replicas" if world > 1 else "single"},
-                "result": result, "fp64": fp64, "kernels": kern, "roofline": roofline, "cpu_baseline": cpu,
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "graph": not args.no_graph},
+                "result": result, "phases": phases, "fp64": fp64, "kernels": kern, "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     ctx.close()
