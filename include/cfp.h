@@ -49,7 +49,8 @@ enum { CFP_SPHERE = 0, CFP_ELLIPSOID = 1, CFP_TORUS = 2 };
 typedef struct {
     int kind;      /* CFP_SPHERE, CFP_ELLIPSOID or CFP_TORUS                */
     double c[3];   /* centre                                               */
-    double R[9];   /* row-major body-to-world rotation (identity if none)  */
+    double R[9];   /* row-major body-to-world rotation (identity if none);
+                      must be orthonormal to 1e-9 (else CFP_EINVAL)        */
     double p[3];   /* sphere: radius; ellipsoid: semi-axes; torus: major
                       radius, minor radius (torus axis = body z axis)      */
 } cfp_body;

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "cfp_internal.cuh"
 
@@ -94,6 +95,12 @@ cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny, cons
         const int np = b.kind == CFP_SPHERE ? 1 : (b.kind == CFP_TORUS ? 2 : 3);
         for (int q = 0; q < np; ++q)
             if (!(b.p[q] > 0.0)) return fail(CFP_EINVAL, "body sizes must be positive");
+        for (int r = 0; r < 3; ++r)       // R must be a rotation: R^T R = I
+            for (int q = 0; q < 3; ++q) {
+                double d = 0.0;
+                for (int m2 = 0; m2 < 3; ++m2) d += b.R[3 * m2 + r] * b.R[3 * m2 + q];
+                if (!(fabs(d - (r == q ? 1.0 : 0.0)) <= 1e-9)) return fail(CFP_EINVAL, "body R is not a rotation");
+            }
     }
     cfp_ctx* c = new cfp_ctx();
     c->N = N;
@@ -115,6 +122,7 @@ cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny, cons
     chk(cudaMalloc(&c->dcoef32, sizeof(float) * ncoef), "cudaMalloc");
     for (int d = 0; d < 3; ++d) chk(cudaMalloc(&c->dX[d], sizeof(double) * n[d]), "cudaMalloc");
     chk(cudaMalloc(&c->dbodies, sizeof(cfp_body) * std::max(nbodies, 1)), "cudaMalloc");
+    chk(cudaMalloc(&c->dbound2, sizeof(double) * std::max(nbodies, 1)), "cudaMalloc");
     chk(cudaMalloc(&c->type, (size_t)N), "cudaMalloc");
     chk(cudaMalloc(&c->slot, sizeof(int32_t) * (size_t)N), "cudaMalloc");
     chk(cudaMalloc(&c->dtotal, sizeof(long long) * 8), "cudaMalloc");
@@ -126,9 +134,23 @@ cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny, cons
             chk(cudaMemcpyAsync(c->dX[d], src[d], sizeof(double) * n[d], cudaMemcpyHostToDevice, c->stream),
                 "cudaMemcpyAsync");
         launch_metrics(c);
-        if (nbodies)
+        if (nbodies) {
             chk(cudaMemcpyAsync(c->dbodies, bodies, sizeof(cfp_body) * nbodies, cudaMemcpyHostToDevice, c->stream),
                 "cudaMemcpyAsync");
+            // bounding radius: sphere r, ellipsoid largest semi-axis, torus R + r;
+            // the 1e-3 relative margin keeps phi far from zero outside it
+            // (R is a rotation, so the body frame keeps distances)
+            static thread_local std::vector<double> b2;
+            b2.assign(nbodies, 0.0);
+            for (int m = 0; m < nbodies; ++m) {
+                const cfp_body& b = bodies[m];
+                const double r = b.kind == CFP_SPHERE ? b.p[0]
+                               : b.kind == CFP_ELLIPSOID ? std::max(b.p[0], std::max(b.p[1], b.p[2]))
+                                                         : b.p[0] + b.p[1];
+                b2[m] = (r * 1.001) * (r * 1.001);
+            }
+            chk(cudaMemcpy(c->dbound2, b2.data(), sizeof(double) * nbodies, cudaMemcpyHostToDevice), "cudaMemcpy");
+        }
         chk(cudaGetLastError(), "k_metrics");
         chk(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
     }
@@ -147,7 +169,7 @@ void cfp_ctx_destroy(cfp_ctx* c) {
     for (int q = 0; q < 2; ++q)
         if (c->gexec[q]) cudaGraphExecDestroy(c->gexec[q]);
     free_mg(c);
-    void* ptrs[] = {c->dcoef64, c->dcoef32, c->dX[0], c->dX[1], c->dX[2], c->dbodies, c->type, c->slot, c->irr_lin,
+    void* ptrs[] = {c->dcoef64, c->dcoef32, c->dX[0], c->dX[1], c->dX[2], c->dbodies, c->dbound2, c->type, c->slot, c->irr_lin,
                     c->ibi_off, c->ibi_xyz, c->corr_ptr, c->corr_off, c->corr_val, c->corr_val32, c->bib_ptr,
                     c->bib_idx, c->bib_val, c->krow, c->krow32, c->scan_bsum, c->dtotal, c->derr, c->v64, c->v32,
                     c->partial, c->kst, c->hs_f, c->hs_g, c->hs_u, c->hs_gi};

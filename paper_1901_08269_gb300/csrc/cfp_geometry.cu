@@ -70,9 +70,34 @@ __device__ __forceinline__ double edge_pos(double xa, double xb, double t) {
 struct GeoArgs {
     const double* X[3];
     const cfp_body* bodies;
+    const double* bound2;  // per body: squared radius of a sphere around it, with margin
     int nb, inside;
     int n[3];
 };
+
+// Sign of the level set at a grid node.  A body is evaluated exactly only
+// when the node lies inside its bounding sphere; outside it phi > 0 holds
+// with a margin far above rounding, so the sign (and the classification)
+// is the one the exact evaluation gives.
+__device__ bool node_solid(const GeoArgs& g, double x, double y, double z) {
+    bool solid = false;
+    double phi = INFINITY;
+    for (int m = 0; m < g.nb; ++m) {
+        const cfp_body& b = g.bodies[m];
+        const double dx = x - b.c[0], dy = y - b.c[1], dz = z - b.c[2];
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        if (g.inside) {
+            const double v = body_phi(b, x, y, z);
+            if (v < phi) phi = v;
+        } else if (d2 <= g.bound2[m]) {
+            const double v = body_phi(b, x, y, z);
+            if (v < phi) phi = v;
+        }
+    }
+    if (g.inside) return -phi <= 0.0;
+    solid = phi <= 0.0;
+    return solid;
+}
 
 // ------------------------------------------------------------ classification
 __global__ void k_classify_solid(GeoArgs g, uint8_t* type, int64_t N) {
@@ -86,8 +111,7 @@ __global__ void k_classify_solid(GeoArgs g, uint8_t* type, int64_t N) {
         if (i == 0 || j == 0 || k == 0 || i == nx - 1 || j == ny - 1 || k == nz - 1) {
             t = CFP_BOUNDARY;
         } else {
-            const double ph = union_phi(g.bodies, g.nb, g.inside, g.X[0][i], g.X[1][j], g.X[2][k]);
-            t = ph <= 0.0 ? CFP_SOLID : CFP_REGULAR;
+            t = node_solid(g, g.X[0][i], g.X[1][j], g.X[2][k]) ? CFP_SOLID : CFP_REGULAR;
         }
         type[l] = t;
     }
@@ -561,12 +585,12 @@ __device__ void record_error(DevError* e, int code, int lin, int detail) {
     }
 }
 
-// mode 0: count entries; mode 1: write them (and the K rows)
-template <int MODE>
-__global__ void __launch_bounds__(64) k_side(SideArgs S, int* ccount, int* bcount,
-                                             const int32_t* corr_ptr, int32_t* corr_off,
-                                             double* corr_val, const int32_t* bib_ptr,
-                                             int32_t* bib_idx, double* bib_val, double* krow,
+// Builds the row of every irregular point once: its merged correction
+// entries and IBI weights go to a fixed-capacity scratch (kMaxCorr / kMaxBib
+// per slot) with their counts, its K row to krow.  A later kernel compacts
+// the scratch into CSR order.
+__global__ void __launch_bounds__(64) k_side(SideArgs S, int* ccount, int* bcount, int32_t* toff, double* tval,
+                                             int32_t* tbidx, double* tbval, double* krow,
                                              unsigned long long* ndeg, DevError* err) {
     const int nx = S.a.n[0], ny = S.a.n[1];
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S.a.n_irr;
@@ -590,27 +614,20 @@ __global__ void __launch_bounds__(64) k_side(SideArgs S, int* ccount, int* bcoun
         build_row(S, R);
         if (R.err) {
             record_error(err, CFP_EGEOM, (int)R.lin, R.err);
-            if (MODE == 0) {
-                ccount[s] = 0;
-                bcount[s] = 0;
-            }
+            ccount[s] = 0;
+            bcount[s] = 0;
             continue;
         }
-        if (MODE == 0) {
-            ccount[s] = corr.n;
-            bcount[s] = bib.n;
-            if (R.ndeg) atomicAdd(ndeg, (unsigned long long)R.ndeg);
-            continue;
-        }
-        const int c0 = corr_ptr[s];
+        ccount[s] = corr.n;
+        bcount[s] = bib.n;
+        if (R.ndeg) atomicAdd(ndeg, (unsigned long long)R.ndeg);
         for (int q = 0; q < corr.n; ++q) {
-            corr_off[c0 + q] = corr.off[q];
-            corr_val[c0 + q] = corr.val[q];
+            toff[s * kMaxCorr + q] = corr.off[q];
+            tval[s * kMaxCorr + q] = corr.val[q];
         }
-        const int b0 = bib_ptr[s];
         for (int q = 0; q < bib.n; ++q) {
-            bib_idx[b0 + q] = bib.idx[q];
-            bib_val[b0 + q] = bib.val[q];
+            tbidx[s * kMaxBib + q] = bib.idx[q];
+            tbval[s * kMaxBib + q] = bib.val[q];
         }
         // Shortley-Weller row of K (Eqs. 2ndorder_coef_mod, A7_mod): the IBI
         // distance replaces the spacing on a solid side, whose term is dropped.
@@ -633,6 +650,30 @@ __global__ void __launch_bounds__(64) k_side(SideArgs S, int* ccount, int* bcoun
             kr[2 + 2 * d] = ip >= 0 ? 0.0 : cc;
         }
         for (int q = 0; q < 7; ++q) krow[7 * s + q] = kr[q];
+    }
+}
+
+// scratch -> CSR (one warp per irregular point), with the FP32 copies
+__global__ void k_side_compact(int64_t n_irr, const int* ccount, const int* bcount, const int32_t* toff,
+                               const double* tval, const int32_t* tbidx, const double* tbval,
+                               const int32_t* corr_ptr, int32_t* corr_off, double* corr_val, float* corr_val32,
+                               const int32_t* bib_ptr, int32_t* bib_idx, double* bib_val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = warp; s < n_irr; s += nwarps) {
+        const int c0 = corr_ptr[s], nc = ccount[s];
+        for (int q = lane; q < nc; q += 32) {
+            const double v = tval[s * kMaxCorr + q];
+            corr_off[c0 + q] = toff[s * kMaxCorr + q];
+            corr_val[c0 + q] = v;
+            corr_val32[c0 + q] = (float)v;
+        }
+        const int b0 = bib_ptr[s], nb = bcount[s];
+        for (int q = lane; q < nb; q += 32) {
+            bib_idx[b0 + q] = tbidx[s * kMaxBib + q];
+            bib_val[b0 + q] = tbval[s * kMaxBib + q];
+        }
     }
 }
 
@@ -680,6 +721,7 @@ cfp_status classify(cfp_ctx* c) {
         g.n[d] = c->n[d];
     }
     g.bodies = c->dbodies;
+    g.bound2 = c->dbound2;
     g.nb = (int)c->bodies.size();
     g.inside = c->fluid_inside;
 
@@ -752,9 +794,19 @@ cfp_status classify(cfp_ctx* c) {
     CFP_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(DevError), c->stream));
     CFP_CUDA(cudaMemsetAsync(c->dtotal + 4, 0, sizeof(long long), c->stream));
     unsigned long long* ndeg = reinterpret_cast<unsigned long long*>(c->dtotal + 4);
+    int32_t* toff = nullptr;
+    double* tval = nullptr;
+    int32_t* tbidx = nullptr;
+    double* tbval = nullptr;
+    CFP_CUDA(cudaMalloc(&toff, sizeof(int32_t) * kMaxCorr * std::max<int64_t>(nirr, 1)));
+    CFP_CUDA(cudaMalloc(&tval, sizeof(double) * kMaxCorr * std::max<int64_t>(nirr, 1)));
+    CFP_CUDA(cudaMalloc(&tbidx, sizeof(int32_t) * kMaxBib * std::max<int64_t>(nirr, 1)));
+    CFP_CUDA(cudaMalloc(&tbval, sizeof(double) * kMaxBib * std::max<int64_t>(nirr, 1)));
+    CFP_CUDA(cudaMalloc(&c->krow, sizeof(double) * 7 * std::max<int64_t>(nirr, 1)));
+    CFP_CUDA(cudaMalloc(&c->krow32, sizeof(float) * 7 * std::max<int64_t>(nirr, 1)));
     if (nirr)
-        k_side<0><<<grid_for(nirr, 64), 64, 0, c->stream>>>(S, cnt, cnt2, nullptr, nullptr, nullptr, nullptr,
-                                                           nullptr, nullptr, nullptr, ndeg, c->derr);
+        k_side<<<grid_for(nirr, 64), 64, 0, c->stream>>>(S, cnt, cnt2, toff, tval, tbidx, tbval, c->krow, ndeg,
+                                                        c->derr);
     if (nirr) c->launches += 1;
     CFP_CUDA(cudaGetLastError());
     DevError he;
@@ -766,6 +818,10 @@ cfp_status classify(cfp_ctx* c) {
     if (he.code) {
         cudaFree(cnt);
         cudaFree(cnt2);
+        cudaFree(toff);
+        cudaFree(tval);
+        cudaFree(tbidx);
+        cudaFree(tbval);
         const int i = he.lin % nx, j = (he.lin / nx) % ny, k = he.lin / (nx * ny);
         const char* why = he.detail == DETAIL_BOXIBI ? "a modified stencil needs an IBI at a box node"
                         : he.detail == DETAIL_FEWPOINTS ? "fewer than three points for a modified operator"
@@ -789,20 +845,21 @@ cfp_status classify(cfp_ctx* c) {
     CFP_CUDA(cudaMalloc(&c->corr_val32, sizeof(float) * std::max<int64_t>(c->n_corr, 1)));
     CFP_CUDA(cudaMalloc(&c->bib_idx, sizeof(int32_t) * std::max<int64_t>(c->n_bib, 1)));
     CFP_CUDA(cudaMalloc(&c->bib_val, sizeof(double) * std::max<int64_t>(c->n_bib, 1)));
-    CFP_CUDA(cudaMalloc(&c->krow, sizeof(double) * 7 * std::max<int64_t>(nirr, 1)));
-    CFP_CUDA(cudaMalloc(&c->krow32, sizeof(float) * 7 * std::max<int64_t>(nirr, 1)));
     if (nirr)
-        k_side<1><<<grid_for(nirr, 64), 64, 0, c->stream>>>(S, nullptr, nullptr, c->corr_ptr, c->corr_off,
-                                                           c->corr_val, c->bib_ptr, c->bib_idx, c->bib_val,
-                                                           c->krow, ndeg, c->derr);
-    if (c->n_corr)
-        k_to_float<<<grid_for(c->n_corr, 256), 256, 0, c->stream>>>(c->corr_val, c->corr_val32, c->n_corr);
+        k_side_compact<<<grid_for(32 * nirr, 256), 256, 0, c->stream>>>(nirr, cnt, cnt2, toff, tval, tbidx, tbval,
+                                                                        c->corr_ptr, c->corr_off, c->corr_val,
+                                                                        c->corr_val32, c->bib_ptr, c->bib_idx,
+                                                                        c->bib_val);
     if (nirr) k_to_float<<<grid_for(7 * nirr, 256), 256, 0, c->stream>>>(c->krow, c->krow32, 7 * nirr);
-    c->launches += (nirr ? 2 : 0) + (c->n_corr ? 1 : 0);
+    c->launches += nirr ? 2 : 0;
     CFP_CUDA(cudaGetLastError());
     CFP_CUDA(cudaStreamSynchronize(c->stream));
     cudaFree(cnt);
     cudaFree(cnt2);
+    cudaFree(toff);
+    cudaFree(tval);
+    cudaFree(tbidx);
+    cudaFree(tbval);
     c->classified = true;
     c->class_status = CFP_OK;
     return CFP_OK;

@@ -124,6 +124,7 @@ struct cfp_ctx {
     double* dcoef64 = nullptr;  // 8 arrays per axis, n[d] each
     float* dcoef32 = nullptr;
     cfp_body* dbodies = nullptr;
+    double* dbound2 = nullptr;  // per body: squared bounding radius with margin
 
     // classification and side data
     bool classified = false;

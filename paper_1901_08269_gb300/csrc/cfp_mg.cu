@@ -47,12 +47,17 @@ __global__ void k_resid7(Grid<T> G, Side<T> S, const uint8_t* __restrict__ type,
     if (i > nx - 2) return;
     const int64_t sy = nx, sz = (int64_t)nx * ny;
     const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
+    // all loads in bounds for an interior node: issue them before the type test
     const uint8_t t = type[l];
+    const T bl = b[l], e0 = e[l], exm = e[l - 1], exp_ = e[l + 1], eym = e[l - sy], eyp = e[l + sy];
+    const T ezm = e[l - sz], ezp = e[l + sz];
+    T dg = G.ax[0].kb[i] + G.ax[1].kb[j] + G.ax[2].kb[k];
+    T cxm = G.ax[0].ka[i], cxp = G.ax[0].kc[i], cym = G.ax[1].ka[j], cyp = G.ax[1].kc[j];
+    T czm = G.ax[2].ka[k], czp = G.ax[2].kc[k];
     if (t != CFP_REGULAR && t != CFP_IRREGULAR) {
         r[l] = T(0);
         return;
     }
-    T dg, cxm, cxp, cym, cyp, czm, czp;
     if (t == CFP_IRREGULAR) {
         const T* kr = S.krow + 7 * (int64_t)S.slot[l];
         dg = kr[0];
@@ -62,18 +67,9 @@ __global__ void k_resid7(Grid<T> G, Side<T> S, const uint8_t* __restrict__ type,
         cyp = kr[4];
         czm = kr[5];
         czp = kr[6];
-    } else {
-        dg = G.ax[0].kb[i] + G.ax[1].kb[j] + G.ax[2].kb[k];
-        cxm = G.ax[0].ka[i];
-        cxp = G.ax[0].kc[i];
-        cym = G.ax[1].ka[j];
-        cyp = G.ax[1].kc[j];
-        czm = G.ax[2].ka[k];
-        czp = G.ax[2].kc[k];
     }
-    const T ke = dg * e[l] + (cxm * e[l - 1] + cxp * e[l + 1]) + (cym * e[l - sy] + cyp * e[l + sy]) +
-                 (czm * e[l - sz] + czp * e[l + sz]);
-    r[l] = b[l] - ke;
+    const T ke = dg * e0 + (cxm * exm + cxp * exp_) + (cym * eym + cyp * eyp) + (czm * ezm + czp * ezp);
+    r[l] = bl - ke;
 }
 
 __device__ __forceinline__ int fine_of(int I, int n) { return min(2 * I, n - 1); }
@@ -123,7 +119,8 @@ __global__ void k_restrict(Transfer<T> X, const uint8_t* __restrict__ ctype, con
     bc[lc] = s / w;
 }
 
-// e_f += P e_c at the fine unknowns
+// e_f += P e_c at the fine unknowns (ilo + 1 is a valid coarse index for
+// every fine node, with weight zero on coincident nodes)
 template <class T>
 __global__ void k_prolong_add(Transfer<T> X, const uint8_t* __restrict__ ftype, const T* __restrict__ ec,
                               T* __restrict__ ef) {
@@ -132,8 +129,6 @@ __global__ void k_prolong_add(Transfer<T> X, const uint8_t* __restrict__ ftype, 
     const int nfx = X.nf[0], nfy = X.nf[1];
     if (i > nfx - 2) return;
     const int64_t l = (int64_t)k * nfx * nfy + (int64_t)j * nfx + i;
-    const uint8_t t = ftype[l];
-    if (t != CFP_REGULAR && t != CFP_IRREGULAR) return;
     const int ncx = X.nc[0], ncy = X.nc[1];
     const int I = X.ax[0].ilo[i], J = X.ax[1].ilo[j], K = X.ax[2].ilo[k];
     const T ax0 = X.ax[0].wlo[i], ax1 = X.ax[0].whi[i];
@@ -141,14 +136,14 @@ __global__ void k_prolong_add(Transfer<T> X, const uint8_t* __restrict__ ftype, 
     const T az0 = X.ax[2].wlo[k], az1 = X.ax[2].whi[k];
     const int64_t csy = ncx, csz = (int64_t)ncx * ncy;
     const int64_t c0 = (int64_t)K * csz + (int64_t)J * csy + I;
-    // whi = 0 on coincident nodes, where index ilo + 1 may be the last node
-    T v = az0 * (ay0 * (ax0 * ec[c0] + (ax1 != T(0) ? ax1 * ec[c0 + 1] : T(0))) +
-                 (ay1 != T(0) ? ay1 * (ax0 * ec[c0 + csy] + (ax1 != T(0) ? ax1 * ec[c0 + csy + 1] : T(0))) : T(0)));
-    if (az1 != T(0))
-        v += az1 * (ay0 * (ax0 * ec[c0 + csz] + (ax1 != T(0) ? ax1 * ec[c0 + csz + 1] : T(0))) +
-                    (ay1 != T(0) ? ay1 * (ax0 * ec[c0 + csz + csy] + (ax1 != T(0) ? ax1 * ec[c0 + csz + csy + 1] : T(0)))
-                                 : T(0)));
-    ef[l] += v;
+    const uint8_t t = ftype[l];
+    const T f0 = ef[l];
+    const T e000 = ec[c0], e001 = ec[c0 + 1], e010 = ec[c0 + csy], e011 = ec[c0 + csy + 1];
+    const T e100 = ec[c0 + csz], e101 = ec[c0 + csz + 1], e110 = ec[c0 + csz + csy], e111 = ec[c0 + csz + csy + 1];
+    if (t != CFP_REGULAR && t != CFP_IRREGULAR) return;
+    const T v = az0 * (ay0 * (ax0 * e000 + ax1 * e001) + ay1 * (ax0 * e010 + ax1 * e011)) +
+                az1 * (ay0 * (ax0 * e100 + ax1 * e101) + ay1 * (ax0 * e110 + ax1 * e111));
+    ef[l] = f0 + v;
 }
 
 // coarse type by injection: box stays box, solid stays solid, fluid -> regular

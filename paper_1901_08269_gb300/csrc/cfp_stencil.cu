@@ -139,8 +139,21 @@ __global__ void __launch_bounds__(kAX* kAY)
 
     T Pm = 0, P0 = 0, Pp = 0, Qm = 0, Q0 = 0, Qp = 0;
     double acc0 = 0.0, acc1 = 0.0;
+    // type byte and dot operand of the next output node (clamped, masked)
+    const int64_t lout0 = (int64_t)k0 * sz + (int64_t)(jin ? j : 1) * sy + ic;
+    uint8_t t_next = type[lout0];
+    T d_next = DOT ? d0[lout0] : T(0);
     for (int kk = k0 - 1; kk <= k1; ++kk) {
         const T c0m = a0m, c0c = a0c, c0p = a0p, c1m = a1m, c1c = a1c, c1p = a1p;
+        // output of this step is plane kk - 1 (from step k0 + 1 on); its type
+        // byte and dot operand were fetched one step earlier
+        const uint8_t t_cur = t_next;
+        const T d_cur = d_next;
+        if (kk >= k0 + 1 && kk < k1) {  // fetch those of plane kk for the next step
+            const int64_t ln = lout0 + (int64_t)(kk - k0) * sz;
+            t_next = type[ln];
+            if (DOT) d_next = d0[ln];
+        }
         if (kk < k1) {  // prefetch plane kk + 1
             p0 += sz;
             p1 += sz;
@@ -174,7 +187,7 @@ __global__ void __launch_bounds__(kAX* kAY)
             const T arz = G.ax[2].ar[k], brz = G.ax[2].br[k], crz = G.ax[2].cr[k];
             T v = az * Pm + P0 + cz * Pp + (arz * Qm + brz * Q0 + crz * Qp);
             const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
-            const uint8_t t = type[l];
+            const uint8_t t = t_cur;
             if (t == CFP_SOLID) {
                 v = 0;
             } else if (t == CFP_IRREGULAR) {
@@ -183,7 +196,7 @@ __global__ void __launch_bounds__(kAX* kAY)
                 for (int e = S.corr_ptr[s]; e < e1; ++e) v += S.corr_val[e] * x[l + S.corr_off[e]];
             }
             y[l] = v;
-            if (DOT >= 1) acc0 += (double)d0[l] * (double)v;
+            if (DOT >= 1) acc0 += (double)d_cur * (double)v;
             if (DOT == 2) acc1 += (double)v * (double)v;
         }
     }
