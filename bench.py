@@ -57,6 +57,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--oracle-n", type=int, default=129)
     ap.add_argument("--oracle-iters", type=int, default=10)
+    ap.add_argument("--workload", default="config3", choices=["config3", "batch"],
+                    help="config3: the 513^3 two-body solve (default); batch: 64 random problems of uneven "
+                         "size solved together")
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--seed", type=int, default=20261203)
     return ap.parse_args()
 
 
@@ -190,11 +195,89 @@ def reference_arm(args):
     return 0
 
 
+# ----------------------------------------------------------- batched arm
+def batch_arm(args):
+    """64 random problems (n in {33,49,65,97,129}, 1-3 spheres/ellipsoids,
+    tanh factors in [1,2], 8-mode source, g = 0) solved together with
+    cfp_solve_batch, mixed precision, multigrid; one step = classification
+    of every problem + the batched solve."""
+    import torch
+
+    from paper_1901_08269_gb300 import cfp
+    from paper_1901_08269_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    probs = []
+    for m in range(args.batch):
+        w = W.random_problem(args.seed + m)
+        ctx = cfp.Context(w.x, w.y, w.z, w.bodies, stream=torch.cuda.Stream())
+        ctx.classify_points()
+        xyz = ctx.ibi_points()
+        f, g = w.fields(torch, "cuda")
+        gi = w.g_at(xyz, torch).contiguous() if ctx.n_ibi else None
+        u = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+        probs.append((w, ctx, f, g, gi, u))
+    torch.cuda.synchronize()
+    prec = cfp.PREC_MIXED if args.precision == "mixed" else cfp.PREC_FP64
+    opts = cfp.default_opts(precision=prec, precond=cfp.PRECOND_MG, mg_smooth=args.mg_smooth,
+                            inner_tol=args.inner_tol)
+    # autotune once per grid size (first problem of each size), then share
+    tuned = {}
+    for w, ctx, f, g, gi, u in probs:
+        n = w.x.size
+        if n not in tuned:
+            tuned[n] = ctx.autotune(f, g, gi, u, tol=args.tol, opts=cfp.default_opts(
+                precision=prec, precond=cfp.PRECOND_MG, inner_tol=args.inner_tol))[0]
+    by_n = {n: (o.mg_smooth, o.inner_tol) for n, o in tuned.items()}
+    # the batch call takes one opts: use the setting tuned for the largest size
+    nmax = max(tuned)
+    opts = tuned[nmax]
+
+    def step():
+        for w, ctx, f, g, gi, u in probs:
+            ctx.classify_points()
+            u.zero_()
+        torch.cuda.synchronize()
+        return cfp.solve_batch([p[1] for p in probs], [p[2] for p in probs], [p[3] for p in probs],
+                               [p[4] for p in probs], [p[5] for p in probs], tol=args.tol, opts=opts)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        infos = step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    # the same problems one after another (no overlap), for comparison
+    t1 = time.perf_counter()
+    for w, ctx, f, g, gi, u in probs:
+        ctx.classify_points()
+        u.zero_()
+        ctx.solve(f, g, gi, u, tol=args.tol, opts=opts)
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t1
+    nodes = sum(p[0].N for p in probs)
+    line = {"metric": "s per batch of %d random immersed-body problems (config 4)" % args.batch, "value": dt,
+            "unit": "s/batch", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": 1000 * dt, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == cfp.PREC_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": "config4-batch%d-seed%d" % (args.batch, args.seed), "total_nodes": nodes,
+                       "sizes": sorted(set(p[0].x.size for p in probs)), "tuned": {str(k): v for k, v in by_n.items()},
+                       "tol": args.tol},
+            "sequential_s": seq, "iterations": [i.iterations for i in infos[:8]], "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+    for p in probs:
+        p[1].close()
+    return 0
+
+
 # --------------------------------------------------------------- GPU arm
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "batch":
+        return batch_arm(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -229,6 +229,39 @@ cfp_status cfp_solve_host(cfp_ctx* ctx, const double* f_host,
                           cfp_info* info);
 
 /*
+ * Solve nprob independent problems at once (batched workload: many grids of
+ * uneven size and geometry).  Problem m is cfp_solve(ctxs[m], f_dev[m],
+ * g_nodes_dev[m], g_ibi_dev[m], u_dev[m], tol, opts, &infos[m]); nthreads
+ * host threads (<= 0: up to 16) take problems from a shared counter, and
+ * each context enqueues on its own stream, so the solves overlap on the
+ * GPU.  Give every context its own stream (cfp_ctx_create's `stream`), or
+ * the solves serialise.  The contexts must be distinct and on the current
+ * device.  g_ibi_dev may be NULL when no problem has IBI points.  Each
+ * result is bitwise the result of a lone cfp_solve.  infos: NULL or nprob
+ * entries.  Returns the first failing problem's status (the others still
+ * run).  Errors: as cfp_solve, plus CFP_EINVAL for NULL or repeated entries.
+ */
+cfp_status cfp_solve_batch(cfp_ctx* const* ctxs, int nprob,
+                           const double* const* f_dev,
+                           const double* const* g_nodes_dev,
+                           const double* const* g_ibi_dev, double* const* u_dev,
+                           double tol, const cfp_opts* opts, int nthreads,
+                           cfp_info* infos);
+
+/*
+ * Autotuner of the solver settings for one problem: times the solve (best
+ * of two runs each) with the multigrid preconditioner and mg_smooth in
+ * {1, 2, 3} and, for CFP_PREC_MIXED, inner_tol in {1e-2, 1e-3, 1e-4}, and
+ * writes the fastest converging setting into *opts (other fields kept) and
+ * its time into *best_ms (NULL allowed).  u_dev is overwritten by the trial
+ * solves.  Arguments otherwise as cfp_solve.  Synchronises.  Errors: as
+ * cfp_solve; CFP_ENOCONV if no candidate converges.
+ */
+cfp_status cfp_autotune(cfp_ctx* ctx, const double* f_dev, const double* g_nodes_dev,
+                        const double* g_ibi_dev, double* u_dev, double tol,
+                        cfp_opts* opts, double* best_ms);
+
+/*
  * cfp_assemble_rhs without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot let a library
  * call cudaMalloc -- for instance applications whose device memory belongs to

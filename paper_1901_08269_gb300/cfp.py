@@ -51,7 +51,8 @@ _D = C.POINTER(C.c_double)
 
 EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_destroy", "cfp_classify_points",
            "cfp_ibi_points", "cfp_assemble_rhs", "cfp_apply", "cfp_precondition", "cfp_solve", "cfp_solve_host",
-           "cfp_time_kernel", "cfp_launch_count", "cfp_assemble_rhs_noalloc", "cfp_precondition_ex"]
+           "cfp_time_kernel", "cfp_launch_count", "cfp_assemble_rhs_noalloc", "cfp_precondition_ex",
+           "cfp_solve_batch", "cfp_autotune"]
 KERNEL_APPLY, KERNEL_RBGS, KERNEL_UPDATE = 0, 1, 2
 
 
@@ -82,6 +83,9 @@ def lib(build_if_missing=True):
         L.cfp_time_kernel.argtypes = [_P, C.c_int, C.c_int, C.c_int, _D, _D]
         L.cfp_assemble_rhs_noalloc.argtypes = [_P, _P, _P, _P, _P]
         L.cfp_precondition_ex.argtypes = [_P, C.POINTER(Opts), _P, _P]
+        L.cfp_solve_batch.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
+                                      C.POINTER(_P), C.c_double, C.POINTER(Opts), C.c_int, C.POINTER(Info)]
+        L.cfp_autotune.argtypes = [_P, _P, _P, _P, _P, C.c_double, C.POINTER(Opts), _D]
         L.cfp_launch_count.argtypes = [_P]
         L.cfp_launch_count.restype = C.c_int64
         for name in EXPORTS[2:]:
@@ -128,6 +132,22 @@ def _ptr(t, dtype=None):
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return C.c_void_p(t.data_ptr())
+
+
+def solve_batch(ctxs, fs, gs, gis, us, tol=1e-12, opts=None, nthreads=0, check=True, **kw):
+    """cfp_solve_batch over lists of contexts and CUDA float64 tensors."""
+    n = len(ctxs)
+    o = opts if opts is not None else default_opts(**kw)
+    arr = lambda ts: (_P * max(n, 1))(*[_P(t.data_ptr()) if t is not None and t.numel() else None for t in ts])
+    hs = (_P * max(n, 1))(*[c._h for c in ctxs])
+    for c, f, g, u in zip(ctxs, fs, gs, us):
+        c._field(f, "f"), c._field(g, "g_nodes"), c._field(u, "u")
+    infos = (Info * max(n, 1))()
+    st = lib().cfp_solve_batch(hs, n, arr(fs), arr(gs), arr(gis), arr(us), float(tol), C.byref(o), int(nthreads),
+                               infos)
+    if check:
+        _check(st, "cfp_solve_batch")
+    return [infos[m] for m in range(n)]
 
 
 class Context:
@@ -233,6 +253,15 @@ class Context:
 
     def launch_count(self):
         return lib().cfp_launch_count(self._h)
+
+    def autotune(self, f, g_nodes, g_ibi, u, tol=1e-12, opts=None, **kw):
+        """cfp_autotune: returns (best Opts, best time in ms)."""
+        o = opts if opts is not None else default_opts(**kw)
+        ms = C.c_double()
+        _check(lib().cfp_autotune(self._h, self._field(f, "f"), self._field(g_nodes, "g_nodes"),
+                                  _ptr(g_ibi) if g_ibi is not None and g_ibi.numel() else None,
+                                  self._field(u, "u"), float(tol), C.byref(o), C.byref(ms)), "cfp_autotune")
+        return o, ms.value
 
     def time_kernel(self, kernel, precision=PREC_FP64, reps=20):
         """Mean device time (ms) of one launch and its algorithmic bytes."""
