@@ -36,6 +36,16 @@ def tanh_grid(a: float, b: float, n: int, beta: float) -> np.ndarray:
     return x
 
 
+def sinh_grid(n: int, beta: float, L: float, H: float, offset: float = 0.0) -> np.ndarray:
+    """Sinh stretching of Sec. 4 (Eqs. p2_y, p2_s): x_j = offset + L (1 +
+    sinh(beta (eta - s)) / sinh(beta s)), eta = j / (n - 1), with
+    s = log((1 + (e^beta - 1) L / H) / (1 + (e^-beta - 1) L / H)) / (2 beta).
+    Nodes cluster around offset + L; the interval is [offset, offset + H]."""
+    eta = np.arange(n, dtype=np.float64) / (n - 1)
+    s = math.log((1.0 + (math.exp(beta) - 1.0) * L / H) / (1.0 + (math.exp(-beta) - 1.0) * L / H)) / (2.0 * beta)
+    return offset + L * (1.0 + np.sinh(beta * (eta - s)) / math.sinh(beta * s))
+
+
 # ---------------------------------------------------------------- bodies
 def rot_z(deg: float) -> np.ndarray:
     t = math.radians(deg)
@@ -224,6 +234,23 @@ def paper_problem1(n: int, bodies=()) -> Workload:
     uniform unit cube."""
     x = uniform_grid(0.0, 1.0, n)
     return Workload("p1-%d^3" % n, x, x.copy(), x.copy(), list(bodies), _p1_u, _p1_f)
+
+
+def interior_sphere(n: int = 41) -> Workload:
+    """Interior problem (fluid inside the body, as in Problem 4 of Sec. 4):
+    a sphere of radius 0.72 centred near the middle of [-1,1]^3,
+    u = exp(-(x^2 + y^2 + z^2)) on it and on Gamma."""
+    x = tanh_grid(-1.0, 1.0, n, 0.8)
+
+    def u(X, Y, Z, xp):
+        return xp.exp(-(X * X + Y * Y + Z * Z))
+
+    def f(X, Y, Z, xp):
+        r2 = X * X + Y * Y + Z * Z
+        return (4.0 * r2 - 6.0) * xp.exp(-r2)
+
+    return Workload("interior-sphere-%d^3" % n, x, x.copy(), x.copy(), [sphere((0.02, -0.01, 0.03), 0.72)], u, f,
+                    fluid_inside=True)
 
 
 def quartic_workload(x, y, z, bodies=(), seed=0, fluid_inside=False) -> Workload:

@@ -39,6 +39,7 @@ CASES = {
     "c3-bodies-65": lambda: W.Workload("c3b", W.tanh_grid(-1, 1, 65, 1.0), W.tanh_grid(-1, 1, 65, 0.6),
                                        W.tanh_grid(-1, 1, 65, 0.6), W.config3_bodies(), W._c3_u, W._c3_f),
     "random-3": lambda: W.random_problem(3, sizes=(33, 49)),
+    "interior-sphere": lambda: W.interior_sphere(41),
     "random-8": lambda: W.random_problem(8, sizes=(33, 49)),
 }
 
@@ -107,7 +108,11 @@ def test_apply_parity(name, zero_off):
     yo = p.P.apply_B(x)
     scale = p.P.apply_B(x, absval=True)
     err = np.abs(y.cpu().numpy() - yo)
-    assert np.all(err <= 1e-13 * scale + 1e-300), np.max(err / (scale + 1e-300))
+    # The GPU forms an irregular row as the regular 27-point row plus the
+    # merged corrections of its modified lines (the split of Eq. Bdec), whose
+    # intermediate terms can exceed the merged coefficients behind |B||x|:
+    # rounding relative to |B||x| is bounded by 1e-12 rather than 1e-13.
+    assert np.all(err <= 1e-12 * scale + 1e-300), np.max(err / (scale + 1e-300))
     nonunk = np.ones(p.w.N, bool)
     nonunk[p.unk] = False
     assert np.all(y.cpu().numpy()[nonunk] == 0.0)

@@ -257,6 +257,41 @@ def test_fourth_order_config2_sphere():
     assert 3.6 < p < 4.3, (errs, p)
 
 
+def test_sinh_grid_matches_eq_p2_and_converges():
+    # Eqs. p2_y / p2_s with beta = 3, L = 0.3, H = 0.6 (Problem 2): the nodes
+    # span [offset, offset + H] and cluster around offset + L.
+    y = W.sinh_grid(65, 3.0, 0.3, 0.6)
+    assert abs(y[0]) < 1e-14 and abs(y[-1] - 0.6) < 1e-12 and np.all(np.diff(y) > 0)
+    dy = np.diff(y)
+    assert np.argmin(dy) in range(25, 40) and dy.max() / dy.min() > 2
+    errs = []
+    for n in (17, 33, 65):
+        x = W.uniform_grid(0.0, 1.0, n)
+        yy = W.sinh_grid(n, 3.0, 0.3, 0.6)
+        w = W.Workload("sinh", x, yy, x.copy(), [], W._p1_u, W._p1_f)
+        P, t, f, g, gi = _setup(w)
+        u, st, it, rel = P.solve(f, g, gi, tol=1e-13)
+        assert st == 0
+        X, Y, Z = w.mesh()
+        errs.append(np.max(np.abs(u - w.u(X, Y, Z, np).reshape(-1))))
+    p = _order(errs[1], errs[2], 33, 65)
+    assert 3.7 < p < 4.4, (errs, p)
+
+
+def test_interior_problem_fourth_order():
+    # fluid inside the body (Problem 4 style)
+    errs = []
+    for n in (25, 33, 49):
+        w = W.interior_sphere(n)
+        P, t, f, g, gi = _setup(w)
+        u, st, it, rel = P.solve(f, g, gi, tol=1e-13)
+        assert st == 0
+        X, Y, Z = w.mesh()
+        errs.append(np.max(np.abs(u - w.u(X, Y, Z, np).reshape(-1))[t != O.SOLID]))
+    p = _order(errs[0], errs[2], 25, 49)
+    assert 3.5 < p < 4.6, (errs, p)
+
+
 def test_flop_extra_formula_reproduces_tables():
     # Eq. flop with iter_prec = 8 and N = n^3 reproduces Tables p1 and p2_flop.
     rows = [l.split() for l in open(os.path.join(GOLDEN, "flop_tables.txt")) if l.strip() and l[0] != "#"]
