@@ -85,7 +85,7 @@ struct DevError {
 enum { DETAIL_OFFGRID = 1, DETAIL_FEWPOINTS = 2, DETAIL_SINGULAR = 3, DETAIL_BOXIBI = 4,
        DETAIL_OVERFLOW = 5, DETAIL_MISSINGIBI = 6 };
 
-constexpr int kAX = 32, kAY = 8;   // apply CTA tile (threads) in x and y
+constexpr int kAX = 128;           // apply CTA: columns (threads) along x
 constexpr int kApplyKC = 32;       // planes per apply CTA
 constexpr int kUpdBlocks = 152 * 8;   // grid of the vector-update kernels
 constexpr int kUpdThreads = 256;
@@ -232,7 +232,8 @@ void launch_rhs_finish(cfp_ctx* c, const double* qf, const double* bg, const dou
 void launch_boundary_lift(cfp_ctx* c, const double* g, double* gb, cudaStream_t s);
 void launch_finish_solution(cfp_ctx* c, const double* x, const double* g, double* u, cudaStream_t s);
 void launch_mask_unknowns(cfp_ctx* c, const double* in, double* out, cudaStream_t s);
-int apply_blocks(cfp_ctx* c);
+int apply_blocks(cfp_ctx* c);  // partial pairs written by one launch_apply
+int corr_blocks(const cfp_ctx* c);
 void launch_metrics(cfp_ctx* c);  // Eq. app_xxx and Eq. 2ndorder_coef per axis
 
 // Krylov (cfp_krylov.cu)

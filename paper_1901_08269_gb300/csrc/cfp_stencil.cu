@@ -84,117 +84,89 @@ __device__ __forceinline__ void block_reduce2(double& a, double& b) {
     }
 }
 
-// B x at the unknowns.  A CTA of kAX x kAY threads owns a kAX x kAY tile of
-// (i, j) columns and marches kApplyKC planes in z.  Per plane, rows j0-1 ..
-// j0+kAY of the tile form the x-pass XR = Rx x, XL = Lx x (shared memory),
-// each thread then forms the y-pass P = Ly XR + Ry XL, Q = Ly XL of its
-// column and keeps P, Q of three planes in registers for the z-pass
+// Regular part of B x at the unknowns.  One thread owns the column (i, j) and marches
+// kApplyKC planes in z.  Per plane it loads the 3 x 3 values x(i-1..i+1,
+// j-1..j+1) (the x and y neighbours come from L1/L2; the loads of the next
+// plane are issued before the current one is used), forms the x-pass
+// XR = Rx x, XL = Lx x of its three rows, the y-pass P = Ly XR + Ry XL,
+// Q = Ly XL, and keeps P, Q of three planes in registers for the z-pass
 //   out(k) = Lz (P(k-1), P(k), P(k+1)) + Rz (Q(k-1), Q(k), Q(k+1)).
-// The loads of the next plane are issued before the current plane is
-// processed (clamped addresses, results masked), so memory latency overlaps
-// the arithmetic and the barriers.  Irregular rows add their side-list
-// corrections; solid rows are zero.
+// No shared memory and no barriers.  Solid rows are zero; the rows of
+// irregular points get their side-list corrections from k_apply_corr.
 // DOT = 0: y only; 1: partial (d0, y); 2: partials (d0, y) and (y, y).
 template <class T, int DOT>
-__global__ void __launch_bounds__(kAX* kAY)
+__global__ void __launch_bounds__(kAX)
     k_apply(Grid<T> G, Side<T> S, const uint8_t* __restrict__ type, const T* __restrict__ x,
             T* __restrict__ y, const T* __restrict__ d0, double* __restrict__ partial) {
-    __shared__ T sR[kAY + 2][kAX];
-    __shared__ T sL[kAY + 2][kAX];
     const int nx = G.nx, ny = G.ny, nz = G.nz;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = 1 + blockIdx.x * kAX + tx;
-    const int j0 = 1 + blockIdx.y * kAY;
-    const int j = j0 + ty;
+    const int i = 1 + blockIdx.x * kAX + threadIdx.x;
+    const int j = 1 + blockIdx.y;
     const int k0 = 1 + blockIdx.z * kApplyKC;
     const int k1 = min(k0 + kApplyKC, nz - 1);
     const bool iin = i <= nx - 2;
-    const bool jin = j <= ny - 2;
+    const int ic = iin ? i : 1;  // clamped: every load stays inside the grid
     const int64_t sy = nx, sz = (int64_t)nx * ny;
-
-    T ax = 0, cx = 0, arx = 0, brx = 0, crx = 0;
-    if (iin) {
-        ax = G.ax[0].a[i];
-        cx = G.ax[0].c[i];
-        arx = G.ax[0].ar[i];
-        brx = G.ax[0].br[i];
-        crx = G.ax[0].cr[i];
+    const T ax = G.ax[0].a[ic], cx = G.ax[0].c[ic];
+    const T arx = G.ax[0].ar[ic], brx = G.ax[0].br[ic], crx = G.ax[0].cr[ic];
+    const T ay = G.ax[1].a[j], cy = G.ax[1].c[j];
+    const T ary = G.ax[1].ar[j], bry = G.ax[1].br[j], cry = G.ax[1].cr[j];
+    const T* p = x + (int64_t)(k0 - 1) * sz + (int64_t)j * sy + ic;
+    T n[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const T* q = p + (r - 1) * sy;
+        n[3 * r] = q[-1];
+        n[3 * r + 1] = q[0];
+        n[3 * r + 2] = q[1];
     }
-    T ay = 0, cy = 0, ary = 0, bry = 0, cry = 0;
-    if (jin) {
-        ay = G.ax[1].a[j];
-        cy = G.ax[1].c[j];
-        ary = G.ax[1].ar[j];
-        bry = G.ax[1].br[j];
-        cry = G.ax[1].cr[j];
-    }
-    // the two x-pass rows this thread loads: ty and (ty < 2) ty + kAY
-    const int ic = iin ? i : 1;
-    const bool v0 = iin && (j0 - 1 + ty) <= ny - 1;
-    const bool v1 = iin && ty < 2 && (j0 - 1 + ty + kAY) <= ny - 1;
-    const T* p0 = x + (int64_t)(k0 - 1) * sz + (int64_t)(v0 ? j0 - 1 + ty : 1) * sy + ic;
-    const T* p1 = x + (int64_t)(k0 - 1) * sz + (int64_t)(v1 ? j0 - 1 + ty + kAY : 1) * sy + ic;
-    T a0m = p0[-1], a0c = p0[0], a0p = p0[1];
-    T a1m = p1[-1], a1c = p1[0], a1p = p1[1];
-
-    T Pm = 0, P0 = 0, Pp = 0, Qm = 0, Q0 = 0, Qp = 0;
-    double acc0 = 0.0, acc1 = 0.0;
-    // type byte and dot operand of the next output node (clamped, masked)
-    const int64_t lout0 = (int64_t)k0 * sz + (int64_t)(jin ? j : 1) * sy + ic;
+    // type byte and dot operand of the next output node
+    const int64_t lout0 = (int64_t)k0 * sz + (int64_t)j * sy + ic;
     uint8_t t_next = type[lout0];
     T d_next = DOT ? d0[lout0] : T(0);
+    T Pm = 0, P0 = 0, Pp = 0, Qm = 0, Q0 = 0, Qp = 0;
+    double acc0 = 0.0, acc1 = 0.0;
     for (int kk = k0 - 1; kk <= k1; ++kk) {
-        const T c0m = a0m, c0c = a0c, c0p = a0p, c1m = a1m, c1c = a1c, c1p = a1p;
+        T c[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) c[q] = n[q];
+        if (kk < k1) {  // prefetch plane kk + 1
+            p += sz;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const T* q = p + (r - 1) * sy;
+                n[3 * r] = q[-1];
+                n[3 * r + 1] = q[0];
+                n[3 * r + 2] = q[1];
+            }
+        }
         // output of this step is plane kk - 1 (from step k0 + 1 on); its type
         // byte and dot operand were fetched one step earlier
         const uint8_t t_cur = t_next;
         const T d_cur = d_next;
-        if (kk >= k0 + 1 && kk < k1) {  // fetch those of plane kk for the next step
+        if (kk >= k0 + 1 && kk < k1) {
             const int64_t ln = lout0 + (int64_t)(kk - k0) * sz;
             t_next = type[ln];
             if (DOT) d_next = d0[ln];
         }
-        if (kk < k1) {  // prefetch plane kk + 1
-            p0 += sz;
-            p1 += sz;
-            a0m = p0[-1];
-            a0c = p0[0];
-            a0p = p0[1];
-            a1m = p1[-1];
-            a1c = p1[0];
-            a1p = p1[1];
+        T XR[3], XL[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            XR[r] = arx * c[3 * r] + brx * c[3 * r + 1] + crx * c[3 * r + 2];
+            XL[r] = ax * c[3 * r] + c[3 * r + 1] + cx * c[3 * r + 2];
         }
-        sR[ty][tx] = v0 ? arx * c0m + brx * c0c + crx * c0p : T(0);
-        sL[ty][tx] = v0 ? ax * c0m + c0c + cx * c0p : T(0);
-        if (ty < 2) {
-            sR[ty + kAY][tx] = v1 ? arx * c1m + brx * c1c + crx * c1p : T(0);
-            sL[ty + kAY][tx] = v1 ? ax * c1m + c1c + cx * c1p : T(0);
-        }
-        __syncthreads();
-        const T P = ay * sR[ty][tx] + sR[ty + 1][tx] + cy * sR[ty + 2][tx] + ary * sL[ty][tx] +
-                    bry * sL[ty + 1][tx] + cry * sL[ty + 2][tx];
-        const T Q = ay * sL[ty][tx] + sL[ty + 1][tx] + cy * sL[ty + 2][tx];
-        __syncthreads();
         Pm = P0;
         P0 = Pp;
-        Pp = P;
         Qm = Q0;
         Q0 = Qp;
-        Qp = Q;
-        if (kk >= k0 + 1 && iin && jin) {
+        Pp = ay * XR[0] + XR[1] + cy * XR[2] + ary * XL[0] + bry * XL[1] + cry * XL[2];
+        Qp = ay * XL[0] + XL[1] + cy * XL[2];
+        if (kk >= k0 + 1 && iin) {
             const int k = kk - 1;
             const T az = G.ax[2].a[k], cz = G.ax[2].c[k];
             const T arz = G.ax[2].ar[k], brz = G.ax[2].br[k], crz = G.ax[2].cr[k];
             T v = az * Pm + P0 + cz * Pp + (arz * Qm + brz * Q0 + crz * Qp);
             const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
-            const uint8_t t = t_cur;
-            if (t == CFP_SOLID) {
-                v = 0;
-            } else if (t == CFP_IRREGULAR) {
-                const int s = S.slot[l];
-                const int e1 = S.corr_ptr[s + 1];
-                for (int e = S.corr_ptr[s]; e < e1; ++e) v += S.corr_val[e] * x[l + S.corr_off[e]];
-            }
+            if (t_cur == CFP_SOLID) v = 0;  // irregular rows: k_apply_corr adds their corrections
             y[l] = v;
             if (DOT >= 1) acc0 += (double)d_cur * (double)v;
             if (DOT == 2) acc1 += (double)v * (double)v;
@@ -202,10 +174,46 @@ __global__ void __launch_bounds__(kAX* kAY)
     }
     if (DOT) {
         block_reduce2(acc0, acc1);
-        if (tx == 0 && ty == 0) {
+        if (threadIdx.x == 0) {
             const int64_t b = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
             partial[2 * b] = acc0;
             partial[2 * b + 1] = acc1;
+        }
+    }
+}
+
+// Side-list corrections of the irregular rows (the modified stencils of
+// Secs. 2.2-2.3, the C part of Eq. Bdec), one warp per irregular point: the
+// lanes gather the merged entries in parallel, lane 0 adds the sum to y and
+// updates the dot partials: (d0, y) gains d0 c, (y, y) gains 2 v c + c^2
+// where v is the row's regular part.  Partials are written after those of
+// k_apply, one pair per CTA.
+template <class T, int DOT>
+__global__ void __launch_bounds__(256)
+    k_apply_corr(Side<T> S, const int32_t* __restrict__ irr_lin, int64_t n_irr, const T* __restrict__ x,
+                 T* __restrict__ y, const T* __restrict__ d0, double* __restrict__ partial) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int64_t s = warp; s < n_irr; s += nwarps) {
+        const int64_t l = irr_lin[s];
+        const int e0 = S.corr_ptr[s], e1 = S.corr_ptr[s + 1];
+        T c = T(0);
+        for (int e = e0 + lane; e < e1; e += 32) c += S.corr_val[e] * x[l + S.corr_off[e]];
+        for (int o = 16; o; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        if (lane == 0) {
+            const T v = y[l];
+            y[l] = v + c;
+            if (DOT >= 1) acc0 += (double)d0[l] * (double)c;
+            if (DOT == 2) acc1 += 2.0 * (double)v * (double)c + (double)c * (double)c;
+        }
+    }
+    if (DOT) {
+        block_reduce2(acc0, acc1);
+        if (threadIdx.x == 0) {
+            partial[2 * blockIdx.x] = acc0;
+            partial[2 * blockIdx.x + 1] = acc1;
         }
     }
 }
@@ -384,7 +392,7 @@ template void launch_half_sweep<float>(const Grid<float>&, const Side<float>&, c
 namespace {
 
 dim3 apply_grid(const cfp_ctx* c) {
-    return dim3((unsigned)((c->n[0] - 2 + kAX - 1) / kAX), (unsigned)((c->n[1] - 2 + kAY - 1) / kAY),
+    return dim3((unsigned)((c->n[0] - 2 + kAX - 1) / kAX), (unsigned)(c->n[1] - 2),
                 (unsigned)((c->n[2] - 2 + kApplyKC - 1) / kApplyKC));
 }
 
@@ -400,23 +408,37 @@ void launch_metrics(cfp_ctx* c) {
     c->launches += 3;
 }
 
+// CTAs of the correction kernel (8 irregular points per CTA, at most 152 x 16)
+int corr_blocks(const cfp_ctx* c) {
+    if (c->n_irr <= 0) return 0;
+    return (int)std::min<int64_t>((c->n_irr + 7) / 8, 152 * 16);
+}
+
 int apply_blocks(cfp_ctx* c) {
     const dim3 g = apply_grid(c);
-    return (int)(g.x * g.y * g.z);
+    return (int)(g.x * g.y * g.z) + corr_blocks(c);
 }
 
 template <class T>
 void launch_apply(cfp_ctx* c, const T* x, T* y, const T* d0, int dotmode, double* partial, cudaStream_t s,
                   int* nblocks_out) {
     const dim3 grid = apply_grid(c);
-    const dim3 block(kAX, kAY);
+    const dim3 block(kAX);
     const Grid<T> G = grid_view<T>(c);
     const Side<T> S = side_view<T>(c);
     if (dotmode == 0) k_apply<T, 0><<<grid, block, 0, s>>>(G, S, c->type, x, y, d0, partial);
     else if (dotmode == 1) k_apply<T, 1><<<grid, block, 0, s>>>(G, S, c->type, x, y, d0, partial);
     else k_apply<T, 2><<<grid, block, 0, s>>>(G, S, c->type, x, y, d0, partial);
-    c->launches += 1;
-    if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+    const int nmain = (int)(grid.x * grid.y * grid.z);
+    const int ncorr = corr_blocks(c);
+    double* pc = partial ? partial + 2 * (int64_t)nmain : nullptr;
+    if (ncorr) {
+        if (dotmode == 0) k_apply_corr<T, 0><<<ncorr, 256, 0, s>>>(S, c->irr_lin, c->n_irr, x, y, d0, pc);
+        else if (dotmode == 1) k_apply_corr<T, 1><<<ncorr, 256, 0, s>>>(S, c->irr_lin, c->n_irr, x, y, d0, pc);
+        else k_apply_corr<T, 2><<<ncorr, 256, 0, s>>>(S, c->irr_lin, c->n_irr, x, y, d0, pc);
+    }
+    c->launches += ncorr ? 2 : 1;
+    if (nblocks_out) *nblocks_out = nmain + ncorr;
 }
 
 template <>
