@@ -375,22 +375,27 @@ def main():
         del u64
 
     # roofline of the dominant kernel: a red-black half-sweep of the
-    # preconditioner, in the precision of the inner solve
+    # preconditioner (the multigrid smoother on the fine level, or the plain
+    # inner iterations), in the precision of the inner solve
     kprec = prec
     kern = {}
-    for name, kid in (("rbgs_half", cfp.KERNEL_RBGS), ("apply", cfp.KERNEL_APPLY), ("update", cfp.KERNEL_UPDATE)):
+    for name, kid in (("mg_half", cfp.KERNEL_MG_SWEEP), ("rbgs_half", cfp.KERNEL_RBGS),
+                      ("apply", cfp.KERNEL_APPLY), ("update", cfp.KERNEL_UPDATE)):
         kms, kbytes = ctx.time_kernel(kid, kprec, reps=20)
         kern[name] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6}
     peak, psrc = hbm_peak()
-    dom = kern["rbgs_half"]
+    tname = "float" if kprec == cfp.PREC_MIXED else "double"
+    if pc == cfp.PRECOND_MG:
+        dom, kname, src = kern["mg_half"], "k_sweep_split<%s> half-sweep" % tname, "cfp_mg.cu"
+    else:
+        dom, kname, src = kern["rbgs_half"], "k_rbgs<%s> half-sweep" % tname, "cfp_stencil.cu"
     roofline = {"bound": "hbm", "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
-                "frac": dom["gbs"] / peak, "traffic": None, "kernel": "k_rbgs<%s> half-sweep" %
-                ("float" if kprec == cfp.PREC_MIXED else "double"), "peak_source": psrc}
+                "frac": dom["gbs"] / peak, "traffic": None, "kernel": kname, "peak_source": psrc}
     tr = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tr):
         try:
-            d = json.load(open(tr)).get(roofline["kernel"])
-            if d and d.get("stencil_sha") == _src_hash():
+            d = json.load(open(tr)).get(kname)
+            if d and d.get("source_sha") == _src_hash(src):
                 roofline["traffic"] = d["bytes_per_interior_node"] * (args.n - 2) ** 3
         except Exception:
             pass
@@ -445,9 +450,9 @@ def main():
     return 0
 
 
-def _src_hash():
+def _src_hash(name):
     import hashlib
-    p = os.path.join(ROOT, "paper_1901_08269_gb300", "csrc", "cfp_stencil.cu")
+    p = os.path.join(ROOT, "paper_1901_08269_gb300", "csrc", name)
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 

@@ -285,12 +285,17 @@ cfp_status cfp_assemble_rhs_noalloc(cfp_ctx* ctx, const double* f_dev,
  * counted once per executed iteration).  0 for NULL. */
 int64_t cfp_launch_count(const cfp_ctx* ctx);
 
-enum { CFP_KERNEL_APPLY = 0,   /* B x with the fused (r_hat0, v) dot, as in
-                                  Algorithm 1 line 5                         */
-       CFP_KERNEL_RBGS = 1,    /* one red-black Gauss-Seidel sweep (both
-                                  colours, one fused kernel)                 */
-       CFP_KERNEL_UPDATE = 2   /* the fused x/r update with two dots (lines
-                                  11-12)                                     */ };
+enum { CFP_KERNEL_APPLY = 0,    /* B x with the fused (r_hat0, v) dot, as in
+                                   Algorithm 1 line 5                        */
+       CFP_KERNEL_RBGS = 1,     /* one red half-sweep of red-black Gauss-Seidel
+                                   on K (Eq. A7), natural node order: the
+                                   inner iterations of Sec. 3.3              */
+       CFP_KERNEL_UPDATE = 2,   /* the fused x/r update with two dots (lines
+                                   11-12)                                    */
+       CFP_KERNEL_MG_SWEEP = 3  /* one red half-sweep on the fine level of the
+                                   multigrid preconditioner (CFP_PRECOND_MG),
+                                   red and black nodes stored in separate
+                                   arrays                                    */ };
 
 /*
  * Profiling aid: time `reps` >= 1 back-to-back launches of one kernel of the
@@ -299,10 +304,10 @@ enum { CFP_KERNEL_APPLY = 0,   /* B x with the fused (r_hat0, v) dot, as in
  * context's own work vectors (their contents are overwritten).
  *   ms_per_launch     host pointer: mean device time of one launch
  *   bytes_per_launch  host pointer or NULL: algorithmic bytes of one launch
- *                     (minimum traffic: per unknown, apply 3 values (x, y
- *                     and the dot operand), sweep 2.5 values (rho, the new
- *                     phi and the black half of the previous phi), update
- *                     8 values over all nodes)
+ *                     (minimum traffic: per interior node, apply 3 values
+ *                     (x, y and the dot operand); a half-sweep 1.5 values
+ *                     (rho and the new phi of its colour, phi of the other
+ *                     colour); update 8 values over all nodes)
  * Requires classification.  Synchronises.  Errors: CFP_ESTATE, CFP_EINVAL,
  * CFP_ECUDA.
  */

@@ -53,7 +53,7 @@ EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_dest
            "cfp_ibi_points", "cfp_assemble_rhs", "cfp_apply", "cfp_precondition", "cfp_solve", "cfp_solve_host",
            "cfp_time_kernel", "cfp_launch_count", "cfp_assemble_rhs_noalloc", "cfp_precondition_ex",
            "cfp_solve_batch", "cfp_autotune"]
-KERNEL_APPLY, KERNEL_RBGS, KERNEL_UPDATE = 0, 1, 2
+KERNEL_APPLY, KERNEL_RBGS, KERNEL_UPDATE, KERNEL_MG_SWEEP = 0, 1, 2, 3
 
 
 def library_path():

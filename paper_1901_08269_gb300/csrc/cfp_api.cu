@@ -261,7 +261,7 @@ cfp_status cfp_precondition_ex(cfp_ctx* c, const cfp_opts* o, const double* rho,
     if (phi == c->v64 + (int64_t)V_TMP2 * c->N) return fail(CFP_EINVAL, "phi aliases the context's work space");
     c->precond_kind = opts.precond;
     c->mg_smooth = std::max(1, opts.mg_smooth);
-    if (c->precond_kind == CFP_PRECOND_MG) CFP_TRY(ensure_mg(c));
+    if (c->precond_kind == CFP_PRECOND_MG) CFP_TRY(ensure_mg(c, 0));
     CFP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * c->N, c->stream));
     launch_precond<double>(c, opts.sweeps, rho, phi, c->stream);
     c->precond_kind = CFP_PRECOND_RBGS;

@@ -98,9 +98,14 @@ struct MgLevel {
     std::vector<double> X[3];
     double* coef64 = nullptr;  // 8 arrays per axis (only ka, kb, kc used)
     float* coef32 = nullptr;
-    uint8_t* type = nullptr;
-    double* v64 = nullptr;     // e, b, r
-    float* v32 = nullptr;
+    uint8_t* type = nullptr;   // natural layout (levels >= 1; level 0 uses the context's)
+    // red-black split layout: node (i, j, k) of colour (i + j + k) & 1 sits at
+    // entry (k * n[1] + j) * hp + (i >> 1) of its colour's array
+    int hp = 0;                // entries per row of one colour, padded to 8
+    int64_t Nh = 0;            // entries per colour array: hp * n[1] * n[2]
+    uint8_t* stype = nullptr;  // split type, colour c at stype + c * Nh
+    double* s64 = nullptr;     // split e0 e1 b0 b1 r0 (Nh each), FP64
+    float* s32 = nullptr;      // the same in FP32
     int* ilo[3] = {nullptr, nullptr, nullptr};  // interpolation from the next coarser level
     int64_t off[3] = {0, 0, 0};
     double* w64 = nullptr;
@@ -222,10 +227,13 @@ template <>
 float* precond_tmp<float>(cfp_ctx* c);
 
 // multigrid (cfp_mg.cu)
-cfp_status ensure_mg(cfp_ctx* c);
+cfp_status ensure_mg(cfp_ctx* c, int prec);  // prec: 0 FP64 vectors, 1 FP32 vectors
 void free_mg(cfp_ctx* c);
 template <class T>
 void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s);
+// one plain red half-sweep on the fine level's split vectors (timing aid)
+template <class T>
+void launch_mg_half_sweep(cfp_ctx* c, cudaStream_t s);
 void launch_qf(cfp_ctx* c, const double* f, double* out, cudaStream_t s);
 void launch_rhs_finish(cfp_ctx* c, const double* qf, const double* bg, const double* g_ibi,
                        double* rhs, cudaStream_t s);

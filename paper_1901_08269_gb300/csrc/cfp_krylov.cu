@@ -423,6 +423,7 @@ cfp_status time_kernel_t(cfp_ctx* c, int prec, int kernel, int reps, double* ms,
     auto launch = [&]() {
         if (kernel == CFP_KERNEL_APPLY) launch_apply<T>(c, V.ph, V.v, V.rh, 1, c->partial, c->stream, nullptr);
         else if (kernel == CFP_KERNEL_RBGS) launch_rbgs_half<T>(c, V.p, V.ph, c->stream);
+        else if (kernel == CFP_KERNEL_MG_SWEEP) launch_mg_half_sweep<T>(c, c->stream);
         else
             k_update_xr<T><<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(V.x, V.r, V.ph, V.sh, V.s, V.t, V.rh, st,
                                                                       c->partial, c->N);
@@ -444,16 +445,17 @@ cfp_status time_kernel_t(cfp_ctx* c, int prec, int kernel, int reps, double* ms,
     const double w = (double)sizeof(T);
     if (bytes)
         *bytes = kernel == CFP_KERNEL_APPLY ? 3.0 * w * nint
-               : kernel == CFP_KERNEL_RBGS ? 1.5 * w * nint
+               : kernel == CFP_KERNEL_RBGS || kernel == CFP_KERNEL_MG_SWEEP ? 1.5 * w * nint
                                            : 8.0 * w * (double)c->N;
     return CFP_OK;
 }
 }  // namespace
 
 cfp_status time_kernel(cfp_ctx* c, int kernel, int prec, int reps, double* ms, double* bytes) {
-    if (kernel < CFP_KERNEL_APPLY || kernel > CFP_KERNEL_UPDATE || reps < 1 || !ms)
+    if (kernel < CFP_KERNEL_APPLY || kernel > CFP_KERNEL_MG_SWEEP || reps < 1 || !ms)
         return fail(CFP_EINVAL, "bad kernel id, reps or output pointer");
     CFP_TRY(ensure_work(c, prec == CFP_PREC_MIXED));
+    if (kernel == CFP_KERNEL_MG_SWEEP) CFP_TRY(ensure_mg(c, prec == CFP_PREC_MIXED ? 1 : 0));
     return prec == CFP_PREC_MIXED ? time_kernel_t<float>(c, 1, kernel, reps, ms, bytes)
                                   : time_kernel_t<double>(c, 0, kernel, reps, ms, bytes);
 }
@@ -480,8 +482,8 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
         return fail(CFP_EINVAL, "unknown preconditioner");
     c->precond_kind = opts.precond;
     c->mg_smooth = std::max(1, opts.mg_smooth);
-    if (c->precond_kind == CFP_PRECOND_MG) CFP_TRY(ensure_mg(c));
     const bool mixed = opts.precision == CFP_PREC_MIXED;
+    if (c->precond_kind == CFP_PRECOND_MG) CFP_TRY(ensure_mg(c, mixed ? 1 : 0));
     CFP_TRY(ensure_work(c, mixed));
     const int64_t N = c->N;
     double* rhs = c->v64 + V_RHS * N;

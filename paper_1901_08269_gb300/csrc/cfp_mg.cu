@@ -13,9 +13,22 @@
 // its solid neighbours enter with value zero (Dirichlet at the node, no
 // Shortley-Weller distance).  Prolongation is trilinear in the coordinates;
 // restriction is its transpose normalised by the weight sums (full
-// weighting).  Smoother: red-black Gauss-Seidel half-sweeps (the same kernel
-// as the plain inner iterations), mg_smooth sweeps before and after, 16 on
-// the coarsest level.
+// weighting).  Smoother: red-black Gauss-Seidel, mg_smooth sweeps (red then
+// black) before and after the coarse correction, 16 on the coarsest level.
+//
+// Storage: every level keeps its vectors in a red-black split layout (each
+// colour in its own array, rows of (n_x + 1) / 2 entries padded to 8), so a
+// half-sweep reads the other colour and writes its own without moving the
+// unused half of each cache line.  The fine level converts on the way in
+// (the first red half-sweep reads rho in the natural layout and stores both
+// colours of it) and on the way out (the last black half-sweep writes both
+// colours of phi in the natural layout).
+//
+// Two exact shortcuts of red-black smoothing: after a sweep ends with the
+// black half, the residual of every black row is zero (that half-sweep just
+// solved those rows), so only red residuals are formed and restricted; and a
+// red half-sweep overwrites every red value without reading it, so the
+// coarse correction is only added to the black nodes.
 #include <algorithm>
 #include <vector>
 
@@ -24,8 +37,10 @@
 namespace cfp {
 namespace {
 
+constexpr int kSplitThreads = 128;
+
 template <class T>
-struct Interp {       // per axis: fine node i = wlo * coarse[ilo] + whi * coarse[ilo + 1]
+struct Interp {  // per axis: fine node i = wlo * coarse[ilo] + whi * coarse[ilo + 1]
     const int* ilo;
     const T* wlo;
     const T* whi;
@@ -34,31 +49,29 @@ struct Interp {       // per axis: fine node i = wlo * coarse[ilo] + whi * coars
 template <class T>
 struct Transfer {
     Interp<T> ax[3];
-    int nf[3], nc[3];
 };
 
-// r = b - K e at the unknowns of a level, 0 at its other interior nodes.
+// one level in the split layout
 template <class T>
-__global__ void k_resid7(Grid<T> G, Side<T> S, const uint8_t* __restrict__ type, const T* __restrict__ b,
-                         const T* __restrict__ e, T* __restrict__ r) {
-    const int nx = G.nx, ny = G.ny;
-    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y, k = 1 + blockIdx.z;
-    if (i > nx - 2) return;
-    const int64_t sy = nx, sz = (int64_t)nx * ny;
-    const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
-    // all loads in bounds for an interior node: issue them before the type test
-    const uint8_t t = type[l];
-    const T bl = b[l], e0 = e[l], exm = e[l - 1], exp_ = e[l + 1], eym = e[l - sy], eyp = e[l + sy];
-    const T ezm = e[l - sz], ezp = e[l + sz];
-    T dg = G.ax[0].kb[i] + G.ax[1].kb[j] + G.ax[2].kb[k];
-    T cxm = G.ax[0].ka[i], cxp = G.ax[0].kc[i], cym = G.ax[1].ka[j], cyp = G.ax[1].kc[j];
-    T czm = G.ax[2].ka[k], czp = G.ax[2].kc[k];
-    if (t != CFP_REGULAR && t != CFP_IRREGULAR) {
-        r[l] = T(0);
-        return;
-    }
+struct SLev {
+    Grid<T> G;           // coefficients (ka, kb, kc) and sizes
+    const uint8_t* ty;   // split type, colour c at ty + c * Nh
+    T* v;                // e0 e1 b0 b1 r0, Nh each
+    int hp;
+    int64_t Nh;
+};
+
+enum { E0 = 0, E1 = 1, B0 = 2, B1 = 3, R0 = 4, kSplitVecs = 5 };
+
+__device__ __forceinline__ bool is_unknown(uint8_t t) { return t == CFP_REGULAR || t == CFP_IRREGULAR; }
+
+// K's row at (i, j, k): diagonal and the six neighbour weights (x-, x+, y-,
+// y+, z-, z+); Shortley-Weller rows come from the fine level's krow table.
+template <class T>
+__device__ __forceinline__ void k_row(const Grid<T>& G, const Side<T>& S, uint8_t t, int i, int j, int k,
+                                      T& dg, T& cxm, T& cxp, T& cym, T& cyp, T& czm, T& czp) {
     if (t == CFP_IRREGULAR) {
+        const int64_t l = ((int64_t)k * G.ny + j) * G.nx + i;
         const T* kr = S.krow + 7 * (int64_t)S.slot[l];
         dg = kr[0];
         cxm = kr[1];
@@ -67,12 +80,110 @@ __global__ void k_resid7(Grid<T> G, Side<T> S, const uint8_t* __restrict__ type,
         cyp = kr[4];
         czm = kr[5];
         czp = kr[6];
+    } else {
+        dg = G.ax[0].kb[i] + G.ax[1].kb[j] + G.ax[2].kb[k];
+        cxm = G.ax[0].ka[i];
+        cxp = G.ax[0].kc[i];
+        cym = G.ax[1].ka[j];
+        cyp = G.ax[1].kc[j];
+        czm = G.ax[2].ka[k];
+        czp = G.ax[2].kc[k];
     }
-    const T ke = dg * e0 + (cxm * exm + cxp * exp_) + (cym * eym + cyp * eyp) + (czm * ezm + czp * ezp);
-    r[l] = bl - ke;
 }
 
-__device__ __forceinline__ int fine_of(int I, int n) { return min(2 * I, n - 1); }
+// x * (1 / d) with a correctly rounded reciprocal: two roundings instead of
+// the division's one, several times cheaper than an IEEE division.
+__device__ __forceinline__ float times_rcp(float x, float d) { return x * __frcp_rn(d); }
+__device__ __forceinline__ double times_rcp(double x, double d) { return x * __drcp_rn(d); }
+
+// One red-black half-sweep of colour `colour` on a split level.  Thread
+// (m, j, k) owns the pair of nodes i = 2m, 2m + 1 of row (j, k); its node of
+// this colour is i = 2m + par.  Its x-neighbours (the other colour) sit at
+// entries m - 1 + par and m + par of the other colour's row.  Every load is
+// in bounds for every thread that passes the first test (rows j, k and the
+// pair are interior, entry m - 1 exists for m = 0 because the row is not the
+// first), so all of them are issued before the type decides whether the
+// value is stored.
+// MODE 0: plain; 1: from zero (the other colour is taken as zero);
+// 2: from zero, and b of both colours is first read from the natural-layout
+//    rho; 3: plain, and both nodes of the pair are written to the
+//    natural-layout phi (the own node's new value is not stored).
+template <class T, int MODE>
+__global__ void __launch_bounds__(kSplitThreads)
+    k_sweep_split(SLev<T> L, Side<T> S, int colour, const T* __restrict__ rho, T* __restrict__ phi) {
+    const int nx = L.G.nx, ny = L.G.ny;
+    const int m = blockIdx.x * kSplitThreads + threadIdx.x;
+    const int j = 1 + blockIdx.y, k = 1 + blockIdx.z;
+    if (2 * m > nx - 2) return;
+    const int par = (colour + j + k) & 1;
+    const int i = 2 * m + par, io = 2 * m + 1 - par;
+    const int hp = L.hp;
+    const int64_t hs = (int64_t)hp * ny;
+    const int64_t o = (int64_t)k * hs + (int64_t)j * hp + m;
+    const int64_t Nh = L.Nh;
+    T* __restrict__ eown = L.v + (E0 + colour) * Nh;
+    const T* __restrict__ eoth = L.v + (E1 - colour) * Nh;
+    T* __restrict__ bown = L.v + (B0 + colour) * Nh;
+    const int64_t row = ((int64_t)k * ny + j) * nx;
+    const uint8_t t = L.ty[colour * Nh + o];
+    const T bv = MODE == 2 ? rho[row + i] : bown[o];
+    T xm = T(0), xp = T(0), ym = T(0), yp = T(0), zm = T(0), zp = T(0);
+    if (MODE == 0 || MODE == 3) {
+        xm = eoth[o - 1 + par];
+        xp = eoth[o + par];
+        ym = eoth[o - hp];
+        yp = eoth[o + hp];
+        zm = eoth[o - hs];
+        zp = eoth[o + hs];
+    }
+    T dg = L.G.ax[0].kb[i] + L.G.ax[1].kb[j] + L.G.ax[2].kb[k];
+    T cxm = L.G.ax[0].ka[i], cxp = L.G.ax[0].kc[i], cym = L.G.ax[1].ka[j], cyp = L.G.ax[1].kc[j];
+    T czm = L.G.ax[2].ka[k], czp = L.G.ax[2].kc[k];
+    if (MODE == 2) {
+        bown[o] = bv;
+        L.v[(B1 - colour) * Nh + o] = rho[row + io];
+    }
+    const bool live = i >= 1 && i <= nx - 2 && is_unknown(t);
+    if (t == CFP_IRREGULAR) k_row(L.G, S, t, i, j, k, dg, cxm, cxp, cym, cyp, czm, czp);
+    T v = bv;
+    if (MODE == 0 || MODE == 3)
+        v -= (cxm * xm + cxp * xp) + (cym * ym + cyp * yp) + (czm * zm + czp * zp);
+    v = times_rcp(v, dg);
+    if (MODE == 3) {
+        if (i >= 1 && i <= nx - 2) phi[row + i] = live ? v : T(0);
+        if (io >= 1 && io <= nx - 2) phi[row + io] = par ? xm : xp;  // the other node of the pair
+        return;
+    }
+    if (live) eown[o] = v;
+}
+
+// r0 = b0 - K e at the red unknowns (black residuals are zero after a
+// black half-sweep; r0 stays zero at the other red entries).  Loads are
+// issued before the type test, as in the half-sweep.
+template <class T>
+__global__ void __launch_bounds__(kSplitThreads) k_resid_split(SLev<T> L, Side<T> S) {
+    const int nx = L.G.nx, ny = L.G.ny;
+    const int m = blockIdx.x * kSplitThreads + threadIdx.x;
+    const int j = 1 + blockIdx.y, k = 1 + blockIdx.z;
+    if (2 * m > nx - 2) return;
+    const int par = (j + k) & 1;
+    const int i = 2 * m + par;
+    const int hp = L.hp;
+    const int64_t hs = (int64_t)hp * ny;
+    const int64_t o = (int64_t)k * hs + (int64_t)j * hp + m;
+    const int64_t Nh = L.Nh;
+    const T* __restrict__ e1 = L.v + E1 * Nh;
+    const uint8_t t = L.ty[o];
+    const T e0 = L.v[o], b0 = L.v[B0 * Nh + o];
+    const T xm = e1[o - 1 + par], xp = e1[o + par], ym = e1[o - hp], yp = e1[o + hp], zm = e1[o - hs], zp = e1[o + hs];
+    T dg = L.G.ax[0].kb[i] + L.G.ax[1].kb[j] + L.G.ax[2].kb[k];
+    T cxm = L.G.ax[0].ka[i], cxp = L.G.ax[0].kc[i], cym = L.G.ax[1].ka[j], cyp = L.G.ax[1].kc[j];
+    T czm = L.G.ax[2].ka[k], czp = L.G.ax[2].kc[k];
+    if (i < 1 || i > nx - 2 || !is_unknown(t)) return;
+    if (t == CFP_IRREGULAR) k_row(L.G, S, t, i, j, k, dg, cxm, cxp, cym, cyp, czm, czp);
+    const T ke = dg * e0 + (cxm * xm + cxp * xp) + (cym * ym + cyp * yp) + (czm * zm + czp * zp);
+    L.v[R0 * Nh + o] = b0 - ke;
+}
 
 template <class T>
 __device__ __forceinline__ T weight_to(const Interp<T>& A, int i, int I) {
@@ -80,73 +191,82 @@ __device__ __forceinline__ T weight_to(const Interp<T>& A, int i, int I) {
     return (lo == I ? A.wlo[i] : T(0)) + (lo + 1 == I ? A.whi[i] : T(0));
 }
 
-// b_c = (P^T r_f) / (P^T 1) at the coarse unknowns
+// b_c = (P^T r_f) / (P^T 1) at the coarse unknowns; r_f is the fine red
+// residual (zero on black nodes).  One thread per coarse node (I, J, K);
+// interior coarse nodes sit on fine node (2I, 2J, 2K).
 template <class T>
-__global__ void k_restrict(Transfer<T> X, const uint8_t* __restrict__ ctype, const T* __restrict__ rf,
-                           T* __restrict__ bc) {
+__global__ void k_restrict_split(Transfer<T> X, SLev<T> F, SLev<T> C) {
     const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     const int J = 1 + blockIdx.y, K = 1 + blockIdx.z;
-    const int ncx = X.nc[0], ncy = X.nc[1];
+    const int ncx = C.G.nx, ncy = C.G.ny;
     if (I > ncx - 2) return;
-    const int64_t lc = (int64_t)K * ncx * ncy + (int64_t)J * ncx + I;
-    const uint8_t t = ctype[lc];
-    if (t != CFP_REGULAR && t != CFP_IRREGULAR) return;
-    const int nfx = X.nf[0], nfy = X.nf[1], nfz = X.nf[2];
-    const int fi = fine_of(I, nfx), fj = fine_of(J, nfy), fk = fine_of(K, X.nf[2]);
+    const int cc = (I + J + K) & 1;
+    const int64_t oc = ((int64_t)K * ncy + J) * C.hp + (I >> 1);
+    if (!is_unknown(C.ty[cc * C.Nh + oc])) return;
+    const int nfy = F.G.ny;
+    const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
     T wx[3], wy[3], wz[3];
-    for (int o = 0; o < 3; ++o) {
-        const int i = fi - 1 + o, j = fj - 1 + o, k = fk - 1 + o;
-        wx[o] = (i >= 0 && i < nfx) ? weight_to(X.ax[0], i, I) : T(0);
-        wy[o] = (j >= 0 && j < nfy) ? weight_to(X.ax[1], j, J) : T(0);
-        wz[o] = (k >= 0 && k < nfz) ? weight_to(X.ax[2], k, K) : T(0);
+    for (int q = 0; q < 3; ++q) {
+        wx[q] = weight_to(X.ax[0], fi - 1 + q, I);
+        wy[q] = weight_to(X.ax[1], fj - 1 + q, J);
+        wz[q] = weight_to(X.ax[2], fk - 1 + q, K);
     }
+    const T* __restrict__ r0 = F.v + R0 * F.Nh;
     T s = 0, w = 0;
-    const int64_t fsy = nfx, fsz = (int64_t)nfx * nfy;
     for (int c = 0; c < 3; ++c) {
-        if (wz[c] == T(0)) continue;
+        const int k = fk - 1 + c;
         for (int b = 0; b < 3; ++b) {
-            if (wy[b] == T(0)) continue;
+            const int j = fj - 1 + b;
             const T wyz = wy[b] * wz[c];
-            const int64_t base = (int64_t)(fk - 1 + c) * fsz + (int64_t)(fj - 1 + b) * fsy + (fi - 1);
+            const int64_t rowo = ((int64_t)k * nfy + j) * F.hp;
             for (int a = 0; a < 3; ++a) {
-                if (wx[a] == T(0)) continue;
+                const int i = fi - 1 + a;
                 const T ww = wx[a] * wyz;
-                s += ww * rf[base + a];
                 w += ww;
+                if (((i + j + k) & 1) == 0) s += ww * r0[rowo + (i >> 1)];
             }
         }
     }
-    bc[lc] = s / w;
+    C.v[(B0 + cc) * C.Nh + oc] = s / w;
 }
 
-// e_f += P e_c at the fine unknowns (ilo + 1 is a valid coarse index for
-// every fine node, with weight zero on coincident nodes)
+// e1 += P e_c at the fine black unknowns (the red values are overwritten by
+// the next red half-sweep without being read).
 template <class T>
-__global__ void k_prolong_add(Transfer<T> X, const uint8_t* __restrict__ ftype, const T* __restrict__ ec,
-                              T* __restrict__ ef) {
-    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kSplitThreads) k_prolong_split(Transfer<T> X, SLev<T> F, SLev<T> C) {
+    const int nx = F.G.nx, ny = F.G.ny;
+    const int m = blockIdx.x * kSplitThreads + threadIdx.x;
     const int j = 1 + blockIdx.y, k = 1 + blockIdx.z;
-    const int nfx = X.nf[0], nfy = X.nf[1];
-    if (i > nfx - 2) return;
-    const int64_t l = (int64_t)k * nfx * nfy + (int64_t)j * nfx + i;
-    const int ncx = X.nc[0], ncy = X.nc[1];
+    if (2 * m > nx - 2) return;
+    const int i = 2 * m + ((1 + j + k) & 1);
+    if (i < 1 || i > nx - 2) return;
+    const int64_t o = ((int64_t)k * ny + j) * F.hp + m;
+    const uint8_t t = F.ty[F.Nh + o];
     const int I = X.ax[0].ilo[i], J = X.ax[1].ilo[j], K = X.ax[2].ilo[k];
     const T ax0 = X.ax[0].wlo[i], ax1 = X.ax[0].whi[i];
     const T ay0 = X.ax[1].wlo[j], ay1 = X.ax[1].whi[j];
     const T az0 = X.ax[2].wlo[k], az1 = X.ax[2].whi[k];
-    const int64_t csy = ncx, csz = (int64_t)ncx * ncy;
-    const int64_t c0 = (int64_t)K * csz + (int64_t)J * csy + I;
-    const uint8_t t = ftype[l];
-    const T f0 = ef[l];
-    const T e000 = ec[c0], e001 = ec[c0 + 1], e010 = ec[c0 + csy], e011 = ec[c0 + csy + 1];
-    const T e100 = ec[c0 + csz], e101 = ec[c0 + csz + 1], e110 = ec[c0 + csz + csy], e111 = ec[c0 + csz + csy + 1];
-    if (t != CFP_REGULAR && t != CFP_IRREGULAR) return;
+    const int ncy = C.G.ny, hc = C.hp;
+    const int64_t Nc = C.Nh;
+    // coarse (I + a, J + b, K + c): colour (I + a + J + b + K + c) & 1, entry ((K + c) * ncy + J + b) * hc + (I + a) >> 1
+    const int p = (I + J + K) & 1;
+    const int64_t r00 = ((int64_t)K * ncy + J) * hc, r01 = r00 + hc, r10 = r00 + (int64_t)ncy * hc, r11 = r10 + hc;
+    const int x0 = I >> 1, x1 = (I + 1) >> 1;
+    const T* __restrict__ ea = C.v + (int64_t)p * Nc;        // colour p
+    const T* __restrict__ eb = C.v + (int64_t)(1 - p) * Nc;  // colour 1 - p
+    const T e000 = ea[r00 + x0], e001 = eb[r00 + x1], e010 = eb[r01 + x0], e011 = ea[r01 + x1];
+    const T e100 = eb[r10 + x0], e101 = ea[r10 + x1], e110 = ea[r11 + x0], e111 = eb[r11 + x1];
+    T* __restrict__ e1 = F.v + E1 * F.Nh;
+    const T f0 = e1[o];
+    if (!is_unknown(t)) return;
     const T v = az0 * (ay0 * (ax0 * e000 + ax1 * e001) + ay1 * (ax0 * e010 + ax1 * e011)) +
                 az1 * (ay0 * (ax0 * e100 + ax1 * e101) + ay1 * (ax0 * e110 + ax1 * e111));
-    ef[l] = f0 + v;
+    e1[o] = f0 + v;
 }
 
 // coarse type by injection: box stays box, solid stays solid, fluid -> regular
+__device__ __forceinline__ int fine_of(int I, int n) { return min(2 * I, n - 1); }
+
 __global__ void k_inject_type(const uint8_t* __restrict__ ft, int nfx, int nfy, int nfz, uint8_t* __restrict__ ct,
                               int ncx, int ncy, int ncz) {
     const int64_t nc = (int64_t)ncx * ncy * ncz;
@@ -157,14 +277,33 @@ __global__ void k_inject_type(const uint8_t* __restrict__ ft, int nfx, int nfy, 
     }
 }
 
-dim3 level_grid(int nx, int ny, int nz, int threads) {
-    return dim3((unsigned)((nx - 2 + threads - 1) / threads), (unsigned)(ny - 2), (unsigned)(nz - 2));
+// natural-layout type -> split type (padding entries are boundary)
+__global__ void k_split_type(const uint8_t* __restrict__ nat, int nx, int ny, int nz, int hp,
+                             uint8_t* __restrict__ st) {
+    const int64_t Nh = (int64_t)hp * ny * nz;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * Nh; q += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(q / Nh);
+        const int64_t e = q - c * Nh;
+        const int m = (int)(e % hp);
+        const int64_t rowi = e / hp;  // k * ny + j
+        const int j = (int)(rowi % ny), k = (int)(rowi / ny);
+        const int i = 2 * m + ((c + j + k) & 1);
+        st[q] = i < nx ? nat[rowi * nx + i] : (uint8_t)CFP_BOUNDARY;
+    }
+}
+
+unsigned flat_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+
+dim3 pair_grid(const int n[3]) {
+    const int pairs = n[0] / 2;  // m = 0 .. (n_x - 2) / 2
+    return dim3((unsigned)((pairs + kSplitThreads - 1) / kSplitThreads), (unsigned)(n[1] - 2), (unsigned)(n[2] - 2));
 }
 
 template <class T>
-Grid<T> level_grid_view(MgLevel& L);
+Grid<T> level_grid_view(cfp_ctx* c, MgLevel& L, int l);
 template <>
-Grid<double> level_grid_view<double>(MgLevel& L) {
+Grid<double> level_grid_view<double>(cfp_ctx* c, MgLevel& L, int l) {
+    if (l == 0) return grid_view<double>(c);
     Grid<double> g;
     int64_t off = 0;
     for (int d = 0; d < 3; ++d) {
@@ -179,7 +318,8 @@ Grid<double> level_grid_view<double>(MgLevel& L) {
     return g;
 }
 template <>
-Grid<float> level_grid_view<float>(MgLevel& L) {
+Grid<float> level_grid_view<float>(cfp_ctx* c, MgLevel& L, int l) {
+    if (l == 0) return grid_view<float>(c);
     Grid<float> g;
     int64_t off = 0;
     for (int d = 0; d < 3; ++d) {
@@ -195,59 +335,74 @@ Grid<float> level_grid_view<float>(MgLevel& L) {
 }
 
 template <class T>
-T* lvec(MgLevel& L, int which);
+T* svec(MgLevel& L);
 template <>
-double* lvec<double>(MgLevel& L, int which) { return L.v64 + which * L.N; }
+double* svec<double>(MgLevel& L) { return L.s64; }
 template <>
-float* lvec<float>(MgLevel& L, int which) { return L.v32 + which * L.N; }
+float* svec<float>(MgLevel& L) { return L.s32; }
 
 template <class T>
-Transfer<T> transfer(MgLevel& F, MgLevel& Cc);
+SLev<T> slev(cfp_ctx* c, int l) {
+    MgLevel& L = c->mg[l];
+    return SLev<T>{level_grid_view<T>(c, L, l), L.stype, svec<T>(L), L.hp, L.Nh};
+}
+
+template <class T>
+Transfer<T> transfer(MgLevel& F);
 template <>
-Transfer<double> transfer<double>(MgLevel& F, MgLevel& Cc) {
+Transfer<double> transfer<double>(MgLevel& F) {
     Transfer<double> X;
-    for (int d = 0; d < 3; ++d) {
-        X.ax[d] = Interp<double>{F.ilo[d], F.w64 + 2 * F.off[d], F.w64 + 2 * F.off[d] + F.n[d]};
-        X.nf[d] = F.n[d];
-        X.nc[d] = Cc.n[d];
-    }
+    for (int d = 0; d < 3; ++d) X.ax[d] = Interp<double>{F.ilo[d], F.w64 + 2 * F.off[d], F.w64 + 2 * F.off[d] + F.n[d]};
     return X;
 }
 template <>
-Transfer<float> transfer<float>(MgLevel& F, MgLevel& Cc) {
+Transfer<float> transfer<float>(MgLevel& F) {
     Transfer<float> X;
-    for (int d = 0; d < 3; ++d) {
-        X.ax[d] = Interp<float>{F.ilo[d], F.w32 + 2 * F.off[d], F.w32 + 2 * F.off[d] + F.n[d]};
-        X.nf[d] = F.n[d];
-        X.nc[d] = Cc.n[d];
-    }
+    for (int d = 0; d < 3; ++d) X.ax[d] = Interp<float>{F.ilo[d], F.w32 + 2 * F.off[d], F.w32 + 2 * F.off[d] + F.n[d]};
     return X;
 }
 
 template <class T>
-void smooth(const Grid<T>& G, const Side<T>& S, const uint8_t* type, const T* b, T* e, int sweeps, bool from_zero,
-            cudaStream_t s, int64_t& launches) {
-    for (int q = 0; q < sweeps; ++q) {
-        launch_half_sweep<T>(G, S, type, b, e, 0, from_zero && q == 0, s);
-        launch_half_sweep<T>(G, S, type, b, e, 1, false, s);
+void half_sweep(cfp_ctx* c, int l, const SLev<T>& L, const Side<T>& S, int colour, int mode, const T* rho, T* phi,
+                cudaStream_t s) {
+    const dim3 g = pair_grid(c->mg[l].n);
+    switch (mode) {
+        case 0: k_sweep_split<T, 0><<<g, kSplitThreads, 0, s>>>(L, S, colour, rho, phi); break;
+        case 1: k_sweep_split<T, 1><<<g, kSplitThreads, 0, s>>>(L, S, colour, rho, phi); break;
+        case 2: k_sweep_split<T, 2><<<g, kSplitThreads, 0, s>>>(L, S, colour, rho, phi); break;
+        default: k_sweep_split<T, 3><<<g, kSplitThreads, 0, s>>>(L, S, colour, rho, phi); break;
     }
-    launches += 2 * sweeps;
+    c->launches += 1;
+}
+
+// `sweeps` red-black sweeps at level l.  first_red / last_black: the modes of
+// the first red and the last black half-sweep.
+template <class T>
+void smooth(cfp_ctx* c, int l, const Side<T>& S, int sweeps, int first_red, int last_black, const T* rho, T* phi,
+            cudaStream_t s) {
+    const SLev<T> L = slev<T>(c, l);
+    for (int q = 0; q < sweeps; ++q) {
+        half_sweep<T>(c, l, L, S, 0, q == 0 ? first_red : 0, rho, phi, s);
+        half_sweep<T>(c, l, L, S, 1, q == sweeps - 1 ? last_black : 0, rho, phi, s);
+    }
 }
 
 }  // namespace
 
 void free_mg(cfp_ctx* c) {
     for (MgLevel& L : c->mg) {
-        void* ptrs[] = {L.coef64, L.coef32, L.type, L.v64, L.v32, L.ilo[0], L.ilo[1], L.ilo[2], L.w64, L.w32};
+        void* ptrs[] = {L.coef64, L.coef32, L.type, L.stype, L.s64, L.s32, L.ilo[0], L.ilo[1], L.ilo[2], L.w64, L.w32};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     }
     c->mg.clear();
 }
 
-// Build the level hierarchy below the fine grid (after classification).
-cfp_status ensure_mg(cfp_ctx* c) {
-    if (!c->mg.empty()) return CFP_OK;
+namespace {
+
+// The level hierarchy below the fine grid (after classification): sizes,
+// coordinates, interpolation tables, coarse coefficients and types.
+cfp_status build_levels(cfp_ctx* c) {
     std::vector<MgLevel> levels(1);
     MgLevel& F0 = levels[0];
     for (int d = 0; d < 3; ++d) {
@@ -268,12 +423,14 @@ cfp_status ensure_mg(cfp_ctx* c) {
         levels.push_back(Cn);
     }
     const int nl = (int)levels.size();
+    // from here on every device pointer is owned by c->mg, so free_mg cleans
+    // up after a failure
+    c->mg = levels;
     for (int l = 0; l < nl; ++l) {
-        MgLevel& L = levels[l];
+        MgLevel& L = c->mg[l];
         // interpolation tables from level l + 1 (per fine index of level l)
         if (l + 1 < nl) {
-            const MgLevel& Cn = levels[l + 1];
-            std::vector<double> w;
+            const MgLevel& Cn = c->mg[l + 1];
             int64_t tot = 0;
             for (int d = 0; d < 3; ++d) {
                 L.off[d] = tot;
@@ -310,91 +467,117 @@ cfp_status ensure_mg(cfp_ctx* c) {
             CFP_CUDA(cudaMemcpy(L.w64, wv.data(), sizeof(double) * wv.size(), cudaMemcpyHostToDevice));
             CFP_CUDA(cudaMemcpy(L.w32, wf.data(), sizeof(float) * wf.size(), cudaMemcpyHostToDevice));
         }
-        if (l == 0) continue;  // the fine level uses the context's own arrays
-        // metrics of the coarse coordinates
-        int64_t nco = 0;
-        for (int d = 0; d < 3; ++d) nco += 8 * (int64_t)L.n[d];
-        std::vector<double> cf(nco, 0.0);
-        int64_t off = 0;
-        for (int d = 0; d < 3; ++d) {
-            const int n = L.n[d];
-            for (int i = 1; i < n - 1; ++i) {
-                const double f = L.X[d][i + 1] - L.X[d][i], b = L.X[d][i] - L.X[d][i - 1];
-                cf[off + 5 * n + i] = 2.0 / (b * (f + b));
-                cf[off + 6 * n + i] = -2.0 / (b * f);
-                cf[off + 7 * n + i] = 2.0 / (f * (f + b));
+        L.hp = ((L.n[0] + 1) / 2 + 7) / 8 * 8;
+        L.Nh = (int64_t)L.hp * L.n[1] * L.n[2];
+        const uint8_t* nat = c->type;
+        if (l > 0) {
+            // metrics of the coarse coordinates
+            int64_t nco = 0;
+            for (int d = 0; d < 3; ++d) nco += 8 * (int64_t)L.n[d];
+            std::vector<double> cf(nco, 0.0);
+            int64_t off = 0;
+            for (int d = 0; d < 3; ++d) {
+                const int n = L.n[d];
+                for (int i = 1; i < n - 1; ++i) {
+                    const double f = L.X[d][i + 1] - L.X[d][i], b = L.X[d][i] - L.X[d][i - 1];
+                    cf[off + 5 * n + i] = 2.0 / (b * (f + b));
+                    cf[off + 6 * n + i] = -2.0 / (b * f);
+                    cf[off + 7 * n + i] = 2.0 / (f * (f + b));
+                }
+                off += 8 * (int64_t)n;
             }
-            off += 8 * (int64_t)n;
+            std::vector<float> cf32(cf.begin(), cf.end());
+            CFP_CUDA(cudaMalloc(&L.coef64, sizeof(double) * nco));
+            CFP_CUDA(cudaMalloc(&L.coef32, sizeof(float) * nco));
+            CFP_CUDA(cudaMemcpy(L.coef64, cf.data(), sizeof(double) * nco, cudaMemcpyHostToDevice));
+            CFP_CUDA(cudaMemcpy(L.coef32, cf32.data(), sizeof(float) * nco, cudaMemcpyHostToDevice));
+            CFP_CUDA(cudaMalloc(&L.type, (size_t)L.N));
+            const MgLevel& Fp = c->mg[l - 1];
+            const uint8_t* ft = l == 1 ? c->type : Fp.type;
+            k_inject_type<<<flat_blocks(L.N), 256, 0, c->stream>>>(ft, Fp.n[0], Fp.n[1], Fp.n[2], L.type, L.n[0],
+                                                                   L.n[1], L.n[2]);
+            CFP_CUDA(cudaGetLastError());
+            nat = L.type;
         }
-        std::vector<float> cf32(cf.begin(), cf.end());
-        CFP_CUDA(cudaMalloc(&L.coef64, sizeof(double) * nco));
-        CFP_CUDA(cudaMalloc(&L.coef32, sizeof(float) * nco));
-        CFP_CUDA(cudaMemcpy(L.coef64, cf.data(), sizeof(double) * nco, cudaMemcpyHostToDevice));
-        CFP_CUDA(cudaMemcpy(L.coef32, cf32.data(), sizeof(float) * nco, cudaMemcpyHostToDevice));
-        CFP_CUDA(cudaMalloc(&L.type, (size_t)L.N));
-        const MgLevel& Fp = levels[l - 1];
-        const uint8_t* ft = l == 1 ? c->type : Fp.type;
-        k_inject_type<<<(unsigned)std::min<int64_t>((L.N + 255) / 256, 152 * 16), 256, 0, c->stream>>>(
-            ft, Fp.n[0], Fp.n[1], Fp.n[2], L.type, L.n[0], L.n[1], L.n[2]);
+        CFP_CUDA(cudaMalloc(&L.stype, (size_t)(2 * L.Nh)));
+        k_split_type<<<flat_blocks(2 * L.Nh), 256, 0, c->stream>>>(nat, L.n[0], L.n[1], L.n[2], L.hp, L.stype);
         CFP_CUDA(cudaGetLastError());
-        // e, b, r per level in both precisions, zero-filled
-        CFP_CUDA(cudaMalloc(&L.v64, sizeof(double) * 3 * L.N));
-        CFP_CUDA(cudaMalloc(&L.v32, sizeof(float) * 3 * L.N));
-        CFP_CUDA(cudaMemsetAsync(L.v64, 0, sizeof(double) * 3 * L.N, c->stream));
-        CFP_CUDA(cudaMemsetAsync(L.v32, 0, sizeof(float) * 3 * L.N, c->stream));
     }
     CFP_CUDA(cudaStreamSynchronize(c->stream));
-    c->mg = levels;
     return CFP_OK;
 }
 
-// phi = V(rho): one V-cycle from zero on the level hierarchy.
+}  // namespace
+
+// Build the hierarchy if needed and the split vectors of precision `prec`
+// (0: FP64, 1: FP32), zero-filled: entries that are never written (the
+// non-unknowns, the box, the black residuals) must read as zero.
+cfp_status ensure_mg(cfp_ctx* c, int prec) {
+    if (c->mg.empty()) {
+        const cfp_status st = build_levels(c);
+        if (st != CFP_OK) {
+            free_mg(c);
+            return st;
+        }
+    }
+    for (MgLevel& L : c->mg) {
+        const size_t n = (size_t)kSplitVecs * L.Nh;
+        if (prec == 0 && !L.s64) {
+            CFP_CUDA(cudaMalloc(&L.s64, sizeof(double) * n));
+            CFP_CUDA(cudaMemsetAsync(L.s64, 0, sizeof(double) * n, c->stream));
+        }
+        if (prec == 1 && !L.s32) {
+            CFP_CUDA(cudaMalloc(&L.s32, sizeof(float) * n));
+            CFP_CUDA(cudaMemsetAsync(L.s32, 0, sizeof(float) * n, c->stream));
+        }
+    }
+    CFP_CUDA(cudaStreamSynchronize(c->stream));
+    return CFP_OK;
+}
+
+// phi = V(rho): one V-cycle from zero on the level hierarchy.  phi is written
+// at every interior node of the interior rows (zero at the non-unknowns).
 template <class T>
 void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
     const int nl = (int)c->mg.size();
     const int nu = std::max(1, c->mg_smooth);
     const Side<T> S0 = side_view<T>(c);
     const Side<T> Sc = Side<T>{nullptr, nullptr, nullptr, nullptr, nullptr};
-    T* r0 = precond_tmp<T>(c);
-    // downward leg
+    if (nl == 1) {
+        smooth<T>(c, 0, S0, 16, 2, 3, rho, phi, s);
+        return;
+    }
+    // downward leg: smooth from zero, red residual, restrict to b of l + 1
     for (int l = 0; l < nl - 1; ++l) {
-        MgLevel& L = c->mg[l];
-        MgLevel& Cn = c->mg[l + 1];
-        const Grid<T> G = l == 0 ? grid_view<T>(c) : level_grid_view<T>(L);
         const Side<T>& S = l == 0 ? S0 : Sc;
-        const uint8_t* ty = l == 0 ? c->type : L.type;
-        const T* b = l == 0 ? rho : lvec<T>(L, 1);
-        T* e = l == 0 ? phi : lvec<T>(L, 0);
-        T* r = l == 0 ? r0 : lvec<T>(L, 2);
-        smooth<T>(G, S, ty, b, e, nu, true, s, c->launches);
-        k_resid7<T><<<level_grid(L.n[0], L.n[1], L.n[2], 128), 128, 0, s>>>(G, S, ty, b, e, r);
-        k_restrict<T><<<level_grid(Cn.n[0], Cn.n[1], Cn.n[2], 128), 128, 0, s>>>(transfer<T>(L, Cn), Cn.type, r,
-                                                                                 lvec<T>(Cn, 1));
+        smooth<T>(c, l, S, nu, l == 0 ? 2 : 1, 0, rho, phi, s);
+        const SLev<T> F = slev<T>(c, l), C = slev<T>(c, l + 1);
+        k_resid_split<T><<<pair_grid(c->mg[l].n), kSplitThreads, 0, s>>>(F, S);
+        const MgLevel& Cn = c->mg[l + 1];
+        const dim3 gr((unsigned)((Cn.n[0] - 2 + 127) / 128), (unsigned)(Cn.n[1] - 2), (unsigned)(Cn.n[2] - 2));
+        k_restrict_split<T><<<gr, 128, 0, s>>>(transfer<T>(c->mg[l]), F, C);
         c->launches += 2;
     }
-    {  // coarsest level
-        MgLevel& L = c->mg[nl - 1];
-        const Grid<T> G = nl == 1 ? grid_view<T>(c) : level_grid_view<T>(L);
-        smooth<T>(G, nl == 1 ? S0 : Sc, nl == 1 ? c->type : L.type, nl == 1 ? rho : lvec<T>(L, 1),
-                  nl == 1 ? phi : lvec<T>(L, 0), 16, true, s, c->launches);
-    }
-    // upward leg
+    smooth<T>(c, nl - 1, Sc, 16, 1, 0, rho, phi, s);  // coarsest level
+    // upward leg: black coarse correction, smooth; the last half-sweep of the
+    // fine level writes phi
     for (int l = nl - 2; l >= 0; --l) {
-        MgLevel& L = c->mg[l];
-        MgLevel& Cn = c->mg[l + 1];
-        const Grid<T> G = l == 0 ? grid_view<T>(c) : level_grid_view<T>(L);
-        const Side<T>& S = l == 0 ? S0 : Sc;
-        const uint8_t* ty = l == 0 ? c->type : L.type;
-        const T* b = l == 0 ? rho : lvec<T>(L, 1);
-        T* e = l == 0 ? phi : lvec<T>(L, 0);
-        k_prolong_add<T><<<level_grid(L.n[0], L.n[1], L.n[2], 128), 128, 0, s>>>(transfer<T>(L, Cn), ty,
-                                                                                 lvec<T>(Cn, 0), e);
+        const SLev<T> F = slev<T>(c, l), C = slev<T>(c, l + 1);
+        k_prolong_split<T><<<pair_grid(c->mg[l].n), kSplitThreads, 0, s>>>(transfer<T>(c->mg[l]), F, C);
         c->launches += 1;
-        smooth<T>(G, S, ty, b, e, nu, false, s, c->launches);
+        smooth<T>(c, l, l == 0 ? S0 : Sc, nu, 0, l == 0 ? 3 : 0, rho, phi, s);
     }
+}
+
+template <class T>
+void launch_mg_half_sweep(cfp_ctx* c, cudaStream_t s) {
+    const SLev<T> L = slev<T>(c, 0);
+    half_sweep<T>(c, 0, L, side_view<T>(c), 0, 0, (const T*)nullptr, (T*)nullptr, s);
 }
 
 template void launch_precond_mg<double>(cfp_ctx*, const double*, double*, cudaStream_t);
 template void launch_precond_mg<float>(cfp_ctx*, const float*, float*, cudaStream_t);
+template void launch_mg_half_sweep<double>(cfp_ctx*, cudaStream_t);
+template void launch_mg_half_sweep<float>(cfp_ctx*, cudaStream_t);
 
 }  // namespace cfp
