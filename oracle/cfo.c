@@ -67,6 +67,8 @@ struct cfo_problem {
     double* ibi_t;
     double* ibi_xyz;
     csr_t B, BI, K, KI;
+    int precond_kind;      /* CFO_PRECOND_RBGS or CFO_PRECOND_ILU */
+    double* ilu_d;         /* ILU(0) pivots of K, NULL until first needed */
     char err[256];
 };
 
@@ -204,6 +206,7 @@ void cfo_destroy(cfo_problem* p) {
     free(p->bodies); free(p->type);
     free(p->ibi_key); free(p->ibi_t); free(p->ibi_xyz);
     csr_free(&p->B); csr_free(&p->BI); csr_free(&p->K); csr_free(&p->KI);
+    free(p->ilu_d);
     free(p);
 }
 
@@ -614,6 +617,8 @@ static int k_row(cfo_problem* p, int i, int j, int k, rowacc_t* row, rowacc_t* r
 int cfo_assemble(cfo_problem* p) {
     if (!p->classified) { seterr(p, "classify first"); return CFO_EINVAL; }
     csr_free(&p->B); csr_free(&p->BI); csr_free(&p->K); csr_free(&p->KI);
+    free(p->ilu_d);
+    p->ilu_d = NULL;
     const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
     builder_t bB, bBI, bK, bKI;
     int64_t nun = (int64_t)(nx - 2) * (ny - 2) * (nz - 2);
@@ -762,6 +767,102 @@ void cfo_precond(cfo_problem* p, int sweeps, const double* rho, double* phi) {
 }
 
 /* ------------------------------------------------------------------ */
+/* The second inner iteration on K (Sec. 3.3 solves K phi = rho with a  */
+/* few iterations of an incomplete-factorisation method): ILU(0) of K   */
+/* in natural node order, used as a Richardson iteration from phi = 0.  */
+/*                                                                      */
+/* Restricted to the unknowns, K = L + D + U (strictly lower, diagonal, */
+/* strictly upper in natural order).  ILU(0) keeps the sparsity of K;   */
+/* for a 7-point pattern the factorisation is M = (P + L) P^-1 (P + U)  */
+/* with the pivots                                                      */
+/*     P_l = K_ll - sum over unknown m < l in row l of K_lm K_ml / P_m, */
+/* which makes M equal to K at every position of K's pattern (the       */
+/* products L P^-1 U only add entries outside it).  One sweep:          */
+/*     w = rho - K phi;  (P + L) y = w;  (P + U) z = P y;  phi += z.    */
+/* ------------------------------------------------------------------ */
+static double k_entry(const cfo_problem* p, int64_t row, int64_t col) {
+    for (int64_t e = p->K.ptr[row]; e < p->K.ptr[row + 1]; ++e)
+        if (p->K.col[e] == col) return p->K.val[e];
+    return 0.0;
+}
+
+static int ilu_pivots(cfo_problem* p) {
+    if (p->ilu_d) return CFO_OK;
+    double* d = (double*)calloc((size_t)p->N, sizeof(double));
+    if (!d) { seterr(p, "out of memory"); return CFO_ENOMEM; }
+    for (int64_t l = 0; l < p->N; ++l) {       /* natural order: every m < l is final */
+        if (!is_unknown(p->type[l])) continue;
+        double v = k_entry(p, l, l);
+        for (int64_t e = p->K.ptr[l]; e < p->K.ptr[l + 1]; ++e) {
+            const int64_t m = p->K.col[e];
+            if (m >= l || !is_unknown(p->type[m])) continue;
+            v -= p->K.val[e] * k_entry(p, m, l) / d[m];
+        }
+        d[l] = v;
+    }
+    p->ilu_d = d;
+    return CFO_OK;
+}
+
+int cfo_ilu_pivots(cfo_problem* p, double* d_out) {
+    if (!p->assembled) { seterr(p, "assemble first"); return CFO_EINVAL; }
+    int st = ilu_pivots(p);
+    if (st) return st;
+    memcpy(d_out, p->ilu_d, sizeof(double) * p->N);
+    return CFO_OK;
+}
+
+void cfo_precond_ilu(cfo_problem* p, int sweeps, const double* rho, double* phi) {
+    const int64_t N = p->N;
+    memset(phi, 0, sizeof(double) * N);
+    if (sweeps <= 0) {
+        for (int64_t l = 0; l < N; ++l) phi[l] = is_unknown(p->type[l]) ? rho[l] : 0.0;
+        return;
+    }
+    if (ilu_pivots(p)) return;
+    const double* d = p->ilu_d;
+    double* w = (double*)calloc((size_t)N, sizeof(double));
+    if (!w) return;
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int64_t l = 0; l < N; ++l) {      /* w = rho - K phi at the unknowns */
+            if (!is_unknown(p->type[l])) { w[l] = 0.0; continue; }
+            double s = rho[l];
+            for (int64_t e = p->K.ptr[l]; e < p->K.ptr[l + 1]; ++e) s -= p->K.val[e] * phi[p->K.col[e]];
+            w[l] = s;
+        }
+        for (int64_t l = 0; l < N; ++l) {      /* forward: (P + L) y = w, y over w */
+            if (!is_unknown(p->type[l])) continue;
+            double s = w[l];
+            for (int64_t e = p->K.ptr[l]; e < p->K.ptr[l + 1]; ++e) {
+                const int64_t m = p->K.col[e];
+                if (m < l && is_unknown(p->type[m])) s -= p->K.val[e] * w[m];
+            }
+            w[l] = s / d[l];
+        }
+        for (int64_t l = N - 1; l >= 0; --l) { /* backward: (P + U) z = P y, z over y */
+            if (!is_unknown(p->type[l])) continue;
+            double s = 0.0;
+            for (int64_t e = p->K.ptr[l]; e < p->K.ptr[l + 1]; ++e) {
+                const int64_t m = p->K.col[e];
+                if (m > l && is_unknown(p->type[m])) s += p->K.val[e] * w[m];
+            }
+            w[l] -= s / d[l];
+        }
+        for (int64_t l = 0; l < N; ++l) phi[l] += w[l];
+    }
+    free(w);
+}
+
+void cfo_set_precond(cfo_problem* p, int kind) {
+    p->precond_kind = kind == CFO_PRECOND_ILU ? CFO_PRECOND_ILU : CFO_PRECOND_RBGS;
+}
+
+static void precond_any(cfo_problem* p, int sweeps, const double* rho, double* phi) {
+    if (p->precond_kind == CFO_PRECOND_ILU) cfo_precond_ilu(p, sweeps, rho, phi);
+    else cfo_precond(p, sweeps, rho, phi);
+}
+
+/* ------------------------------------------------------------------ */
 /* Algorithm 1 (Sec. 3.2), right preconditioned by K (Sec. 3.3).        */
 /* ------------------------------------------------------------------ */
 enum { RUN_CONV = 0, RUN_BREAK = 1, RUN_MAXIT = 2, RUN_NAN = 3 };
@@ -778,7 +879,7 @@ static int bicgstab_run(cfo_problem* p, const double* rhs, double* x, double tol
     if (!isfinite(rr)) return RUN_NAN;
     if (sqrt(rr) <= tol * bnorm) return RUN_CONV;
     for (int it = 1; it <= maxit; ++it) {
-        cfo_precond(p, sweeps, pp, ph);                 /* line 4 */
+        precond_any(p, sweeps, pp, ph);                 /* line 4 */
         cfo_apply_B(p, ph, v);                          /* line 5 */
         const double sigma = dot(N, rh, v);
         *used = it;
@@ -786,7 +887,7 @@ static int bicgstab_run(cfo_problem* p, const double* rhs, double* x, double tol
         if (sigma == 0.0) return RUN_BREAK;
         const double alpha = rho / sigma;               /* line 6 */
         for (int64_t q = 0; q < N; ++q) s[q] = r[q] - alpha * v[q];   /* line 7 */
-        cfo_precond(p, sweeps, s, sh);                  /* line 8 */
+        precond_any(p, sweeps, s, sh);                  /* line 8 */
         cfo_apply_B(p, sh, t);                          /* line 9 */
         const double ts = dot(N, t, s), tt = dot(N, t, t);
         if (!isfinite(tt)) return RUN_NAN;

@@ -77,7 +77,15 @@ void cfo_apply_B(cfo_problem* p, const double* x, double* y);
 void cfo_apply_B_abs(cfo_problem* p, const double* x, double* y);
 int  cfo_rhs(cfo_problem* p, const double* f, const double* g_nodes,
              const double* g_ibi, double* rhs);
+/* inner iterations on K from phi = 0: red-black Gauss-Seidel sweeps
+ * (cfo_precond) or ILU(0)-Richardson sweeps (cfo_precond_ilu); the solve
+ * uses the kind set by cfo_set_precond (red-black by default) */
+enum { CFO_PRECOND_RBGS = 0, CFO_PRECOND_ILU = 1 };
 void cfo_precond(cfo_problem* p, int sweeps, const double* rho, double* phi);
+void cfo_precond_ilu(cfo_problem* p, int sweeps, const double* rho, double* phi);
+void cfo_set_precond(cfo_problem* p, int kind);
+/* ILU(0) pivots of K in natural order (N values, 0 at non-unknowns) */
+int  cfo_ilu_pivots(cfo_problem* p, double* d_out);
 int  cfo_bicgstab(cfo_problem* p, const double* rhs, double* x, double tol,
                   int maxit, int sweeps, int* iters, double* relres);
 int  cfo_solve(cfo_problem* p, const double* f, const double* g_nodes,

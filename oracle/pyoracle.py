@@ -11,6 +11,7 @@ from . import build as _build
 
 BOUNDARY, REGULAR, IRREGULAR, SOLID = 0, 1, 2, 3
 MAT_B, MAT_BIBI, MAT_K, MAT_KIBI = 0, 1, 2, 3
+PRECOND_RBGS, PRECOND_ILU = 0, 1
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 4: "EGEOM", 5: "ENOCONV", 6: "EBREAKDOWN", 7: "ENAN"}
 KINDS = {"sphere": 0, "ellipsoid": 1, "torus": 2}
 
@@ -51,6 +52,9 @@ def lib():
         L.cfo_apply_B_abs.argtypes = [C.c_void_p, _D, _D]
         L.cfo_rhs.argtypes = [C.c_void_p, _D, _D, _D, _D]
         L.cfo_precond.argtypes = [C.c_void_p, C.c_int, _D, _D]
+        L.cfo_precond_ilu.argtypes = [C.c_void_p, C.c_int, _D, _D]
+        L.cfo_set_precond.argtypes = [C.c_void_p, C.c_int]
+        L.cfo_ilu_pivots.argtypes = [C.c_void_p, _D]
         L.cfo_bicgstab.argtypes = [C.c_void_p, _D, _D, C.c_double, C.c_int, C.c_int,
                                    C.POINTER(C.c_int), _D]
         L.cfo_solve.argtypes = [C.c_void_p, _D, _D, _D, _D, C.c_double, C.c_int, C.c_int,
@@ -214,13 +218,27 @@ class Problem:
         self._check(lib().cfo_rhs(self._h, _dp(f), _dp(g), _dp(gi), _dp(out)), "rhs")
         return out
 
-    def precond(self, rho, sweeps=8):
+    def precond(self, rho, sweeps=8, kind=PRECOND_RBGS):
+        """sweeps inner iterations on K from phi = 0 (red-black Gauss-Seidel
+        or ILU(0)-Richardson)."""
         if not self.assembled:
             self.assemble()
         rho = _f64(rho).reshape(-1)
         out = np.zeros(self.N)
-        lib().cfo_precond(self._h, int(sweeps), _dp(rho), _dp(out))
+        fn = lib().cfo_precond_ilu if kind == PRECOND_ILU else lib().cfo_precond
+        fn(self._h, int(sweeps), _dp(rho), _dp(out))
         return out
+
+    def ilu_pivots(self):
+        if not self.assembled:
+            self.assemble()
+        out = np.zeros(self.N)
+        self._check(lib().cfo_ilu_pivots(self._h, _dp(out)), "ilu_pivots")
+        return out
+
+    def set_precond(self, kind):
+        """inner iteration used by bicgstab / solve (PRECOND_RBGS or PRECOND_ILU)"""
+        lib().cfo_set_precond(self._h, int(kind))
 
     def bicgstab(self, rhs, x0=None, tol=1e-12, maxit=10000, sweeps=8):
         if not self.assembled:
