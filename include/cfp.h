@@ -63,15 +63,23 @@ enum { CFP_PREC_FP64 = 0,   /* the whole solve in FP64                       */
 enum { CFP_PRECOND_RBGS = 0, /* `sweeps` red-black Gauss-Seidel sweeps on K from
                                 zero (the paper's fixed count of inner
                                 iterations, Sec. 3.3)                         */
-       CFP_PRECOND_MG = 1    /* one multigrid V-cycle on K from zero: red-black
+       CFP_PRECOND_MG = 1,   /* one multigrid V-cycle on K from zero: red-black
                                 smoothing (mg_smooth sweeps before and after),
                                 rediscretised coarse levels; quality
-                                independent of the grid size                  */ };
+                                independent of the grid size                  */
+       CFP_PRECOND_ILU = 2   /* `sweeps` Richardson sweeps from zero with ILU(0)
+                                of K in natural order (the incomplete-
+                                factorisation class of the paper's inner
+                                solver, Sec. 3.3); each triangular solve is
+                                n_x + n_y + n_z - 8 dependent launches, one
+                                per hyperplane i + j + k = const: slow by
+                                construction, for fidelity, not speed       */ };
 
 typedef struct {
     int precision;     /* CFP_PREC_FP64 (default) or CFP_PREC_MIXED            */
-    int sweeps;        /* red-black Gauss-Seidel sweeps of the preconditioner
-                          solve (Sec. 3.3 uses 8 inner iterations; default 8) */
+    int sweeps;        /* inner iterations of the preconditioner solve with
+                          CFP_PRECOND_RBGS or CFP_PRECOND_ILU (Sec. 3.3 uses
+                          8; default 8)                                      */
     int maxit;         /* cap on BiCGSTAB iterations (default 50000)           */
     int max_restarts;  /* restarts after a breakdown or a failed true-residual
                           check (default 3)                                  */
@@ -80,7 +88,8 @@ typedef struct {
     int max_refine;    /* CFP_PREC_MIXED: cap on refinement steps (default 40) */
     int use_graph;     /* 1 (default): the iteration runs as one CUDA graph
                           with a device-side while loop; 0: plain launches   */
-    int precond;       /* CFP_PRECOND_RBGS (default) or CFP_PRECOND_MG        */
+    int precond;       /* CFP_PRECOND_RBGS (default), CFP_PRECOND_MG or
+                          CFP_PRECOND_ILU                                    */
     int mg_smooth;     /* CFP_PRECOND_MG: sweeps before and after the coarse
                           correction on each level (default 2)               */
 } cfp_opts;

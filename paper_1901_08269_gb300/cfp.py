@@ -14,7 +14,7 @@ OK, EINVAL, ENOMEM, ECUDA, EGEOM, ENOCONV, EBREAKDOWN, ENAN, ESTATE = range(9)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EGEOM", "ENOCONV", "EBREAKDOWN", "ENAN", "ESTATE"]
 BOUNDARY, REGULAR, IRREGULAR, SOLID = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
-PRECOND_RBGS, PRECOND_MG = 0, 1
+PRECOND_RBGS, PRECOND_MG, PRECOND_ILU = 0, 1, 2
 KINDS = {"sphere": 0, "ellipsoid": 1, "torus": 2}
 
 

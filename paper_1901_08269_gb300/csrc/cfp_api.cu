@@ -169,6 +169,7 @@ void cfp_ctx_destroy(cfp_ctx* c) {
     for (int q = 0; q < 2; ++q)
         if (c->gexec[q]) cudaGraphExecDestroy(c->gexec[q]);
     free_mg(c);
+    free_ilu(c);
     void* ptrs[] = {c->dcoef64, c->dcoef32, c->dX[0], c->dX[1], c->dX[2], c->dbodies, c->dbound2, c->type, c->slot, c->irr_lin,
                     c->ibi_off, c->ibi_xyz, c->corr_ptr, c->corr_off, c->corr_val, c->corr_val32, c->bib_ptr,
                     c->bib_idx, c->bib_val, c->krow, c->krow32, c->scan_bsum, c->dtotal, c->derr, c->v64, c->v32,
@@ -254,7 +255,8 @@ cfp_status cfp_precondition_ex(cfp_ctx* c, const cfp_opts* o, const double* rho,
     CFP_TRY(need_classified(c));
     CFP_TRY(need_field(rho, "rho_dev"));
     CFP_TRY(need_field(phi, "phi_dev"));
-    if (opts.sweeps < 0 || (opts.precond != CFP_PRECOND_RBGS && opts.precond != CFP_PRECOND_MG))
+    if (opts.sweeps < 0 ||
+        (opts.precond != CFP_PRECOND_RBGS && opts.precond != CFP_PRECOND_MG && opts.precond != CFP_PRECOND_ILU))
         return fail(CFP_EINVAL, "bad sweeps or preconditioner");
     if (rho == phi) return fail(CFP_EINVAL, "rho and phi must not overlap");
     CFP_TRY(ensure_work(c, false));
@@ -262,6 +264,7 @@ cfp_status cfp_precondition_ex(cfp_ctx* c, const cfp_opts* o, const double* rho,
     c->precond_kind = opts.precond;
     c->mg_smooth = std::max(1, opts.mg_smooth);
     if (c->precond_kind == CFP_PRECOND_MG) CFP_TRY(ensure_mg(c, 0));
+    if (c->precond_kind == CFP_PRECOND_ILU) CFP_TRY(ensure_ilu(c, 0));
     CFP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * c->N, c->stream));
     launch_precond<double>(c, opts.sweeps, rho, phi, c->stream);
     c->precond_kind = CFP_PRECOND_RBGS;

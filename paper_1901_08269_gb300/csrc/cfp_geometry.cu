@@ -714,6 +714,7 @@ cfp_status classify(cfp_ctx* c) {
     free_ptr(c->krow32);
     c->gsweeps[0] = c->gsweeps[1] = -1;  // side data changes: rebuild graphs
     free_mg(c);
+    free_ilu(c);
 
     GeoArgs g;
     for (int d = 0; d < 3; ++d) {

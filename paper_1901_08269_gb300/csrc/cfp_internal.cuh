@@ -178,6 +178,9 @@ struct cfp_ctx {
     int precond_kind = CFP_PRECOND_RBGS;
     int mg_smooth = 2;
     std::vector<cfp::MgLevel> mg;
+    // ILU(0) of K (CFP_PRECOND_ILU): [pivots | work field], FP64 and FP32
+    double* ilu64 = nullptr;
+    float* ilu32 = nullptr;
 
     // graphs: [precision][sweeps-config]
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -231,6 +234,11 @@ cfp_status ensure_mg(cfp_ctx* c, int prec);  // prec: 0 FP64 vectors, 1 FP32 vec
 void free_mg(cfp_ctx* c);
 template <class T>
 void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s);
+// ILU(0)-Richardson inner iteration (cfp_ilu.cu)
+cfp_status ensure_ilu(cfp_ctx* c, int prec);  // prec: 0 FP64, 1 FP32 (and FP64 pivots)
+void free_ilu(cfp_ctx* c);
+template <class T>
+void launch_precond_ilu(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s);
 // one plain red half-sweep on the fine level's split vectors (timing aid)
 template <class T>
 void launch_mg_half_sweep(cfp_ctx* c, cudaStream_t s);

@@ -478,12 +478,13 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
     if (!(tol > 0.0) || opts.maxit < 1 || opts.sweeps < 0) return fail(CFP_EINVAL, "bad tol, maxit or sweeps");
     const int64_t launches0 = c->launches;
     if (!c->classified) CFP_TRY(classify(c));
-    if (opts.precond != CFP_PRECOND_RBGS && opts.precond != CFP_PRECOND_MG)
+    if (opts.precond != CFP_PRECOND_RBGS && opts.precond != CFP_PRECOND_MG && opts.precond != CFP_PRECOND_ILU)
         return fail(CFP_EINVAL, "unknown preconditioner");
     c->precond_kind = opts.precond;
     c->mg_smooth = std::max(1, opts.mg_smooth);
     const bool mixed = opts.precision == CFP_PREC_MIXED;
     if (c->precond_kind == CFP_PRECOND_MG) CFP_TRY(ensure_mg(c, mixed ? 1 : 0));
+    if (c->precond_kind == CFP_PRECOND_ILU) CFP_TRY(ensure_ilu(c, mixed ? 1 : 0));
     CFP_TRY(ensure_work(c, mixed));
     const int64_t N = c->N;
     double* rhs = c->v64 + V_RHS * N;

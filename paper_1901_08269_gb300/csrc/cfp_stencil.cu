@@ -465,6 +465,7 @@ void launch_precond_rbgs(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStrea
 template <class T>
 void launch_precond(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s) {
     if (c->precond_kind == CFP_PRECOND_MG) launch_precond_mg<T>(c, rho, phi, s);
+    else if (c->precond_kind == CFP_PRECOND_ILU && sweeps > 0) launch_precond_ilu<T>(c, sweeps, rho, phi, s);
     else launch_precond_rbgs<T>(c, sweeps, rho, phi, s);
 }
 
