@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=1e-3)
     ap.add_argument("--sweeps", type=int, default=8)
     ap.add_argument("--precond", default="mg", choices=["mg", "rbgs"])
-    ap.add_argument("--mg-smooth", type=int, default=2)
+    ap.add_argument("--mg-smooth", type=int, default=3)
     ap.add_argument("--no-graph", action="store_true",
                     help="plain launches instead of the CUDA graph (ncu cannot profile kernel nodes of graphs "
                          "with conditional nodes)")

@@ -106,6 +106,8 @@ struct MgLevel {
     uint8_t* stype = nullptr;  // split type, colour c at stype + c * Nh
     double* s64 = nullptr;     // split e0 e1 b0 b1 r0 (Nh each), FP64
     float* s32 = nullptr;      // the same in FP32
+    void* pk64 = nullptr;      // packed (ka, kb, kc, 0) per index, x then y then z, FP64
+    void* pk32 = nullptr;      // the same in FP32
     int* ilo[3] = {nullptr, nullptr, nullptr};  // interpolation from the next coarser level
     int64_t off[3] = {0, 0, 0};
     double* w64 = nullptr;

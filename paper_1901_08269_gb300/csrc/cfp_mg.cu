@@ -51,27 +51,60 @@ struct Transfer {
     Interp<T> ax[3];
 };
 
-// one level in the split layout
+// (ka, kb, kc) of one index of one axis, packed for a single wide load
+template <class T>
+struct Pk;
+template <>
+struct Pk<float> {
+    using type = float4;
+};
+struct __align__(32) PkD {
+    double x, y, z, w;
+};
+template <>
+struct Pk<double> {
+    using type = PkD;
+};
+template <class T>
+using PkT = typename Pk<T>::type;
+
+// one level in the split layout; entry offsets within a colour array are
+// 32-bit (the level build rejects arrays of 2^31 entries or more)
 template <class T>
 struct SLev {
-    Grid<T> G;           // coefficients (ka, kb, kc) and sizes
-    const uint8_t* ty;   // split type, colour c at ty + c * Nh
-    T* v;                // e0 e1 b0 b1 r0, Nh each
-    int hp;
-    int64_t Nh;
+    int nx, ny;
+    int hp;                     // entries per row of one colour
+    unsigned hs;                // hp * ny
+    const PkT<T>* cx;           // packed K coefficients per axis index
+    const PkT<T>* cy;
+    const PkT<T>* cz;
+    const uint8_t* ty[2];       // split type per colour
+    T* e[2];                    // the iterate per colour
+    T* b[2];                    // the right-hand side per colour
+    T* r0;                      // the red residual
 };
 
-enum { E0 = 0, E1 = 1, B0 = 2, B1 = 3, R0 = 4, kSplitVecs = 5 };
+// the arrays one half-sweep of colour c touches (chosen on the host)
+template <class T>
+struct Half {
+    const uint8_t* ty;  // type of colour c
+    T* eown;            // e of colour c (written)
+    const T* eoth;      // e of the other colour (read)
+    T* bown;            // b of colour c
+    T* both;            // b of the other colour (written in MODE 2)
+};
+
+enum { kSplitVecs = 5 };  // e0 e1 b0 b1 r0
 
 __device__ __forceinline__ bool is_unknown(uint8_t t) { return t == CFP_REGULAR || t == CFP_IRREGULAR; }
 
-// K's row at (i, j, k): diagonal and the six neighbour weights (x-, x+, y-,
-// y+, z-, z+); Shortley-Weller rows come from the fine level's krow table.
+// K's row at a node: the packed regular coefficients, or the Shortley-Weller
+// row of an irregular node of the fine level (krow, natural index l)
 template <class T>
-__device__ __forceinline__ void k_row(const Grid<T>& G, const Side<T>& S, uint8_t t, int i, int j, int k,
+__device__ __forceinline__ void k_row(const SLev<T>& L, const Side<T>& S, uint8_t t, int i, int j, int k,
                                       T& dg, T& cxm, T& cxp, T& cym, T& cyp, T& czm, T& czp) {
     if (t == CFP_IRREGULAR) {
-        const int64_t l = ((int64_t)k * G.ny + j) * G.nx + i;
+        const int64_t l = ((int64_t)k * L.ny + j) * L.nx + i;
         const T* kr = S.krow + 7 * (int64_t)S.slot[l];
         dg = kr[0];
         cxm = kr[1];
@@ -80,14 +113,6 @@ __device__ __forceinline__ void k_row(const Grid<T>& G, const Side<T>& S, uint8_
         cyp = kr[4];
         czm = kr[5];
         czp = kr[6];
-    } else {
-        dg = G.ax[0].kb[i] + G.ax[1].kb[j] + G.ax[2].kb[k];
-        cxm = G.ax[0].ka[i];
-        cxp = G.ax[0].kc[i];
-        cym = G.ax[1].ka[j];
-        cyp = G.ax[1].kc[j];
-        czm = G.ax[2].ka[k];
-        czp = G.ax[2].kc[k];
     }
 }
 
@@ -110,23 +135,20 @@ __device__ __forceinline__ double times_rcp(double x, double d) { return x * __d
 //    natural-layout phi (the own node's new value is not stored).
 template <class T, int MODE>
 __global__ void __launch_bounds__(kSplitThreads)
-    k_sweep_split(SLev<T> L, Side<T> S, int colour, const T* __restrict__ rho, T* __restrict__ phi) {
-    const int nx = L.G.nx, ny = L.G.ny;
+    k_sweep_split(SLev<T> L, Side<T> S, Half<T> H, int colour, const T* __restrict__ rho, T* __restrict__ phi) {
+    const int nx = L.nx;
     const int m = blockIdx.x * kSplitThreads + threadIdx.x;
     const int j = 1 + blockIdx.y, k = 1 + blockIdx.z;
     if (2 * m > nx - 2) return;
     const int par = (colour + j + k) & 1;
     const int i = 2 * m + par, io = 2 * m + 1 - par;
     const int hp = L.hp;
-    const int64_t hs = (int64_t)hp * ny;
-    const int64_t o = (int64_t)k * hs + (int64_t)j * hp + m;
-    const int64_t Nh = L.Nh;
-    T* __restrict__ eown = L.v + (E0 + colour) * Nh;
-    const T* __restrict__ eoth = L.v + (E1 - colour) * Nh;
-    T* __restrict__ bown = L.v + (B0 + colour) * Nh;
-    const int64_t row = ((int64_t)k * ny + j) * nx;
-    const uint8_t t = L.ty[colour * Nh + o];
-    const T bv = MODE == 2 ? rho[row + i] : bown[o];
+    const unsigned hs = L.hs;
+    const unsigned o = (unsigned)k * hs + (unsigned)(j * hp + m);
+    const T* __restrict__ eoth = H.eoth;
+    const int64_t row = ((int64_t)k * L.ny + j) * nx;
+    const uint8_t t = H.ty[o];
+    const T bv = MODE == 2 ? rho[row + i] : H.bown[o];
     T xm = T(0), xp = T(0), ym = T(0), yp = T(0), zm = T(0), zp = T(0);
     if (MODE == 0 || MODE == 3) {
         xm = eoth[o - 1 + par];
@@ -136,15 +158,15 @@ __global__ void __launch_bounds__(kSplitThreads)
         zm = eoth[o - hs];
         zp = eoth[o + hs];
     }
-    T dg = L.G.ax[0].kb[i] + L.G.ax[1].kb[j] + L.G.ax[2].kb[k];
-    T cxm = L.G.ax[0].ka[i], cxp = L.G.ax[0].kc[i], cym = L.G.ax[1].ka[j], cyp = L.G.ax[1].kc[j];
-    T czm = L.G.ax[2].ka[k], czp = L.G.ax[2].kc[k];
+    const PkT<T> ckx = L.cx[i], cky = L.cy[j], ckz = L.cz[k];
+    T dg = ckx.y + (cky.y + ckz.y);
+    T cxm = ckx.x, cxp = ckx.z, cym = cky.x, cyp = cky.z, czm = ckz.x, czp = ckz.z;
     if (MODE == 2) {
-        bown[o] = bv;
-        L.v[(B1 - colour) * Nh + o] = rho[row + io];
+        H.bown[o] = bv;
+        H.both[o] = rho[row + io];
     }
     const bool live = i >= 1 && i <= nx - 2 && is_unknown(t);
-    if (t == CFP_IRREGULAR) k_row(L.G, S, t, i, j, k, dg, cxm, cxp, cym, cyp, czm, czp);
+    k_row(L, S, t, i, j, k, dg, cxm, cxp, cym, cyp, czm, czp);
     T v = bv;
     if (MODE == 0 || MODE == 3)
         v -= (cxm * xm + cxp * xp) + (cym * ym + cyp * yp) + (czm * zm + czp * zp);
@@ -154,7 +176,7 @@ __global__ void __launch_bounds__(kSplitThreads)
         if (io >= 1 && io <= nx - 2) phi[row + io] = par ? xm : xp;  // the other node of the pair
         return;
     }
-    if (live) eown[o] = v;
+    if (live) H.eown[o] = v;
 }
 
 // r0 = b0 - K e at the red unknowns (black residuals are zero after a
@@ -162,27 +184,26 @@ __global__ void __launch_bounds__(kSplitThreads)
 // issued before the type test, as in the half-sweep.
 template <class T>
 __global__ void __launch_bounds__(kSplitThreads) k_resid_split(SLev<T> L, Side<T> S) {
-    const int nx = L.G.nx, ny = L.G.ny;
+    const int nx = L.nx;
     const int m = blockIdx.x * kSplitThreads + threadIdx.x;
     const int j = 1 + blockIdx.y, k = 1 + blockIdx.z;
     if (2 * m > nx - 2) return;
     const int par = (j + k) & 1;
     const int i = 2 * m + par;
     const int hp = L.hp;
-    const int64_t hs = (int64_t)hp * ny;
-    const int64_t o = (int64_t)k * hs + (int64_t)j * hp + m;
-    const int64_t Nh = L.Nh;
-    const T* __restrict__ e1 = L.v + E1 * Nh;
-    const uint8_t t = L.ty[o];
-    const T e0 = L.v[o], b0 = L.v[B0 * Nh + o];
+    const unsigned hs = L.hs;
+    const unsigned o = (unsigned)k * hs + (unsigned)(j * hp + m);
+    const T* __restrict__ e1 = L.e[1];
+    const uint8_t t = L.ty[0][o];
+    const T e0 = L.e[0][o], b0 = L.b[0][o];
     const T xm = e1[o - 1 + par], xp = e1[o + par], ym = e1[o - hp], yp = e1[o + hp], zm = e1[o - hs], zp = e1[o + hs];
-    T dg = L.G.ax[0].kb[i] + L.G.ax[1].kb[j] + L.G.ax[2].kb[k];
-    T cxm = L.G.ax[0].ka[i], cxp = L.G.ax[0].kc[i], cym = L.G.ax[1].ka[j], cyp = L.G.ax[1].kc[j];
-    T czm = L.G.ax[2].ka[k], czp = L.G.ax[2].kc[k];
+    const PkT<T> ckx = L.cx[i], cky = L.cy[j], ckz = L.cz[k];
+    T dg = ckx.y + (cky.y + ckz.y);
+    T cxm = ckx.x, cxp = ckx.z, cym = cky.x, cyp = cky.z, czm = ckz.x, czp = ckz.z;
     if (i < 1 || i > nx - 2 || !is_unknown(t)) return;
-    if (t == CFP_IRREGULAR) k_row(L.G, S, t, i, j, k, dg, cxm, cxp, cym, cyp, czm, czp);
+    k_row(L, S, t, i, j, k, dg, cxm, cxp, cym, cyp, czm, czp);
     const T ke = dg * e0 + (cxm * xm + cxp * xp) + (cym * ym + cyp * yp) + (czm * zm + czp * zp);
-    L.v[R0 * Nh + o] = b0 - ke;
+    L.r0[o] = b0 - ke;
 }
 
 template <class T>
@@ -198,12 +219,12 @@ template <class T>
 __global__ void k_restrict_split(Transfer<T> X, SLev<T> F, SLev<T> C) {
     const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     const int J = 1 + blockIdx.y, K = 1 + blockIdx.z;
-    const int ncx = C.G.nx, ncy = C.G.ny;
+    const int ncx = C.nx, ncy = C.ny;
     if (I > ncx - 2) return;
     const int cc = (I + J + K) & 1;
-    const int64_t oc = ((int64_t)K * ncy + J) * C.hp + (I >> 1);
-    if (!is_unknown(C.ty[cc * C.Nh + oc])) return;
-    const int nfy = F.G.ny;
+    const unsigned oc = (unsigned)(K * ncy + J) * (unsigned)C.hp + (unsigned)(I >> 1);
+    if (!is_unknown((cc ? C.ty[1] : C.ty[0])[oc])) return;
+    const int nfy = F.ny;
     const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
     T wx[3], wy[3], wz[3];
     for (int q = 0; q < 3; ++q) {
@@ -211,57 +232,76 @@ __global__ void k_restrict_split(Transfer<T> X, SLev<T> F, SLev<T> C) {
         wy[q] = weight_to(X.ax[1], fj - 1 + q, J);
         wz[q] = weight_to(X.ax[2], fk - 1 + q, K);
     }
-    const T* __restrict__ r0 = F.v + R0 * F.Nh;
+    const T* __restrict__ r0 = F.r0;
     T s = 0, w = 0;
     for (int c = 0; c < 3; ++c) {
         const int k = fk - 1 + c;
         for (int b = 0; b < 3; ++b) {
             const int j = fj - 1 + b;
             const T wyz = wy[b] * wz[c];
-            const int64_t rowo = ((int64_t)k * nfy + j) * F.hp;
+            const unsigned rowo = (unsigned)(k * nfy + j) * (unsigned)F.hp;
             for (int a = 0; a < 3; ++a) {
                 const int i = fi - 1 + a;
                 const T ww = wx[a] * wyz;
                 w += ww;
-                if (((i + j + k) & 1) == 0) s += ww * r0[rowo + (i >> 1)];
+                if (((i + j + k) & 1) == 0) s += ww * r0[rowo + (unsigned)(i >> 1)];
             }
         }
     }
-    C.v[(B0 + cc) * C.Nh + oc] = s / w;
+    (cc ? C.b[1] : C.b[0])[oc] = s / w;
 }
 
 // e1 += P e_c at the fine black unknowns (the red values are overwritten by
 // the next red half-sweep without being read).
 template <class T>
 __global__ void __launch_bounds__(kSplitThreads) k_prolong_split(Transfer<T> X, SLev<T> F, SLev<T> C) {
-    const int nx = F.G.nx, ny = F.G.ny;
+    const int nx = F.nx, ny = F.ny;
     const int m = blockIdx.x * kSplitThreads + threadIdx.x;
     const int j = 1 + blockIdx.y, k = 1 + blockIdx.z;
     if (2 * m > nx - 2) return;
     const int i = 2 * m + ((1 + j + k) & 1);
     if (i < 1 || i > nx - 2) return;
-    const int64_t o = ((int64_t)k * ny + j) * F.hp + m;
-    const uint8_t t = F.ty[F.Nh + o];
+    const unsigned o = (unsigned)k * F.hs + (unsigned)(j * F.hp + m);
+    const uint8_t t = F.ty[1][o];
     const int I = X.ax[0].ilo[i], J = X.ax[1].ilo[j], K = X.ax[2].ilo[k];
     const T ax0 = X.ax[0].wlo[i], ax1 = X.ax[0].whi[i];
     const T ay0 = X.ax[1].wlo[j], ay1 = X.ax[1].whi[j];
     const T az0 = X.ax[2].wlo[k], az1 = X.ax[2].whi[k];
-    const int ncy = C.G.ny, hc = C.hp;
-    const int64_t Nc = C.Nh;
+    const unsigned hc = (unsigned)C.hp;
     // coarse (I + a, J + b, K + c): colour (I + a + J + b + K + c) & 1, entry ((K + c) * ncy + J + b) * hc + (I + a) >> 1
     const int p = (I + J + K) & 1;
-    const int64_t r00 = ((int64_t)K * ncy + J) * hc, r01 = r00 + hc, r10 = r00 + (int64_t)ncy * hc, r11 = r10 + hc;
-    const int x0 = I >> 1, x1 = (I + 1) >> 1;
-    const T* __restrict__ ea = C.v + (int64_t)p * Nc;        // colour p
-    const T* __restrict__ eb = C.v + (int64_t)(1 - p) * Nc;  // colour 1 - p
+    const unsigned r00 = (unsigned)(K * C.ny + J) * hc, r01 = r00 + hc, r10 = r00 + C.hs, r11 = r10 + hc;
+    const unsigned x0 = (unsigned)(I >> 1), x1 = (unsigned)((I + 1) >> 1);
+    const T* __restrict__ ea = p ? C.e[1] : C.e[0];  // colour p
+    const T* __restrict__ eb = p ? C.e[0] : C.e[1];  // colour 1 - p
     const T e000 = ea[r00 + x0], e001 = eb[r00 + x1], e010 = eb[r01 + x0], e011 = ea[r01 + x1];
     const T e100 = eb[r10 + x0], e101 = ea[r10 + x1], e110 = ea[r11 + x0], e111 = eb[r11 + x1];
-    T* __restrict__ e1 = F.v + E1 * F.Nh;
+    T* __restrict__ e1 = F.e[1];
     const T f0 = e1[o];
     if (!is_unknown(t)) return;
     const T v = az0 * (ay0 * (ax0 * e000 + ax1 * e001) + ay1 * (ax0 * e010 + ax1 * e011)) +
                 az1 * (ay0 * (ax0 * e100 + ax1 * e101) + ay1 * (ax0 * e110 + ax1 * e111));
     e1[o] = f0 + v;
+}
+
+// packed (ka, kb, kc) per index of each axis from a level's metric arrays
+template <class T>
+__global__ void k_pack_coefs(Grid<T> G, PkT<T>* __restrict__ out) {
+    const int n[3] = {G.nx, G.ny, G.nz};
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int d = 0; d < 3; ++d) {
+        if (q < n[d]) {
+            PkT<T> v;
+            v.x = G.ax[d].ka[q];
+            v.y = G.ax[d].kb[q];
+            v.z = G.ax[d].kc[q];
+            v.w = T(0);
+            out[q] = v;
+            return;
+        }
+        q -= n[d];
+        out += n[d];
+    }
 }
 
 // coarse type by injection: box stays box, solid stays solid, fluid -> regular
@@ -342,9 +382,31 @@ template <>
 float* svec<float>(MgLevel& L) { return L.s32; }
 
 template <class T>
+const PkT<T>* packed(MgLevel& L);
+template <>
+const PkD* packed<double>(MgLevel& L) { return static_cast<const PkD*>(L.pk64); }
+template <>
+const float4* packed<float>(MgLevel& L) { return static_cast<const float4*>(L.pk32); }
+
+template <class T>
 SLev<T> slev(cfp_ctx* c, int l) {
     MgLevel& L = c->mg[l];
-    return SLev<T>{level_grid_view<T>(c, L, l), L.stype, svec<T>(L), L.hp, L.Nh};
+    SLev<T> v;
+    v.nx = L.n[0];
+    v.ny = L.n[1];
+    v.hp = L.hp;
+    v.hs = (unsigned)((int64_t)L.hp * L.n[1]);
+    v.cx = packed<T>(L);
+    v.cy = v.cx + L.n[0];
+    v.cz = v.cy + L.n[1];
+    T* sv = svec<T>(L);
+    for (int q = 0; q < 2; ++q) {
+        v.ty[q] = L.stype + q * L.Nh;
+        v.e[q] = sv + q * L.Nh;
+        v.b[q] = sv + (2 + q) * L.Nh;
+    }
+    v.r0 = sv + 4 * L.Nh;
+    return v;
 }
 
 template <class T>
@@ -366,11 +428,12 @@ template <class T>
 void half_sweep(cfp_ctx* c, int l, const SLev<T>& L, const Side<T>& S, int colour, int mode, const T* rho, T* phi,
                 cudaStream_t s) {
     const dim3 g = pair_grid(c->mg[l].n);
+    const Half<T> H{L.ty[colour], L.e[colour], L.e[1 - colour], L.b[colour], L.b[1 - colour]};
     switch (mode) {
-        case 0: k_sweep_split<T, 0><<<g, kSplitThreads, 0, s>>>(L, S, colour, rho, phi); break;
-        case 1: k_sweep_split<T, 1><<<g, kSplitThreads, 0, s>>>(L, S, colour, rho, phi); break;
-        case 2: k_sweep_split<T, 2><<<g, kSplitThreads, 0, s>>>(L, S, colour, rho, phi); break;
-        default: k_sweep_split<T, 3><<<g, kSplitThreads, 0, s>>>(L, S, colour, rho, phi); break;
+        case 0: k_sweep_split<T, 0><<<g, kSplitThreads, 0, s>>>(L, S, H, colour, rho, phi); break;
+        case 1: k_sweep_split<T, 1><<<g, kSplitThreads, 0, s>>>(L, S, H, colour, rho, phi); break;
+        case 2: k_sweep_split<T, 2><<<g, kSplitThreads, 0, s>>>(L, S, H, colour, rho, phi); break;
+        default: k_sweep_split<T, 3><<<g, kSplitThreads, 0, s>>>(L, S, H, colour, rho, phi); break;
     }
     c->launches += 1;
 }
@@ -391,7 +454,8 @@ void smooth(cfp_ctx* c, int l, const Side<T>& S, int sweeps, int first_red, int 
 
 void free_mg(cfp_ctx* c) {
     for (MgLevel& L : c->mg) {
-        void* ptrs[] = {L.coef64, L.coef32, L.type, L.stype, L.s64, L.s32, L.ilo[0], L.ilo[1], L.ilo[2], L.w64, L.w32};
+        void* ptrs[] = {L.coef64, L.coef32, L.type, L.stype, L.s64, L.s32, L.pk64, L.pk32,
+                        L.ilo[0], L.ilo[1], L.ilo[2], L.w64, L.w32};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     }
@@ -469,6 +533,8 @@ cfp_status build_levels(cfp_ctx* c) {
         }
         L.hp = ((L.n[0] + 1) / 2 + 7) / 8 * 8;
         L.Nh = (int64_t)L.hp * L.n[1] * L.n[2];
+        if (L.Nh >= (int64_t(1) << 31))
+            return fail(CFP_EINVAL, "grid too large for the multigrid preconditioner (2^31 entries per colour)");
         const uint8_t* nat = c->type;
         if (l > 0) {
             // metrics of the coarse coordinates
@@ -501,6 +567,14 @@ cfp_status build_levels(cfp_ctx* c) {
         }
         CFP_CUDA(cudaMalloc(&L.stype, (size_t)(2 * L.Nh)));
         k_split_type<<<flat_blocks(2 * L.Nh), 256, 0, c->stream>>>(nat, L.n[0], L.n[1], L.n[2], L.hp, L.stype);
+        CFP_CUDA(cudaGetLastError());
+        // packed K coefficients of the level, both precisions
+        const int ntot = L.n[0] + L.n[1] + L.n[2];
+        CFP_CUDA(cudaMalloc(&L.pk64, sizeof(PkD) * ntot));
+        CFP_CUDA(cudaMalloc(&L.pk32, sizeof(float4) * ntot));
+        const unsigned pb = (unsigned)((ntot + 127) / 128);
+        k_pack_coefs<double><<<pb, 128, 0, c->stream>>>(level_grid_view<double>(c, L, l), static_cast<PkD*>(L.pk64));
+        k_pack_coefs<float><<<pb, 128, 0, c->stream>>>(level_grid_view<float>(c, L, l), static_cast<float4*>(L.pk32));
         CFP_CUDA(cudaGetLastError());
     }
     CFP_CUDA(cudaStreamSynchronize(c->stream));
