@@ -61,6 +61,32 @@ struct Side {
     const T* krow;            // 7 per slot: K diag, -x, +x, -y, +y, -z, +z
 };
 
+// Per-thread accumulator of a dot product.  FP64 operands sum in FP64.  FP32
+// operands sum in FP32 with a compensated (Kahan) sum, converted to FP64 once
+// per thread: no FP64 arithmetic per term (GB300 issues FP64 at 1/58 of the
+// FP32 rate, which made the FP64 pipe the limit of the FP32 kernels) and no
+// branch in the loop, with an error of a few FP32 roundings of the sum
+// instead of one per term.
+template <class T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x, double y) { s += x * y; }
+    __device__ __forceinline__ double total() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+    float s = 0.0f, c = 0.0f;  // running sum and its lost low-order part (negated)
+    __device__ __forceinline__ void add(float x, float y) {
+        const float v = fmaf(x, y, -c);
+        const float t = s + v;
+        c = (t - s) - v;
+        s = t;
+    }
+    __device__ __forceinline__ double total() const { return (double)s - (double)c; }
+};
+
 // Device-resident scalars of one BiCGSTAB run (Algorithm 1).
 struct KState {
     double rho, alpha, omega, beta;

@@ -57,14 +57,15 @@ __device__ void sum_partials(const double* partial, int nb, double& a, double& b
 template <class T>
 __global__ void k_init_r(const T* __restrict__ b, const T* __restrict__ v, T* __restrict__ r, T* __restrict__ rh,
                          T* __restrict__ p, double* __restrict__ partial, int64_t N) {
-    double a = 0.0, z = 0.0;
+    DotAcc<T> aa;
     GRID_STRIDE(l, N) {
         const T x = b[l] - v[l];
         r[l] = x;
         rh[l] = x;
         p[l] = x;
-        a += (double)x * (double)x;
+        aa.add(x, x);
     }
+    double a = aa.total(), z = 0.0;
     block_sum2(a, z);
     if (threadIdx.x == 0) {
         partial[2 * blockIdx.x] = a;
@@ -90,14 +91,15 @@ __global__ void k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __res
                             double* __restrict__ partial, int64_t N) {
     if (st->flag != FLAG_RUN) return;
     const T alpha = (T)st->alpha, omega = (T)st->omega;
-    double a = 0.0, b = 0.0;
+    DotAcc<T> aa, bb;
     GRID_STRIDE(l, N) {
         x[l] += alpha * ph[l] + omega * sh[l];
         const T rn = s[l] - omega * t[l];
         r[l] = rn;
-        a += (double)rh[l] * (double)rn;
-        b += (double)rn * (double)rn;
+        aa.add(rh[l], rn);
+        bb.add(rn, rn);
     }
+    double a = aa.total(), b = bb.total();
     block_sum2(a, b);
     if (threadIdx.x == 0) {
         partial[2 * blockIdx.x] = a;

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kAX)
     uint8_t t_next = type[lout0];
     T d_next = DOT ? d0[lout0] : T(0);
     T Pm = 0, P0 = 0, Pp = 0, Qm = 0, Q0 = 0, Qp = 0;
-    double acc0 = 0.0, acc1 = 0.0;
+    DotAcc<T> dacc0, dacc1;
     for (int kk = k0 - 1; kk <= k1; ++kk) {
         T c[9];
 #pragma unroll
@@ -168,11 +168,12 @@ __global__ void __launch_bounds__(kAX)
             const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
             if (t_cur == CFP_SOLID) v = 0;  // irregular rows: k_apply_corr adds their corrections
             y[l] = v;
-            if (DOT >= 1) acc0 += (double)d_cur * (double)v;
-            if (DOT == 2) acc1 += (double)v * (double)v;
+            if (DOT >= 1) dacc0.add(d_cur, v);
+            if (DOT == 2) dacc1.add(v, v);
         }
     }
     if (DOT) {
+        double acc0 = dacc0.total(), acc1 = dacc1.total();
         block_reduce2(acc0, acc1);
         if (threadIdx.x == 0) {
             const int64_t b = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
