@@ -72,7 +72,7 @@ using PkT = typename Pk<T>::type;
 // 32-bit (the level build rejects arrays of 2^31 entries or more)
 template <class T>
 struct SLev {
-    int nx, ny;
+    int nx, ny, nz;
     int hp;                     // entries per row of one colour
     unsigned hs;                // hp * ny
     const PkT<T>* cx;           // packed K coefficients per axis index
@@ -121,62 +121,114 @@ __device__ __forceinline__ void k_row(const SLev<T>& L, const Side<T>& S, uint8_
 __device__ __forceinline__ float times_rcp(float x, float d) { return x * __frcp_rn(d); }
 __device__ __forceinline__ double times_rcp(double x, double d) { return x * __drcp_rn(d); }
 
-// One red-black half-sweep of colour `colour` on a split level.  Thread
-// (m, j, k) owns the pair of nodes i = 2m, 2m + 1 of row (j, k); its node of
-// this colour is i = 2m + par.  Its x-neighbours (the other colour) sit at
-// entries m - 1 + par and m + par of the other colour's row.  Every load is
-// in bounds for every thread that passes the first test (rows j, k and the
-// pair are interior, entry m - 1 exists for m = 0 because the row is not the
-// first), so all of them are issued before the type decides whether the
-// value is stored.
+// One red-black half-sweep of colour `colour` on a split level, with K's
+// regular coefficients at every node.  Thread (m, j, k0 + q), q <
+// kSweepPlanes, owns the pair of nodes i = 2m, 2m + 1 of rows (j, k0 + q);
+// its node of this colour is i = 2m + par.  Its x-neighbours (the other
+// colour) sit at entries m - 1 + par and m + par of the other colour's row.
+// Every load is in bounds for every thread that passes the first test (rows
+// j, k and the pair are interior, entry m - 1 exists for m = 0 because the
+// row is not the first; planes past the last interior one repeat plane k0
+// and store nothing), so the loads of all kSweepPlanes nodes are issued
+// before any value is stored: three independent nodes per thread keep more
+// loads in flight.  The Shortley-Weller rows of the fine level's irregular
+// nodes are applied afterwards by k_sweep_fix (no node reads another of its
+// own colour, so the order within the half-sweep does not matter).
 // MODE 0: plain; 1: from zero (the other colour is taken as zero);
 // 2: from zero, and b of both colours is first read from the natural-layout
 //    rho; 3: plain, and both nodes of the pair are written to the
 //    natural-layout phi (the own node's new value is not stored).
+constexpr int kSweepPlanes = 3;
+
 template <class T, int MODE>
 __global__ void __launch_bounds__(kSplitThreads)
-    k_sweep_split(SLev<T> L, Side<T> S, Half<T> H, int colour, const T* __restrict__ rho, T* __restrict__ phi) {
+    k_sweep_split(SLev<T> L, Half<T> H, int colour, const T* __restrict__ rho, T* __restrict__ phi) {
     const int nx = L.nx;
     const int m = blockIdx.x * kSplitThreads + threadIdx.x;
-    const int j = 1 + blockIdx.y, k = 1 + blockIdx.z;
+    const int j = 1 + blockIdx.y, k0 = 1 + kSweepPlanes * blockIdx.z;
     if (2 * m > nx - 2) return;
-    const int par = (colour + j + k) & 1;
-    const int i = 2 * m + par, io = 2 * m + 1 - par;
     const int hp = L.hp;
     const unsigned hs = L.hs;
-    const unsigned o = (unsigned)k * hs + (unsigned)(j * hp + m);
     const T* __restrict__ eoth = H.eoth;
-    const int64_t row = ((int64_t)k * L.ny + j) * nx;
-    const uint8_t t = H.ty[o];
-    const T bv = MODE == 2 ? rho[row + i] : H.bown[o];
-    T xm = T(0), xp = T(0), ym = T(0), yp = T(0), zm = T(0), zp = T(0);
-    if (MODE == 0 || MODE == 3) {
-        xm = eoth[o - 1 + par];
-        xp = eoth[o + par];
-        ym = eoth[o - hp];
-        yp = eoth[o + hp];
-        zm = eoth[o - hs];
-        zp = eoth[o + hs];
+    T val[kSweepPlanes], bv[kSweepPlanes], bo[kSweepPlanes], xo[kSweepPlanes];
+    bool inz[kSweepPlanes], live[kSweepPlanes];
+    unsigned oo[kSweepPlanes];
+#pragma unroll
+    for (int q = 0; q < kSweepPlanes; ++q) {
+        inz[q] = k0 + q <= L.nz - 2;
+        const int k = inz[q] ? k0 + q : k0;
+        const int par = (colour + j + k) & 1;
+        const int i = 2 * m + par, io = 2 * m + 1 - par;
+        const unsigned o = (unsigned)k * hs + (unsigned)(j * hp + m);
+        const int64_t row = ((int64_t)k * L.ny + j) * nx;
+        const uint8_t t = H.ty[o];
+        bv[q] = MODE == 2 ? rho[row + i] : H.bown[o];
+        if (MODE == 2) bo[q] = rho[row + io];
+        T xm = T(0), xp = T(0), ym = T(0), yp = T(0), zm = T(0), zp = T(0);
+        if (MODE == 0 || MODE == 3) {
+            xm = eoth[o - 1 + par];
+            xp = eoth[o + par];
+            ym = eoth[o - hp];
+            yp = eoth[o + hp];
+            zm = eoth[o - hs];
+            zp = eoth[o + hs];
+        }
+        const PkT<T> ckx = L.cx[i], cky = L.cy[j], ckz = L.cz[k];
+        const T dg = ckx.y + (cky.y + ckz.y);
+        live[q] = inz[q] && i >= 1 && i <= nx - 2 && is_unknown(t);
+        T v = bv[q];
+        if (MODE == 0 || MODE == 3)
+            v -= (ckx.x * xm + ckx.z * xp) + (cky.x * ym + cky.z * yp) + (ckz.x * zm + ckz.z * zp);
+        val[q] = times_rcp(v, dg);
+        xo[q] = par ? xm : xp;  // MODE 3: the other node of the pair
+        oo[q] = o;
     }
-    const PkT<T> ckx = L.cx[i], cky = L.cy[j], ckz = L.cz[k];
-    T dg = ckx.y + (cky.y + ckz.y);
-    T cxm = ckx.x, cxp = ckx.z, cym = cky.x, cyp = cky.z, czm = ckz.x, czp = ckz.z;
-    if (MODE == 2) {
-        H.bown[o] = bv;
-        H.both[o] = rho[row + io];
+#pragma unroll
+    for (int q = 0; q < kSweepPlanes; ++q) {
+        if (!inz[q]) continue;
+        const unsigned o = oo[q];
+        if (MODE == 2) {
+            H.bown[o] = bv[q];
+            H.both[o] = bo[q];
+        }
+        if (MODE == 3) {
+            const int k = k0 + q;
+            const int par = (colour + j + k) & 1;
+            const int i = 2 * m + par, io = 2 * m + 1 - par;
+            const int64_t row = ((int64_t)k * L.ny + j) * nx;
+            if (i >= 1 && i <= nx - 2) phi[row + i] = live[q] ? val[q] : T(0);
+            if (io >= 1 && io <= nx - 2) phi[row + io] = xo[q];
+        } else if (live[q]) {
+            H.eown[o] = val[q];
+        }
     }
-    const bool live = i >= 1 && i <= nx - 2 && is_unknown(t);
-    k_row(L, S, t, i, j, k, dg, cxm, cxp, cym, cyp, czm, czp);
-    T v = bv;
-    if (MODE == 0 || MODE == 3)
-        v -= (cxm * xm + cxp * xp) + (cym * ym + cyp * yp) + (czm * zm + czp * zp);
-    v = times_rcp(v, dg);
-    if (MODE == 3) {
-        if (i >= 1 && i <= nx - 2) phi[row + i] = live ? v : T(0);
-        if (io >= 1 && io <= nx - 2) phi[row + io] = par ? xm : xp;  // the other node of the pair
-        return;
+}
+
+// The half-sweep's update at the fine level's irregular nodes of colour
+// `colour`, with their Shortley-Weller rows (Eq. A7_mod); one thread per
+// irregular point.  Runs right after k_sweep_split of the same colour and
+// mode, overwriting what it stored there.
+template <class T, int MODE>
+__global__ void k_sweep_fix(SLev<T> L, Side<T> S, Half<T> H, const int32_t* __restrict__ irr_lin, int64_t n_irr,
+                            int colour, T* __restrict__ phi) {
+    const int nx = L.nx, ny = L.ny;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_irr; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = irr_lin[s];
+        const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((int64_t)nx * ny));
+        if (((i + j + k) & 1) != colour) continue;
+        const int par = i & 1;
+        const unsigned o = (unsigned)k * L.hs + (unsigned)(j * L.hp + (i >> 1));
+        const T* kr = S.krow + 7 * s;
+        T v = H.bown[o];
+        if (MODE == 0 || MODE == 3) {
+            const T* __restrict__ eoth = H.eoth;
+            v -= (kr[1] * eoth[o - 1 + par] + kr[2] * eoth[o + par]) + (kr[3] * eoth[o - L.hp] + kr[4] * eoth[o + L.hp]) +
+                 (kr[5] * eoth[o - L.hs] + kr[6] * eoth[o + L.hs]);
+        }
+        v = times_rcp(v, kr[0]);
+        if (MODE == 3) phi[l] = v;
+        else H.eown[o] = v;
     }
-    if (live) H.eown[o] = v;
 }
 
 // r0 = b0 - K e at the red unknowns (black residuals are zero after a
@@ -394,6 +446,7 @@ SLev<T> slev(cfp_ctx* c, int l) {
     SLev<T> v;
     v.nx = L.n[0];
     v.ny = L.n[1];
+    v.nz = L.n[2];
     v.hp = L.hp;
     v.hs = (unsigned)((int64_t)L.hp * L.n[1]);
     v.cx = packed<T>(L);
@@ -427,15 +480,27 @@ Transfer<float> transfer<float>(MgLevel& F) {
 template <class T>
 void half_sweep(cfp_ctx* c, int l, const SLev<T>& L, const Side<T>& S, int colour, int mode, const T* rho, T* phi,
                 cudaStream_t s) {
-    const dim3 g = pair_grid(c->mg[l].n);
+    const int* n = c->mg[l].n;
+    const dim3 g((unsigned)((n[0] / 2 + kSplitThreads - 1) / kSplitThreads), (unsigned)(n[1] - 2),
+                 (unsigned)((n[2] - 2 + kSweepPlanes - 1) / kSweepPlanes));
     const Half<T> H{L.ty[colour], L.e[colour], L.e[1 - colour], L.b[colour], L.b[1 - colour]};
     switch (mode) {
-        case 0: k_sweep_split<T, 0><<<g, kSplitThreads, 0, s>>>(L, S, H, colour, rho, phi); break;
-        case 1: k_sweep_split<T, 1><<<g, kSplitThreads, 0, s>>>(L, S, H, colour, rho, phi); break;
-        case 2: k_sweep_split<T, 2><<<g, kSplitThreads, 0, s>>>(L, S, H, colour, rho, phi); break;
-        default: k_sweep_split<T, 3><<<g, kSplitThreads, 0, s>>>(L, S, H, colour, rho, phi); break;
+        case 0: k_sweep_split<T, 0><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
+        case 1: k_sweep_split<T, 1><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
+        case 2: k_sweep_split<T, 2><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
+        default: k_sweep_split<T, 3><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
     }
     c->launches += 1;
+    if (l == 0 && c->n_irr > 0) {  // the Shortley-Weller rows of the irregular nodes
+        const unsigned nb = (unsigned)std::min<int64_t>((c->n_irr + 255) / 256, 152 * 8);
+        switch (mode) {
+            case 0: k_sweep_fix<T, 0><<<nb, 256, 0, s>>>(L, S, H, c->irr_lin, c->n_irr, colour, phi); break;
+            case 1: k_sweep_fix<T, 1><<<nb, 256, 0, s>>>(L, S, H, c->irr_lin, c->n_irr, colour, phi); break;
+            case 2: k_sweep_fix<T, 2><<<nb, 256, 0, s>>>(L, S, H, c->irr_lin, c->n_irr, colour, phi); break;
+            default: k_sweep_fix<T, 3><<<nb, 256, 0, s>>>(L, S, H, c->irr_lin, c->n_irr, colour, phi); break;
+        }
+        c->launches += 1;
+    }
 }
 
 // `sweeps` red-black sweeps at level l.  first_red / last_black: the modes of
