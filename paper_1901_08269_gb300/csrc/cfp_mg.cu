@@ -98,24 +98,6 @@ enum { kSplitVecs = 5 };  // e0 e1 b0 b1 r0
 
 __device__ __forceinline__ bool is_unknown(uint8_t t) { return t == CFP_REGULAR || t == CFP_IRREGULAR; }
 
-// K's row at a node: the packed regular coefficients, or the Shortley-Weller
-// row of an irregular node of the fine level (krow, natural index l)
-template <class T>
-__device__ __forceinline__ void k_row(const SLev<T>& L, const Side<T>& S, uint8_t t, int i, int j, int k,
-                                      T& dg, T& cxm, T& cxp, T& cym, T& cyp, T& czm, T& czp) {
-    if (t == CFP_IRREGULAR) {
-        const int64_t l = ((int64_t)k * L.ny + j) * L.nx + i;
-        const T* kr = S.krow + 7 * (int64_t)S.slot[l];
-        dg = kr[0];
-        cxm = kr[1];
-        cxp = kr[2];
-        cym = kr[3];
-        cyp = kr[4];
-        czm = kr[5];
-        czp = kr[6];
-    }
-}
-
 // x * (1 / d) with a correctly rounded reciprocal: two roundings instead of
 // the division's one, several times cheaper than an IEEE division.
 __device__ __forceinline__ float times_rcp(float x, float d) { return x * __frcp_rn(d); }
@@ -231,31 +213,62 @@ __global__ void k_sweep_fix(SLev<T> L, Side<T> S, Half<T> H, const int32_t* __re
     }
 }
 
-// r0 = b0 - K e at the red unknowns (black residuals are zero after a
-// black half-sweep; r0 stays zero at the other red entries).  Loads are
-// issued before the type test, as in the half-sweep.
+// r0 = b0 - K e at the red unknowns with K's regular coefficients (black
+// residuals are zero after a black half-sweep; r0 stays zero at the other
+// red entries); three planes per thread with all loads first, as in the
+// half-sweep.  k_resid_fix then redoes the fine level's irregular red nodes.
 template <class T>
-__global__ void __launch_bounds__(kSplitThreads) k_resid_split(SLev<T> L, Side<T> S) {
+__global__ void __launch_bounds__(kSplitThreads) k_resid_split(SLev<T> L) {
     const int nx = L.nx;
     const int m = blockIdx.x * kSplitThreads + threadIdx.x;
-    const int j = 1 + blockIdx.y, k = 1 + blockIdx.z;
+    const int j = 1 + blockIdx.y, k0 = 1 + kSweepPlanes * blockIdx.z;
     if (2 * m > nx - 2) return;
-    const int par = (j + k) & 1;
-    const int i = 2 * m + par;
     const int hp = L.hp;
     const unsigned hs = L.hs;
-    const unsigned o = (unsigned)k * hs + (unsigned)(j * hp + m);
     const T* __restrict__ e1 = L.e[1];
-    const uint8_t t = L.ty[0][o];
-    const T e0 = L.e[0][o], b0 = L.b[0][o];
-    const T xm = e1[o - 1 + par], xp = e1[o + par], ym = e1[o - hp], yp = e1[o + hp], zm = e1[o - hs], zp = e1[o + hs];
-    const PkT<T> ckx = L.cx[i], cky = L.cy[j], ckz = L.cz[k];
-    T dg = ckx.y + (cky.y + ckz.y);
-    T cxm = ckx.x, cxp = ckx.z, cym = cky.x, cyp = cky.z, czm = ckz.x, czp = ckz.z;
-    if (i < 1 || i > nx - 2 || !is_unknown(t)) return;
-    k_row(L, S, t, i, j, k, dg, cxm, cxp, cym, cyp, czm, czp);
-    const T ke = dg * e0 + (cxm * xm + cxp * xp) + (cym * ym + cyp * yp) + (czm * zm + czp * zp);
-    L.r0[o] = b0 - ke;
+    T rv[kSweepPlanes];
+    bool live[kSweepPlanes];
+    unsigned oo[kSweepPlanes];
+#pragma unroll
+    for (int q = 0; q < kSweepPlanes; ++q) {
+        const bool inz = k0 + q <= L.nz - 2;
+        const int k = inz ? k0 + q : k0;
+        const int par = (j + k) & 1;
+        const int i = 2 * m + par;
+        const unsigned o = (unsigned)k * hs + (unsigned)(j * hp + m);
+        const uint8_t t = L.ty[0][o];
+        const T e0 = L.e[0][o], b0 = L.b[0][o];
+        const T xm = e1[o - 1 + par], xp = e1[o + par], ym = e1[o - hp], yp = e1[o + hp], zm = e1[o - hs],
+                zp = e1[o + hs];
+        const PkT<T> ckx = L.cx[i], cky = L.cy[j], ckz = L.cz[k];
+        const T dg = ckx.y + (cky.y + ckz.y);
+        const T ke = dg * e0 + (ckx.x * xm + ckx.z * xp) + (cky.x * ym + cky.z * yp) + (ckz.x * zm + ckz.z * zp);
+        rv[q] = b0 - ke;
+        live[q] = inz && i >= 1 && i <= nx - 2 && is_unknown(t);
+        oo[q] = o;
+    }
+#pragma unroll
+    for (int q = 0; q < kSweepPlanes; ++q)
+        if (live[q]) L.r0[oo[q]] = rv[q];
+}
+
+// the red residual at the fine level's irregular red nodes with their
+// Shortley-Weller rows (after k_resid_split)
+template <class T>
+__global__ void k_resid_fix(SLev<T> L, Side<T> S, const int32_t* __restrict__ irr_lin, int64_t n_irr) {
+    const int nx = L.nx, ny = L.ny;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_irr; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = irr_lin[s];
+        const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((int64_t)nx * ny));
+        if (((i + j + k) & 1) != 0) continue;
+        const int par = i & 1;
+        const unsigned o = (unsigned)k * L.hs + (unsigned)(j * L.hp + (i >> 1));
+        const T* kr = S.krow + 7 * s;
+        const T* __restrict__ e1 = L.e[1];
+        const T ke = kr[0] * L.e[0][o] + (kr[1] * e1[o - 1 + par] + kr[2] * e1[o + par]) +
+                     (kr[3] * e1[o - L.hp] + kr[4] * e1[o + L.hp]) + (kr[5] * e1[o - L.hs] + kr[6] * e1[o + L.hs]);
+        L.r0[o] = L.b[0][o] - ke;
+    }
 }
 
 template <class T>
@@ -304,36 +317,49 @@ __global__ void k_restrict_split(Transfer<T> X, SLev<T> F, SLev<T> C) {
 }
 
 // e1 += P e_c at the fine black unknowns (the red values are overwritten by
-// the next red half-sweep without being read).
+// the next red half-sweep without being read); three planes per thread.
 template <class T>
 __global__ void __launch_bounds__(kSplitThreads) k_prolong_split(Transfer<T> X, SLev<T> F, SLev<T> C) {
-    const int nx = F.nx, ny = F.ny;
+    const int nx = F.nx;
     const int m = blockIdx.x * kSplitThreads + threadIdx.x;
-    const int j = 1 + blockIdx.y, k = 1 + blockIdx.z;
+    const int j = 1 + blockIdx.y, k0 = 1 + kSweepPlanes * blockIdx.z;
     if (2 * m > nx - 2) return;
-    const int i = 2 * m + ((1 + j + k) & 1);
-    if (i < 1 || i > nx - 2) return;
-    const unsigned o = (unsigned)k * F.hs + (unsigned)(j * F.hp + m);
-    const uint8_t t = F.ty[1][o];
-    const int I = X.ax[0].ilo[i], J = X.ax[1].ilo[j], K = X.ax[2].ilo[k];
-    const T ax0 = X.ax[0].wlo[i], ax1 = X.ax[0].whi[i];
-    const T ay0 = X.ax[1].wlo[j], ay1 = X.ax[1].whi[j];
-    const T az0 = X.ax[2].wlo[k], az1 = X.ax[2].whi[k];
     const unsigned hc = (unsigned)C.hp;
-    // coarse (I + a, J + b, K + c): colour (I + a + J + b + K + c) & 1, entry ((K + c) * ncy + J + b) * hc + (I + a) >> 1
-    const int p = (I + J + K) & 1;
-    const unsigned r00 = (unsigned)(K * C.ny + J) * hc, r01 = r00 + hc, r10 = r00 + C.hs, r11 = r10 + hc;
-    const unsigned x0 = (unsigned)(I >> 1), x1 = (unsigned)((I + 1) >> 1);
-    const T* __restrict__ ea = p ? C.e[1] : C.e[0];  // colour p
-    const T* __restrict__ eb = p ? C.e[0] : C.e[1];  // colour 1 - p
-    const T e000 = ea[r00 + x0], e001 = eb[r00 + x1], e010 = eb[r01 + x0], e011 = ea[r01 + x1];
-    const T e100 = eb[r10 + x0], e101 = ea[r10 + x1], e110 = ea[r11 + x0], e111 = eb[r11 + x1];
+    const int J = X.ax[1].ilo[j];
+    const T ay0 = X.ax[1].wlo[j], ay1 = X.ax[1].whi[j];
     T* __restrict__ e1 = F.e[1];
-    const T f0 = e1[o];
-    if (!is_unknown(t)) return;
-    const T v = az0 * (ay0 * (ax0 * e000 + ax1 * e001) + ay1 * (ax0 * e010 + ax1 * e011)) +
-                az1 * (ay0 * (ax0 * e100 + ax1 * e101) + ay1 * (ax0 * e110 + ax1 * e111));
-    e1[o] = f0 + v;
+    T val[kSweepPlanes];
+    bool live[kSweepPlanes];
+    unsigned oo[kSweepPlanes];
+#pragma unroll
+    for (int q = 0; q < kSweepPlanes; ++q) {
+        const bool inz = k0 + q <= F.nz - 2;
+        const int k = inz ? k0 + q : k0;
+        const int i = 2 * m + ((1 + j + k) & 1);
+        const int ic = i <= nx - 2 ? i : nx - 2;  // every load stays inside the tables and the level
+        const unsigned o = (unsigned)k * F.hs + (unsigned)(j * F.hp + m);
+        const uint8_t t = F.ty[1][o];
+        const int I = X.ax[0].ilo[ic], K = X.ax[2].ilo[k];
+        const T ax0 = X.ax[0].wlo[ic], ax1 = X.ax[0].whi[ic];
+        const T az0 = X.ax[2].wlo[k], az1 = X.ax[2].whi[k];
+        // coarse (I + a, J + b, K + c): colour (I + a + J + b + K + c) & 1,
+        // entry ((K + c) * ncy + J + b) * hc + (I + a) >> 1
+        const int p = (I + J + K) & 1;
+        const unsigned r00 = (unsigned)(K * C.ny + J) * hc, r01 = r00 + hc, r10 = r00 + C.hs, r11 = r10 + hc;
+        const unsigned x0 = (unsigned)(I >> 1), x1 = (unsigned)((I + 1) >> 1);
+        const T* __restrict__ ea = p ? C.e[1] : C.e[0];  // colour p
+        const T* __restrict__ eb = p ? C.e[0] : C.e[1];  // colour 1 - p
+        const T e000 = ea[r00 + x0], e001 = eb[r00 + x1], e010 = eb[r01 + x0], e011 = ea[r01 + x1];
+        const T e100 = eb[r10 + x0], e101 = ea[r10 + x1], e110 = ea[r11 + x0], e111 = eb[r11 + x1];
+        const T f0 = e1[o];
+        val[q] = f0 + (az0 * (ay0 * (ax0 * e000 + ax1 * e001) + ay1 * (ax0 * e010 + ax1 * e011)) +
+                       az1 * (ay0 * (ax0 * e100 + ax1 * e101) + ay1 * (ax0 * e110 + ax1 * e111)));
+        live[q] = inz && i >= 1 && i <= nx - 2 && is_unknown(t);
+        oo[q] = o;
+    }
+#pragma unroll
+    for (int q = 0; q < kSweepPlanes; ++q)
+        if (live[q]) e1[oo[q]] = val[q];
 }
 
 // packed (ka, kb, kc) per index of each axis from a level's metric arrays
@@ -386,9 +412,12 @@ __global__ void k_split_type(const uint8_t* __restrict__ nat, int nx, int ny, in
 
 unsigned flat_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
 
-dim3 pair_grid(const int n[3]) {
-    const int pairs = n[0] / 2;  // m = 0 .. (n_x - 2) / 2
-    return dim3((unsigned)((pairs + kSplitThreads - 1) / kSplitThreads), (unsigned)(n[1] - 2), (unsigned)(n[2] - 2));
+// threads over the pairs m = 0 .. (n_x - 2) / 2 and the interior rows j;
+// blocks over groups of kSweepPlanes interior planes
+dim3 plane_grid(const int n[3]) {
+    const int pairs = n[0] / 2;
+    return dim3((unsigned)((pairs + kSplitThreads - 1) / kSplitThreads), (unsigned)(n[1] - 2),
+                (unsigned)((n[2] - 2 + kSweepPlanes - 1) / kSweepPlanes));
 }
 
 template <class T>
@@ -480,9 +509,7 @@ Transfer<float> transfer<float>(MgLevel& F) {
 template <class T>
 void half_sweep(cfp_ctx* c, int l, const SLev<T>& L, const Side<T>& S, int colour, int mode, const T* rho, T* phi,
                 cudaStream_t s) {
-    const int* n = c->mg[l].n;
-    const dim3 g((unsigned)((n[0] / 2 + kSplitThreads - 1) / kSplitThreads), (unsigned)(n[1] - 2),
-                 (unsigned)((n[2] - 2 + kSweepPlanes - 1) / kSweepPlanes));
+    const dim3 g = plane_grid(c->mg[l].n);
     const Half<T> H{L.ty[colour], L.e[colour], L.e[1 - colour], L.b[colour], L.b[1 - colour]};
     switch (mode) {
         case 0: k_sweep_split<T, 0><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
@@ -691,7 +718,12 @@ void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
         const Side<T>& S = l == 0 ? S0 : Sc;
         smooth<T>(c, l, S, nu, l == 0 ? 2 : 1, 0, rho, phi, s);
         const SLev<T> F = slev<T>(c, l), C = slev<T>(c, l + 1);
-        k_resid_split<T><<<pair_grid(c->mg[l].n), kSplitThreads, 0, s>>>(F, S);
+        k_resid_split<T><<<plane_grid(c->mg[l].n), kSplitThreads, 0, s>>>(F);
+        if (l == 0 && c->n_irr > 0) {
+            k_resid_fix<T><<<(unsigned)std::min<int64_t>((c->n_irr + 255) / 256, 152 * 8), 256, 0, s>>>(
+                F, S, c->irr_lin, c->n_irr);
+            c->launches += 1;
+        }
         const MgLevel& Cn = c->mg[l + 1];
         const dim3 gr((unsigned)((Cn.n[0] - 2 + 127) / 128), (unsigned)(Cn.n[1] - 2), (unsigned)(Cn.n[2] - 2));
         k_restrict_split<T><<<gr, 128, 0, s>>>(transfer<T>(c->mg[l]), F, C);
@@ -702,7 +734,7 @@ void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
     // fine level writes phi
     for (int l = nl - 2; l >= 0; --l) {
         const SLev<T> F = slev<T>(c, l), C = slev<T>(c, l + 1);
-        k_prolong_split<T><<<pair_grid(c->mg[l].n), kSplitThreads, 0, s>>>(transfer<T>(c->mg[l]), F, C);
+        k_prolong_split<T><<<plane_grid(c->mg[l].n), kSplitThreads, 0, s>>>(transfer<T>(c->mg[l]), F, C);
         c->launches += 1;
         smooth<T>(c, l, l == 0 ? S0 : Sc, nu, 0, l == 0 ? 3 : 0, rho, phi, s);
     }
