@@ -84,23 +84,32 @@ __device__ __forceinline__ void block_reduce2(double& a, double& b) {
     }
 }
 
-// Regular part of B x at the unknowns.  One thread owns the column (i, j) and marches
-// kApplyKC planes in z.  Per plane it loads the 3 x 3 values x(i-1..i+1,
-// j-1..j+1) (the x and y neighbours come from L1/L2; the loads of the next
-// plane are issued before the current one is used), forms the x-pass
-// XR = Rx x, XL = Lx x of its three rows, the y-pass P = Ly XR + Ry XL,
-// Q = Ly XL, and keeps P, Q of three planes in registers for the z-pass
+// Regular part of B x at the unknowns.  One thread owns the columns (i, j)
+// of kApplyRows<T> consecutive rows j and marches kApplyKC planes in z.  Per
+// plane it loads the values x(i-1..i+1, j) of the rows j0-1 .. j0+TY (the x
+// and y neighbours come from L1/L2; the loads of the next plane are issued
+// before the current one is used), forms the x-pass XR = Rx x, XL = Lx x of
+// those rows (each shared by up to three output rows), the y-pass
+// P = Ly XR + Ry XL, Q = Ly XL of its rows, and keeps P, Q of three planes
+// in registers for the z-pass
 //   out(k) = Lz (P(k-1), P(k), P(k+1)) + Rz (Q(k-1), Q(k), Q(k+1)).
 // No shared memory and no barriers.  Solid rows are zero; the rows of
 // irregular points get their side-list corrections from k_apply_corr.
 // DOT = 0: y only; 1: partial (d0, y); 2: partials (d0, y) and (y, y).
+template <class T>
+struct ApplyRows {
+    static constexpr int value = 2;
+};
+
 template <class T, int DOT>
-__global__ void __launch_bounds__(kAX)
+__global__ void __launch_bounds__(kAX, sizeof(T) == 4 ? 8 : 1)
     k_apply(Grid<T> G, Side<T> S, const uint8_t* __restrict__ type, const T* __restrict__ x,
             T* __restrict__ y, const T* __restrict__ d0, double* __restrict__ partial) {
+    constexpr int TY = ApplyRows<T>::value;
+    constexpr int R = TY + 2;  // rows loaded per plane
     const int nx = G.nx, ny = G.ny, nz = G.nz;
     const int i = 1 + blockIdx.x * kAX + threadIdx.x;
-    const int j = 1 + blockIdx.y;
+    const int j0 = 1 + blockIdx.y * TY;
     const int k0 = 1 + blockIdx.z * kApplyKC;
     const int k1 = min(k0 + kApplyKC, nz - 1);
     const bool iin = i <= nx - 2;
@@ -108,68 +117,105 @@ __global__ void __launch_bounds__(kAX)
     const int64_t sy = nx, sz = (int64_t)nx * ny;
     const T ax = G.ax[0].a[ic], cx = G.ax[0].c[ic];
     const T arx = G.ax[0].ar[ic], brx = G.ax[0].br[ic], crx = G.ax[0].cr[ic];
-    const T ay = G.ax[1].a[j], cy = G.ax[1].c[j];
-    const T ary = G.ax[1].ar[j], bry = G.ax[1].br[j], cry = G.ax[1].cr[j];
-    const T* p = x + (int64_t)(k0 - 1) * sz + (int64_t)j * sy + ic;
-    T n[9];
+    T ay[TY], cy[TY], ary[TY], bry[TY], cry[TY];
+    bool jin[TY];
+    int64_t lout0[TY];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        const T* q = p + (r - 1) * sy;
+    for (int t = 0; t < TY; ++t) {
+        jin[t] = j0 + t <= ny - 2;
+        const int jc = jin[t] ? j0 + t : j0;
+        ay[t] = G.ax[1].a[jc];
+        cy[t] = G.ax[1].c[jc];
+        ary[t] = G.ax[1].ar[jc];
+        bry[t] = G.ax[1].br[jc];
+        cry[t] = G.ax[1].cr[jc];
+        lout0[t] = (int64_t)k0 * sz + (int64_t)jc * sy + ic;
+    }
+    int64_t roff[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) roff[r] = (int64_t)min(j0 - 1 + r, ny - 1) * sy;
+    const T* p = x + (int64_t)(k0 - 1) * sz + ic;
+    T n[3 * R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const T* q = p + roff[r];
         n[3 * r] = q[-1];
         n[3 * r + 1] = q[0];
         n[3 * r + 2] = q[1];
     }
-    // type byte and dot operand of the next output node
-    const int64_t lout0 = (int64_t)k0 * sz + (int64_t)j * sy + ic;
-    uint8_t t_next = type[lout0];
-    T d_next = DOT ? d0[lout0] : T(0);
-    T Pm = 0, P0 = 0, Pp = 0, Qm = 0, Q0 = 0, Qp = 0;
+    // type byte and dot operand of the next output node of each row
+    uint8_t t_next[TY];
+    T d_next[TY];
+#pragma unroll
+    for (int t = 0; t < TY; ++t) {
+        t_next[t] = type[lout0[t]];
+        d_next[t] = DOT ? d0[lout0[t]] : T(0);
+    }
+    T Pm[TY], P0[TY], Pp[TY], Qm[TY], Q0[TY], Qp[TY];
+#pragma unroll
+    for (int t = 0; t < TY; ++t) Pm[t] = P0[t] = Pp[t] = Qm[t] = Q0[t] = Qp[t] = T(0);
     DotAcc<T> dacc0, dacc1;
     for (int kk = k0 - 1; kk <= k1; ++kk) {
-        T c[9];
+        T c[3 * R];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) c[q] = n[q];
+        for (int q = 0; q < 3 * R; ++q) c[q] = n[q];
         if (kk < k1) {  // prefetch plane kk + 1
             p += sz;
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const T* q = p + (r - 1) * sy;
+            for (int r = 0; r < R; ++r) {
+                const T* q = p + roff[r];
                 n[3 * r] = q[-1];
                 n[3 * r + 1] = q[0];
                 n[3 * r + 2] = q[1];
             }
         }
         // output of this step is plane kk - 1 (from step k0 + 1 on); its type
-        // byte and dot operand were fetched one step earlier
-        const uint8_t t_cur = t_next;
-        const T d_cur = d_next;
-        if (kk >= k0 + 1 && kk < k1) {
-            const int64_t ln = lout0 + (int64_t)(kk - k0) * sz;
-            t_next = type[ln];
-            if (DOT) d_next = d0[ln];
-        }
-        T XR[3], XL[3];
+        // bytes and dot operands were fetched one step earlier
+        uint8_t t_cur[TY];
+        T d_cur[TY];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
+        for (int t = 0; t < TY; ++t) {
+            t_cur[t] = t_next[t];
+            d_cur[t] = d_next[t];
+        }
+        if (kk >= k0 + 1 && kk < k1) {
+#pragma unroll
+            for (int t = 0; t < TY; ++t) {
+                const int64_t ln = lout0[t] + (int64_t)(kk - k0) * sz;
+                t_next[t] = type[ln];
+                if (DOT) d_next[t] = d0[ln];
+            }
+        }
+        T XR[R], XL[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
             XR[r] = arx * c[3 * r] + brx * c[3 * r + 1] + crx * c[3 * r + 2];
             XL[r] = ax * c[3 * r] + c[3 * r + 1] + cx * c[3 * r + 2];
         }
-        Pm = P0;
-        P0 = Pp;
-        Qm = Q0;
-        Q0 = Qp;
-        Pp = ay * XR[0] + XR[1] + cy * XR[2] + ary * XL[0] + bry * XL[1] + cry * XL[2];
-        Qp = ay * XL[0] + XL[1] + cy * XL[2];
+#pragma unroll
+        for (int t = 0; t < TY; ++t) {
+            Pm[t] = P0[t];
+            P0[t] = Pp[t];
+            Qm[t] = Q0[t];
+            Q0[t] = Qp[t];
+            Pp[t] = ay[t] * XR[t] + XR[t + 1] + cy[t] * XR[t + 2] + ary[t] * XL[t] + bry[t] * XL[t + 1] +
+                    cry[t] * XL[t + 2];
+            Qp[t] = ay[t] * XL[t] + XL[t + 1] + cy[t] * XL[t + 2];
+        }
         if (kk >= k0 + 1 && iin) {
             const int k = kk - 1;
             const T az = G.ax[2].a[k], cz = G.ax[2].c[k];
             const T arz = G.ax[2].ar[k], brz = G.ax[2].br[k], crz = G.ax[2].cr[k];
-            T v = az * Pm + P0 + cz * Pp + (arz * Qm + brz * Q0 + crz * Qp);
-            const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
-            if (t_cur == CFP_SOLID) v = 0;  // irregular rows: k_apply_corr adds their corrections
-            y[l] = v;
-            if (DOT >= 1) dacc0.add(d_cur, v);
-            if (DOT == 2) dacc1.add(v, v);
+#pragma unroll
+            for (int t = 0; t < TY; ++t) {
+                if (!jin[t]) continue;
+                T v = az * Pm[t] + P0[t] + cz * Pp[t] + (arz * Qm[t] + brz * Q0[t] + crz * Qp[t]);
+                const int64_t l = (int64_t)k * sz + (int64_t)(j0 + t) * sy + i;
+                if (t_cur[t] == CFP_SOLID) v = 0;  // irregular rows: k_apply_corr adds their corrections
+                y[l] = v;
+                if (DOT >= 1) dacc0.add(d_cur[t], v);
+                if (DOT == 2) dacc1.add(v, v);
+            }
         }
     }
     if (DOT) {
@@ -182,13 +228,6 @@ __global__ void __launch_bounds__(kAX)
         }
     }
 }
-
-// Side-list corrections of the irregular rows (the modified stencils of
-// Secs. 2.2-2.3, the C part of Eq. Bdec), one warp per irregular point: the
-// lanes gather the merged entries in parallel, lane 0 adds the sum to y and
-// updates the dot partials: (d0, y) gains d0 c, (y, y) gains 2 v c + c^2
-// where v is the row's regular part.  Partials are written after those of
-// k_apply, one pair per CTA.
 template <class T, int DOT>
 __global__ void __launch_bounds__(256)
     k_apply_corr(Side<T> S, const int32_t* __restrict__ irr_lin, int64_t n_irr, const T* __restrict__ x,
@@ -392,8 +431,10 @@ template void launch_half_sweep<float>(const Grid<float>&, const Side<float>&, c
 
 namespace {
 
+template <class T>
 dim3 apply_grid(const cfp_ctx* c) {
-    return dim3((unsigned)((c->n[0] - 2 + kAX - 1) / kAX), (unsigned)(c->n[1] - 2),
+    constexpr int TY = ApplyRows<T>::value;
+    return dim3((unsigned)((c->n[0] - 2 + kAX - 1) / kAX), (unsigned)((c->n[1] - 2 + TY - 1) / TY),
                 (unsigned)((c->n[2] - 2 + kApplyKC - 1) / kApplyKC));
 }
 
@@ -416,14 +457,14 @@ int corr_blocks(const cfp_ctx* c) {
 }
 
 int apply_blocks(cfp_ctx* c) {
-    const dim3 g = apply_grid(c);
-    return (int)(g.x * g.y * g.z) + corr_blocks(c);
+    const dim3 g = apply_grid<float>(c), h = apply_grid<double>(c);
+    return (int)std::max(g.x * g.y * g.z, h.x * h.y * h.z) + corr_blocks(c);
 }
 
 template <class T>
 void launch_apply(cfp_ctx* c, const T* x, T* y, const T* d0, int dotmode, double* partial, cudaStream_t s,
                   int* nblocks_out) {
-    const dim3 grid = apply_grid(c);
+    const dim3 grid = apply_grid<T>(c);
     const dim3 block(kAX);
     const Grid<T> G = grid_view<T>(c);
     const Side<T> S = side_view<T>(c);
