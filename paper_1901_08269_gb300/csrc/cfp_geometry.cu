@@ -340,19 +340,34 @@ __global__ void k_ibi_roots(IrrArgs a, GeoArgs g, const int32_t* ibi_off, double
 constexpr int kMaxCorr = 192;
 constexpr int kMaxBib = 64;
 
+// Merged correction entries of one row, in first-insertion order.  An
+// open-addressing index (kSlots > kMaxCorr, so an empty slot always exists)
+// finds the entry of an offset in O(1) expected time instead of a scan.
 struct CorrAcc {
+    static constexpr int kSlots = 256;  // power of two
     int n;
     int off[kMaxCorr];
     double val[kMaxCorr];
+    int16_t slot[kSlots];  // entry index + 1, 0 = empty
+    __device__ void clear() {
+        n = 0;
+        for (int q = 0; q < kSlots; ++q) slot[q] = 0;
+    }
     __device__ bool add(int o, double v) {
-        for (int q = 0; q < n; ++q)
-            if (off[q] == o) {
-                val[q] += v;
+        unsigned h = ((unsigned)o * 2654435761u) >> 24;
+        for (int probe = 0; probe < kSlots; ++probe) {
+            const int e = slot[h];
+            if (e == 0) break;
+            if (off[e - 1] == o) {
+                val[e - 1] += v;
                 return true;
             }
+            h = (h + 1) & (kSlots - 1);
+        }
         if (n == kMaxCorr) return false;
         off[n] = o;
         val[n] = v;
+        slot[h] = (int16_t)(n + 1);
         ++n;
         return true;
     }
@@ -597,7 +612,7 @@ __global__ void __launch_bounds__(64) k_side(SideArgs S, int* ccount, int* bcoun
          s += (int64_t)gridDim.x * blockDim.x) {
         CorrAcc corr;
         BibAcc bib;
-        corr.n = 0;
+        corr.clear();
         bib.n = 0;
         RowCtx R;
         R.lin = S.a.irr_lin[s];
