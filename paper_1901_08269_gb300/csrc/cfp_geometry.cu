@@ -414,26 +414,34 @@ __device__ int ibi_index(const SideArgs& S, int64_t l, int dir) {
 
 // Moment matching of Eqs. mat1-mat4 (matrix M of Eq. M): c_n with
 // sum_n c_n (xi_n - xe)^m = sum_s L_s m(m-1) (xs_s - xe)^(m-2), m < M,
-// lengths scaled by hs, Gaussian elimination with partial pivoting.
+// lengths scaled by hs, Gaussian elimination with partial pivoting.  The
+// scaled distances are divided once per node and their powers built up
+// row by row (FP64 division is costly on this GPU).
 __device__ bool moment_solve(int M, const double* xi, double xe, int ns, const double* xs,
                              const double* Ls, double hs, double* c) {
     double A[6][7];
+    double e[6], pw[6], es[3], ps[3];
+    for (int q = 0; q < M; ++q) {
+        e[q] = (xi[q] - xe) / hs;
+        pw[q] = 1.0;
+    }
+    for (int s = 0; s < ns; ++s) {
+        es[s] = (xs[s] - xe) / hs;
+        ps[s] = 1.0;
+    }
+    const double ih2 = 1.0 / (hs * hs);
     for (int m = 0; m < M; ++m) {
         for (int q = 0; q < M; ++q) {
-            const double e = (xi[q] - xe) / hs;
-            double p = 1.0;
-            for (int r = 0; r < m; ++r) p *= e;
-            A[m][q] = p;
+            A[m][q] = pw[q];
+            pw[q] *= e[q];
         }
         double r = 0.0;
         if (m >= 2)
             for (int s = 0; s < ns; ++s) {
-                const double e = (xs[s] - xe) / hs;
-                double p = 1.0;
-                for (int q = 0; q < m - 2; ++q) p *= e;
-                r += Ls[s] * (double)(m * (m - 1)) * p;
+                r += Ls[s] * (double)(m * (m - 1)) * ps[s];
+                ps[s] *= es[s];
             }
-        A[m][M] = r / (hs * hs);
+        A[m][M] = r * ih2;
     }
     for (int col = 0; col < M; ++col) {
         int piv = col;
@@ -446,8 +454,9 @@ __device__ bool moment_solve(int M, const double* xi, double xe, int ns, const d
                 A[col][q] = A[piv][q];
                 A[piv][q] = t;
             }
+        const double ip = 1.0 / A[col][col];
         for (int r = col + 1; r < M; ++r) {
-            const double f = A[r][col] / A[col][col];
+            const double f = A[r][col] * ip;
             for (int q = col; q <= M; ++q) A[r][q] -= f * A[col][q];
         }
     }
