@@ -54,15 +54,6 @@ __device__ double body_phi(const cfp_body& b, double x, double y, double z) {
     return __dsub_rn(__dadd_rn(__dmul_rn(s, s), __dmul_rn(q2, q2)), __dmul_rn(b.p[1], b.p[1]));
 }
 
-__device__ double union_phi(const cfp_body* bodies, int nb, int inside, double x, double y, double z) {
-    double phi = INFINITY;
-    for (int m = 0; m < nb; ++m) {
-        const double v = body_phi(bodies[m], x, y, z);
-        if (v < phi) phi = v;
-    }
-    return inside ? -phi : phi;
-}
-
 __device__ __forceinline__ double edge_pos(double xa, double xb, double t) {
     return __dadd_rn(__dmul_rn(__dsub_rn(1.0, t), xa), __dmul_rn(t, xb));
 }
@@ -290,14 +281,17 @@ __global__ void k_ibi_count(IrrArgs a, int* cnt) {
 
 // Root of phi on the edge from fluid node A (t = 0) to solid node B (t = 1):
 // scan t = 1/8 .. 7/8 for the first sign change seen from A, then 60
-// bisection steps; the solid end of the last bracket is returned.
+// bisection steps; the solid end of the last bracket is returned.  Only the
+// sign of phi decides each step, so node_solid (which skips bodies whose
+// bounding sphere excludes the point, those have phi > 0) gives the same
+// decisions as the full union of the bodies.
 __device__ double ibi_root(const GeoArgs& g, int d, const double pa[3], double xb) {
     double q[3] = {pa[0], pa[1], pa[2]};
     double lo = 0.0, hi = 1.0;
     for (int s = 1; s < 8; ++s) {
         const double ts = (double)s / 8.0;
         q[d] = edge_pos(pa[d], xb, ts);
-        if (union_phi(g.bodies, g.nb, g.inside, q[0], q[1], q[2]) <= 0.0) {
+        if (node_solid(g, q[0], q[1], q[2])) {
             hi = ts;
             break;
         }
@@ -306,33 +300,43 @@ __device__ double ibi_root(const GeoArgs& g, int d, const double pa[3], double x
     for (int it = 0; it < 60; ++it) {
         const double mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
         q[d] = edge_pos(pa[d], xb, mid);
-        if (union_phi(g.bodies, g.nb, g.inside, q[0], q[1], q[2]) > 0.0) lo = mid;
+        if (!node_solid(g, q[0], q[1], q[2])) lo = mid;
         else hi = mid;
     }
     return hi;
 }
 
-__global__ void k_ibi_roots(IrrArgs a, GeoArgs g, const int32_t* ibi_off, double* xyz) {
-    const int nx = a.n[0], ny = a.n[1];
-    const int64_t st[3] = {1, nx, (int64_t)nx * ny};
+// IBI m of the list comes from irregular slot src[m] >> 3 and direction
+// src[m] & 7 (IBIs of a slot in direction order, from its offset ibi_off)
+__global__ void k_ibi_map(IrrArgs a, const int32_t* ibi_off, int32_t* src) {
+    const int64_t st[3] = {1, a.n[0], (int64_t)a.n[0] * a.n[1]};
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < a.n_irr;
          s += (int64_t)gridDim.x * blockDim.x) {
+        const int mask = solid_axis_mask(a.type, a.irr_lin[s], st);
+        int m = ibi_off[s];
+        for (int dir = 0; dir < 6; ++dir)
+            if (mask & (1 << dir)) src[m++] = (int32_t)(s * 8 + dir);
+    }
+}
+
+// one thread per IBI: its root and coordinates
+__global__ void k_ibi_roots(IrrArgs a, GeoArgs g, const int32_t* src, int64_t n_ibi, double* xyz) {
+    const int nx = a.n[0], ny = a.n[1];
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_ibi;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t code = src[m];
+        const int64_t s = code >> 3;
+        const int dir = code & 7;
         const int64_t l = a.irr_lin[s];
         const int idx[3] = {(int)(l % nx), (int)((l / nx) % ny), (int)(l / ((int64_t)nx * ny))};
-        const int mask = solid_axis_mask(a.type, l, st);
-        int m = ibi_off[s];
         const double pa[3] = {g.X[0][idx[0]], g.X[1][idx[1]], g.X[2][idx[2]]};
-        for (int dir = 0; dir < 6; ++dir) {
-            if (!(mask & (1 << dir))) continue;
-            const int d = dir >> 1, sg = (dir & 1) ? 1 : -1;
-            const double xb = g.X[d][idx[d] + sg];
-            const double t = ibi_root(g, d, pa, xb);
-            xyz[3 * (int64_t)m + 0] = pa[0];
-            xyz[3 * (int64_t)m + 1] = pa[1];
-            xyz[3 * (int64_t)m + 2] = pa[2];
-            xyz[3 * (int64_t)m + d] = edge_pos(pa[d], xb, t);
-            ++m;
-        }
+        const int d = dir >> 1, sg = (dir & 1) ? 1 : -1;
+        const double xb = g.X[d][idx[d] + sg];
+        const double t = ibi_root(g, d, pa, xb);
+        xyz[3 * m + 0] = pa[0];
+        xyz[3 * m + 1] = pa[1];
+        xyz[3 * m + 2] = pa[2];
+        xyz[3 * m + d] = edge_pos(pa[d], xb, t);
     }
 }
 
@@ -802,8 +806,16 @@ cfp_status classify(cfp_ctx* c) {
     c->n_ibi = h;
     CFP_CUDA(cudaMemcpyAsync(c->ibi_off + nirr, c->dtotal, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
     CFP_CUDA(cudaMalloc(&c->ibi_xyz, sizeof(double) * 3 * std::max<int64_t>(c->n_ibi, 1)));
-    if (nirr) k_ibi_roots<<<grid_for(nirr, 128), 128, 0, c->stream>>>(ia, g, c->ibi_off, c->ibi_xyz);
-    if (nirr) c->launches += 1;
+    if (c->n_ibi > 0) {
+        int32_t* isrc = nullptr;
+        CFP_CUDA(cudaMalloc(&isrc, sizeof(int32_t) * c->n_ibi));
+        k_ibi_map<<<grid_for(nirr, 256), 256, 0, c->stream>>>(ia, c->ibi_off, isrc);
+        k_ibi_roots<<<grid_for(c->n_ibi, 128), 128, 0, c->stream>>>(ia, g, isrc, c->n_ibi, c->ibi_xyz);
+        c->launches += 2;
+        CFP_CUDA(cudaGetLastError());
+        CFP_CUDA(cudaStreamSynchronize(c->stream));
+        cudaFree(isrc);
+    }
     CFP_CUDA(cudaGetLastError());
 
     // side list: count, scan, fill
