@@ -313,36 +313,68 @@ __global__ void k_mask_copy(const uint8_t* __restrict__ type, const T* __restric
     }
 }
 
-// Eq. q with the weights of solid points set to zero (Q-bar): one thread
-// per interior node, plain 27-term sum.
-__global__ void k_qf(Grid<double> G, const uint8_t* __restrict__ type, const double* __restrict__ f,
-                     double* __restrict__ out) {
+// Eq. q with the weights of solid points set to zero (Q-bar), i.e. the
+// tensor product Q = Lx Ly Lz applied to f with its solid entries replaced
+// by zero, sum-factorised like the apply: each thread owns the columns
+// (i, j0) and (i, j0 + 1) and marches kApplyKC planes in z; per plane it
+// loads rows j0-1 .. j0+2 of the masked f, forms the x-pass XL = Lx f of
+// each row and the y-pass Q = Ly XL of its two rows, and keeps Q of three
+// planes for the z-pass out = Lz Q.  Interior non-unknowns get 0.
+__global__ void __launch_bounds__(kAX) k_qf(Grid<double> G, const uint8_t* __restrict__ type,
+                                            const double* __restrict__ f, double* __restrict__ out) {
+    constexpr int TY = 2, R = TY + 2;
     const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const int i = 1 + blockIdx.x * kAX + threadIdx.x;
+    const int j0 = 1 + blockIdx.y * TY;
+    const int k0 = 1 + blockIdx.z * kApplyKC;
+    const int k1 = min(k0 + kApplyKC, nz - 1);
+    const bool iin = i <= nx - 2;
+    const int ic = iin ? i : 1;  // clamped: every load stays inside the grid
     const int64_t sy = nx, sz = (int64_t)nx * ny;
-    const int64_t nin = (int64_t)(nx - 2) * (ny - 2) * (nz - 2);
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nin;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int i = 1 + (int)(q % (nx - 2));
-        const int j = 1 + (int)((q / (nx - 2)) % (ny - 2));
-        const int k = 1 + (int)(q / ((int64_t)(nx - 2) * (ny - 2)));
-        const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
-        const uint8_t t = type[l];
-        if (t != CFP_REGULAR && t != CFP_IRREGULAR) {
-            out[l] = 0.0;
-            continue;
+    const double ax = G.ax[0].a[ic], cx = G.ax[0].c[ic];
+    double ay[TY], cy[TY];
+    bool jin[TY];
+#pragma unroll
+    for (int t = 0; t < TY; ++t) {
+        jin[t] = j0 + t <= ny - 2;
+        const int jc = jin[t] ? j0 + t : j0;
+        ay[t] = G.ax[1].a[jc];
+        cy[t] = G.ax[1].c[jc];
+    }
+    int64_t roff[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) roff[r] = (int64_t)min(j0 - 1 + r, ny - 1) * sy + ic;
+    double Qm[TY], Q0[TY], Qp[TY];
+#pragma unroll
+    for (int t = 0; t < TY; ++t) Qm[t] = Q0[t] = Qp[t] = 0.0;
+    for (int kk = k0 - 1; kk <= k1; ++kk) {
+        const int64_t pz = (int64_t)kk * sz;
+        double XL[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t q = pz + roff[r];
+            const double fm = type[q - 1] == CFP_SOLID ? 0.0 : f[q - 1];
+            const double f0 = type[q] == CFP_SOLID ? 0.0 : f[q];
+            const double fp = type[q + 1] == CFP_SOLID ? 0.0 : f[q + 1];
+            XL[r] = ax * fm + f0 + cx * fp;
         }
-        const double Lx[3] = {G.ax[0].a[i], 1.0, G.ax[0].c[i]};
-        const double Ly[3] = {G.ax[1].a[j], 1.0, G.ax[1].c[j]};
-        const double Lz[3] = {G.ax[2].a[k], 1.0, G.ax[2].c[k]};
-        double s = 0.0;
-        for (int r = 0; r < 3; ++r)
-            for (int p = 0; p < 3; ++p)
-                for (int o = 0; o < 3; ++o) {
-                    const int64_t c = l + (o - 1) + (p - 1) * sy + (r - 1) * sz;
-                    if (type[c] == CFP_SOLID) continue;
-                    s += Lx[o] * Ly[p] * Lz[r] * f[c];
-                }
-        out[l] = s;
+#pragma unroll
+        for (int t = 0; t < TY; ++t) {
+            Qm[t] = Q0[t];
+            Q0[t] = Qp[t];
+            Qp[t] = ay[t] * XL[t] + XL[t + 1] + cy[t] * XL[t + 2];
+        }
+        if (kk >= k0 + 1 && iin) {
+            const int k = kk - 1;
+            const double az = G.ax[2].a[k], cz = G.ax[2].c[k];
+#pragma unroll
+            for (int t = 0; t < TY; ++t) {
+                if (!jin[t]) continue;
+                const int64_t l = (int64_t)k * sz + (int64_t)(j0 + t) * sy + i;
+                const uint8_t tl = type[l];
+                out[l] = (tl == CFP_REGULAR || tl == CFP_IRREGULAR) ? az * Qm[t] + Q0[t] + cz * Qp[t] : 0.0;
+            }
+        }
     }
 }
 
@@ -528,7 +560,7 @@ template void launch_precond<float>(cfp_ctx*, int, const float*, float*, cudaStr
 
 void launch_qf(cfp_ctx* c, const double* f, double* out, cudaStream_t s) {
     c->launches += 1;
-    k_qf<<<flat_grid(c->N), 256, 0, s>>>(grid_view<double>(c), c->type, f, out);
+    k_qf<<<apply_grid<double>(c), kAX, 0, s>>>(grid_view<double>(c), c->type, f, out);
 }
 
 void launch_rhs_finish(cfp_ctx* c, const double* qf, const double* bg, const double* g_ibi, double* rhs,
