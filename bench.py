@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=8)
     ap.add_argument("--precond", default="mg", choices=["mg", "rbgs"])
     ap.add_argument("--mg-smooth", type=int, default=3)
+    ap.add_argument("--mg-post", type=int, default=0, help="post-smoothing sweeps (0: as --mg-smooth)")
     ap.add_argument("--no-graph", action="store_true",
                     help="plain launches instead of the CUDA graph (ncu cannot profile kernel nodes of graphs "
                          "with conditional nodes)")
@@ -218,7 +219,7 @@ def batch_arm(args):
         probs.append((w, ctx, f, g, gi, u))
     torch.cuda.synchronize()
     prec = cfp.PREC_MIXED if args.precision == "mixed" else cfp.PREC_FP64
-    opts = cfp.default_opts(precision=prec, precond=cfp.PRECOND_MG, mg_smooth=args.mg_smooth,
+    opts = cfp.default_opts(precision=prec, precond=cfp.PRECOND_MG, mg_smooth=args.mg_smooth, mg_post=args.mg_post,
                             inner_tol=args.inner_tol)
     # autotune once per grid size (first problem of each size), then share
     tuned = {}
@@ -304,7 +305,7 @@ def main():
     prec = cfp.PREC_MIXED if args.precision == "mixed" else cfp.PREC_FP64
     pc = cfp.PRECOND_MG if args.precond == "mg" else cfp.PRECOND_RBGS
     opts = cfp.default_opts(precision=prec, sweeps=args.sweeps, inner_tol=args.inner_tol, precond=pc,
-                            mg_smooth=args.mg_smooth, use_graph=0 if args.no_graph else 1)
+                            mg_smooth=args.mg_smooth, mg_post=args.mg_post, use_graph=0 if args.no_graph else 1)
 
     def step():
         ctx.classify_points()
@@ -365,7 +366,7 @@ def main():
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         i64 = ctx.solve(f, g, gi, u64, tol=args.tol, precision=cfp.PREC_FP64, sweeps=args.sweeps, precond=pc,
-                        mg_smooth=args.mg_smooth)
+                        mg_smooth=args.mg_smooth, mg_post=args.mg_post)
         b.record(stream)
         torch.cuda.synchronize()
         e64 = float((u64 - ue).abs()[fluid].max())
@@ -437,7 +438,7 @@ def main():
                 "config": {"workload": "config3-%d^3-ellipsoid+torus" % args.n, "n": args.n,
                            "grid": "tanh (2.0, 1.2, 1.2) on [-1,1]^3", "precision": args.precision,
                            "tol": args.tol, "inner_tol": args.inner_tol, "sweeps": args.sweeps,
-                           "precond": args.precond, "mg_smooth": args.mg_smooth,
+                           "precond": args.precond, "mg_smooth": args.mg_smooth, "mg_post": args.mg_post or args.mg_smooth,
                            "l2": "no flush: every field (1.08 GB at 513^3) exceeds the 129 MB L2",
                            "parallelism": "replicas" if world > 1 else "single",
                            "graph": not args.no_graph},

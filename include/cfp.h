@@ -64,7 +64,8 @@ enum { CFP_PRECOND_RBGS = 0, /* `sweeps` red-black Gauss-Seidel sweeps on K from
                                 zero (the paper's fixed count of inner
                                 iterations, Sec. 3.3)                         */
        CFP_PRECOND_MG = 1,   /* one multigrid V-cycle on K from zero: red-black
-                                smoothing (mg_smooth sweeps before and after),
+                                smoothing (mg_smooth sweeps before, mg_post
+                                after the coarse correction),
                                 rediscretised coarse levels; quality
                                 independent of the grid size                  */
        CFP_PRECOND_ILU = 2   /* `sweeps` Richardson sweeps from zero with ILU(0)
@@ -90,8 +91,11 @@ typedef struct {
                           with a device-side while loop; 0: plain launches   */
     int precond;       /* CFP_PRECOND_RBGS (default), CFP_PRECOND_MG or
                           CFP_PRECOND_ILU                                    */
-    int mg_smooth;     /* CFP_PRECOND_MG: sweeps before and after the coarse
-                          correction on each level (default 2)               */
+    int mg_smooth;     /* CFP_PRECOND_MG: sweeps before the coarse correction
+                          on each level, and after it unless mg_post is set
+                          (default 2)                                       */
+    int mg_post;       /* CFP_PRECOND_MG: sweeps after the coarse correction;
+                          0 (default): mg_smooth                            */
 } cfp_opts;
 
 typedef struct {

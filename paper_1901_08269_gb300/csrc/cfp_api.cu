@@ -70,6 +70,7 @@ void cfp_default_opts(cfp_opts* o) {
     o->use_graph = 1;
     o->precond = CFP_PRECOND_RBGS;
     o->mg_smooth = 2;
+    o->mg_post = 0;
 }
 
 const char* cfp_last_error(void) { return g_last_error.c_str(); }
@@ -263,6 +264,7 @@ cfp_status cfp_precondition_ex(cfp_ctx* c, const cfp_opts* o, const double* rho,
     if (phi == c->v64 + (int64_t)V_TMP2 * c->N) return fail(CFP_EINVAL, "phi aliases the context's work space");
     c->precond_kind = opts.precond;
     c->mg_smooth = std::max(1, opts.mg_smooth);
+    c->mg_post = opts.mg_post > 0 ? opts.mg_post : c->mg_smooth;
     if (c->precond_kind == CFP_PRECOND_MG) CFP_TRY(ensure_mg(c, 0));
     if (c->precond_kind == CFP_PRECOND_ILU) CFP_TRY(ensure_ilu(c, 0));
     CFP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * c->N, c->stream));

@@ -205,6 +205,7 @@ struct cfp_ctx {
     // preconditioner of the current solve and its multigrid hierarchy
     int precond_kind = CFP_PRECOND_RBGS;
     int mg_smooth = 2;
+    int mg_post = 2;
     std::vector<cfp::MgLevel> mg;
     // ILU(0) of K (CFP_PRECOND_ILU): [pivots | work field], FP64 and FP32
     double* ilu64 = nullptr;

@@ -275,7 +275,7 @@ int64_t body_launches(cfp_ctx* c) { return c->body_launches; }
 template <class T>
 cfp_status build_graph(cfp_ctx* c, int prec, int sweeps) {
     if (c->gexec[prec] && c->gsweeps[prec] == sweeps && c->gprecond[prec] == c->precond_kind &&
-        c->gmgs[prec] == c->mg_smooth)
+        c->gmgs[prec] == c->mg_smooth * 1000 + c->mg_post)
         return CFP_OK;
     if (c->gexec[prec]) {
         cudaGraphExecDestroy(c->gexec[prec]);
@@ -316,7 +316,7 @@ cfp_status build_graph(cfp_ctx* c, int prec, int sweeps) {
     c->gexec[prec] = exec;
     c->gsweeps[prec] = sweeps;
     c->gprecond[prec] = c->precond_kind;
-    c->gmgs[prec] = c->mg_smooth;
+    c->gmgs[prec] = c->mg_smooth * 1000 + c->mg_post;
     return CFP_OK;
 }
 
@@ -484,6 +484,7 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
         return fail(CFP_EINVAL, "unknown preconditioner");
     c->precond_kind = opts.precond;
     c->mg_smooth = std::max(1, opts.mg_smooth);
+    c->mg_post = opts.mg_post > 0 ? opts.mg_post : c->mg_smooth;
     const bool mixed = opts.precision == CFP_PREC_MIXED;
     if (c->precond_kind == CFP_PRECOND_MG) CFP_TRY(ensure_mg(c, mixed ? 1 : 0));
     if (c->precond_kind == CFP_PRECOND_ILU) CFP_TRY(ensure_ilu(c, mixed ? 1 : 0));

@@ -14,7 +14,8 @@
 // Shortley-Weller distance).  Prolongation is trilinear in the coordinates;
 // restriction is its transpose normalised by the weight sums (full
 // weighting).  Smoother: red-black Gauss-Seidel, mg_smooth sweeps (red then
-// black) before and after the coarse correction, 16 on the coarsest level.
+// black) before the coarse correction and mg_post after it, 16 on the
+// coarsest level.
 //
 // Storage: every level keeps its vectors in a red-black split layout (each
 // colour in its own array, rows of (n_x + 1) / 2 entries padded to 8), so a
@@ -706,7 +707,8 @@ cfp_status ensure_mg(cfp_ctx* c, int prec) {
 template <class T>
 void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
     const int nl = (int)c->mg.size();
-    const int nu = std::max(1, c->mg_smooth);
+    const int nu = std::max(1, c->mg_smooth);    // sweeps before the coarse correction
+    const int npost = std::max(1, c->mg_post);   // and after it
     const Side<T> S0 = side_view<T>(c);
     const Side<T> Sc = Side<T>{nullptr, nullptr, nullptr, nullptr, nullptr};
     if (nl == 1) {
@@ -736,7 +738,7 @@ void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
         const SLev<T> F = slev<T>(c, l), C = slev<T>(c, l + 1);
         k_prolong_split<T><<<plane_grid(c->mg[l].n), kSplitThreads, 0, s>>>(transfer<T>(c->mg[l]), F, C);
         c->launches += 1;
-        smooth<T>(c, l, l == 0 ? S0 : Sc, nu, 0, l == 0 ? 3 : 0, rho, phi, s);
+        smooth<T>(c, l, l == 0 ? S0 : Sc, npost, 0, l == 0 ? 3 : 0, rho, phi, s);
     }
 }
 

@@ -16,7 +16,8 @@ here, step by step on whole arrays in natural node order:
   transfers   P: piecewise-linear interpolation in the coordinates per axis,
               tensor product; restriction (P^T r) / (P^T 1)
   cycle       nu sweeps from zero, residual, restriction; 16 sweeps from zero
-              on the coarsest level; prolongation added, nu sweeps
+              on the coarsest level; prolongation added, post sweeps
+              (mg_smooth = nu, mg_post = post)
 
 The CUDA path stores colours in separate arrays and skips the black
 residuals and the red prolongation (both exact for red-black smoothing), so
@@ -103,7 +104,8 @@ def sweep(L, b, e):
         e[m] = (b[m] - off[m]) / L["diag"][m]
 
 
-def vcycle(levels, rho, nu, l=0):
+def vcycle(levels, rho, nu, l=0, post=None):
+    post = nu if post is None else post
     L = levels[l]
     e = np.zeros(len(rho))
     if l == len(levels) - 1:
@@ -116,8 +118,8 @@ def vcycle(levels, rho, nu, l=0):
     P = L["P"]
     C = levels[l + 1]
     bc = np.where(C["unk"], (P.T @ r) / (P.T @ np.ones(len(r))), 0.0)
-    e += np.where(L["unk"], P @ vcycle(levels, bc, nu, l + 1), 0.0)
-    for _ in range(nu):
+    e += np.where(L["unk"], P @ vcycle(levels, bc, nu, l + 1, post), 0.0)
+    for _ in range(post):
         sweep(L, rho, e)
     return e
 
@@ -138,9 +140,9 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("nu", [1, 2, 3])
+@pytest.mark.parametrize("nu,post", [(1, 1), (2, 2), (3, 3), (2, 1), (1, 3)])
 @pytest.mark.parametrize("name", list(CASES))
-def test_vcycle_matches_definition(name, nu):
+def test_vcycle_matches_definition(name, nu, post):
     w = CASES[name]()
     P = O.Problem(w.x, w.y, w.z, w.bodies, w.fluid_inside)
     otype = P.classify()
@@ -153,11 +155,12 @@ def test_vcycle_matches_definition(name, nu):
         assert len(levels) >= 3
     rng = np.random.default_rng(11 + nu)
     rho = np.where(levels[0]["unk"], rng.standard_normal(w.N), 0.0)
-    want = vcycle(levels, rho, nu)
+    want = vcycle(levels, rho, nu, post=post)
     ctx = cfp.Context(w.x, w.y, w.z, w.bodies, w.fluid_inside)
     ctx.classify_points()
     phi = torch.full((w.N,), 7.0, dtype=torch.float64, device="cuda")  # overwritten: zeroed, then the V-cycle
-    ctx.precondition_ex(torch.as_tensor(rho, device="cuda"), phi, precond=cfp.PRECOND_MG, mg_smooth=nu)
+    opts = dict(precond=cfp.PRECOND_MG, mg_smooth=nu, mg_post=post)
+    ctx.precondition_ex(torch.as_tensor(rho, device="cuda"), phi, **opts)
     got = phi.cpu().numpy()
     u = levels[0]["unk"]
     assert np.all(got[~u] == 0.0)
@@ -165,7 +168,7 @@ def test_vcycle_matches_definition(name, nu):
     assert err <= 1e-12, err
     # a second call reuses the level vectors: nothing stale may leak in
     phi2 = torch.zeros(w.N, dtype=torch.float64, device="cuda")
-    ctx.precondition_ex(torch.as_tensor(rho, device="cuda"), phi2, precond=cfp.PRECOND_MG, mg_smooth=nu)
+    ctx.precondition_ex(torch.as_tensor(rho, device="cuda"), phi2, **opts)
     assert torch.equal(phi, phi2)
     ctx.close()
 
