@@ -216,7 +216,7 @@ cfp_status cfp_assemble_rhs(cfp_ctx* c, const double* f, const double* g, const 
     double* qf = c->v64 + V_T * N;
     if (rhs == gb || rhs == bg || rhs == qf) return fail(CFP_EINVAL, "rhs aliases the context's work space");
     launch_boundary_lift(c, g, gb, c->stream);
-    launch_apply<double>(c, gb, bg, nullptr, 0, nullptr, c->stream, nullptr);
+    launch_apply_lift(c, gb, bg, c->stream);
     launch_qf(c, f, qf, c->stream);
     launch_rhs_finish(c, qf, bg, c->n_ibi ? gi : c->ibi_xyz, rhs, c->stream);
     CFP_CUDA(cudaGetLastError());

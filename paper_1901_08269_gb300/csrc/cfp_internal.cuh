@@ -241,6 +241,7 @@ template <>
 Side<double> side_view<double>(cfp_ctx* c);
 template <>
 Side<float> side_view<float>(cfp_ctx* c);
+void launch_apply_lift(cfp_ctx* c, const double* gb, double* y, cudaStream_t s);
 template <class T>
 void launch_apply(cfp_ctx* c, const T* x, T* y, const T* d0, int dotmode, double* partial,
                   cudaStream_t s, int* nblocks_out);

@@ -228,6 +228,65 @@ __global__ void __launch_bounds__(kAX, sizeof(T) == 4 ? 8 : 1)
         }
     }
 }
+// B gb for a field gb that is zero away from the box (the boundary lift of
+// the right-hand side): its regular rows can be nonzero only on the shell of
+// interior nodes next to the box, so only those rows are evaluated, with the
+// 27 weights of Eq. A27 (Rx Ly Lz + Lx Ry Lz + Lx Ly Rz); every other
+// interior row is zero (the caller clears y).  Solid rows are zero; the
+// irregular rows get their corrections from k_apply_corr.  Thread q walks
+// the shell as two z-planes, then two y-rows of each inner plane, then the
+// two x-ends of each inner row.
+__global__ void k_lift_shell(Grid<double> G, const uint8_t* __restrict__ type, const double* __restrict__ gb,
+                             double* __restrict__ y) {
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const int64_t ax = nx - 2, ay = ny - 2, az = nz - 2;
+    const int64_t bz = az - 2 > 0 ? az - 2 : 0, by = ay - 2 > 0 ? ay - 2 : 0;
+    const int64_t nA = 2 * ax * ay, nB = 2 * bz * ax, nC = 2 * bz * by;
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nA + nB + nC;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        if (q < nA) {
+            const int64_t r = q % (ax * ay);
+            k = q < ax * ay ? 1 : nz - 2;
+            i = 1 + (int)(r % ax);
+            j = 1 + (int)(r / ax);
+        } else if (q < nA + nB) {
+            const int64_t r = (q - nA) % (bz * ax);
+            j = q - nA < bz * ax ? 1 : ny - 2;
+            i = 1 + (int)(r % ax);
+            k = 2 + (int)(r / ax);
+        } else {
+            const int64_t r = (q - nA - nB) % (bz * by);
+            i = q - nA - nB < bz * by ? 1 : nx - 2;
+            j = 2 + (int)(r % by);
+            k = 2 + (int)(r / by);
+        }
+        const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
+        if (type[l] == CFP_SOLID) {
+            y[l] = 0.0;
+            continue;
+        }
+        const double Lx[3] = {G.ax[0].a[i], 1.0, G.ax[0].c[i]}, Rx[3] = {G.ax[0].ar[i], G.ax[0].br[i], G.ax[0].cr[i]};
+        const double Ly[3] = {G.ax[1].a[j], 1.0, G.ax[1].c[j]}, Ry[3] = {G.ax[1].ar[j], G.ax[1].br[j], G.ax[1].cr[j]};
+        const double Lz[3] = {G.ax[2].a[k], 1.0, G.ax[2].c[k]}, Rz[3] = {G.ax[2].ar[k], G.ax[2].br[k], G.ax[2].cr[k]};
+        double v = 0.0;
+        for (int r = 0; r < 3; ++r)
+            for (int p = 0; p < 3; ++p)
+                for (int o = 0; o < 3; ++o) {
+                    const double w = Rx[o] * Ly[p] * Lz[r] + Lx[o] * Ry[p] * Lz[r] + Lx[o] * Ly[p] * Rz[r];
+                    v += w * gb[l + (o - 1) + (p - 1) * sy + (r - 1) * sz];
+                }
+        y[l] = v;
+    }
+}
+
+// Side-list corrections of the irregular rows (the modified stencils of
+// Secs. 2.2-2.3, the C part of Eq. Bdec), one warp per irregular point: the
+// lanes gather the merged entries in parallel, lane 0 adds the sum to y and
+// updates the dot partials: (d0, y) gains d0 c, (y, y) gains 2 v c + c^2
+// where v is the row's regular part.  Partials are written after those of
+// k_apply, one pair per CTA.
 template <class T, int DOT>
 __global__ void __launch_bounds__(256)
     k_apply_corr(Side<T> S, const int32_t* __restrict__ irr_lin, int64_t n_irr, const T* __restrict__ x,
@@ -552,6 +611,18 @@ void launch_rbgs_half(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
 
 template void launch_rbgs_half<double>(cfp_ctx*, const double*, double*, cudaStream_t);
 template void launch_rbgs_half<float>(cfp_ctx*, const float*, float*, cudaStream_t);
+// y = B gb for the boundary lift gb (zero away from the box), FP64
+void launch_apply_lift(cfp_ctx* c, const double* gb, double* y, cudaStream_t s) {
+    cudaMemsetAsync(y, 0, sizeof(double) * c->N, s);
+    k_lift_shell<<<flat_grid(c->N), 256, 0, s>>>(grid_view<double>(c), c->type, gb, y);
+    c->launches += 1;
+    if (corr_blocks(c)) {
+        k_apply_corr<double, 0><<<corr_blocks(c), 256, 0, s>>>(side_view<double>(c), c->irr_lin, c->n_irr, gb, y,
+                                                               nullptr, nullptr);
+        c->launches += 1;
+    }
+}
+
 template void launch_apply<double>(cfp_ctx*, const double*, double*, const double*, int, double*, cudaStream_t,
                                    int*);
 template void launch_apply<float>(cfp_ctx*, const float*, float*, const float*, int, double*, cudaStream_t, int*);
