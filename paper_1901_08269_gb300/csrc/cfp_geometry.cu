@@ -420,56 +420,88 @@ __device__ int ibi_index(const SideArgs& S, int64_t l, int dir) {
 // sum_n c_n (xi_n - xe)^m = sum_s L_s m(m-1) (xs_s - xe)^(m-2), m < M,
 // lengths scaled by hs, Gaussian elimination with partial pivoting.  The
 // scaled distances are divided once per node and their powers built up
-// row by row (FP64 division is costly on this GPU).
-__device__ bool moment_solve(int M, const double* xi, double xe, int ns, const double* xs,
-                             const double* Ls, double hs, double* c) {
-    double A[6][7];
-    double e[6], pw[6], es[3], ps[3];
+// row by row (FP64 division is costly on this GPU).  M is a template
+// parameter and every loop is unrolled, so the matrix lives in registers
+// (a runtime size or pivot index would put it in local memory); the pivot
+// row is exchanged with predicated selects.
+template <int M>
+__device__ __forceinline__ bool moment_solve_m(const double* xi, double xe, int ns, const double* xs,
+                                               const double* Ls, double hs, double* c) {
+    double A[M][M + 1];
+    double e[M], pw[M];
+#pragma unroll
     for (int q = 0; q < M; ++q) {
         e[q] = (xi[q] - xe) / hs;
         pw[q] = 1.0;
     }
-    for (int s = 0; s < ns; ++s) {
-        es[s] = (xs[s] - xe) / hs;
-        ps[s] = 1.0;
-    }
+    double es[3] = {0.0, 0.0, 0.0}, ps[3] = {1.0, 1.0, 1.0};
+    for (int s = 0; s < ns; ++s) es[s] = (xs[s] - xe) / hs;
     const double ih2 = 1.0 / (hs * hs);
+#pragma unroll
     for (int m = 0; m < M; ++m) {
+#pragma unroll
         for (int q = 0; q < M; ++q) {
             A[m][q] = pw[q];
             pw[q] *= e[q];
         }
         double r = 0.0;
-        if (m >= 2)
-            for (int s = 0; s < ns; ++s) {
-                r += Ls[s] * (double)(m * (m - 1)) * ps[s];
-                ps[s] *= es[s];
-            }
+        if (m >= 2) {
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+                if (s < ns) {
+                    r += Ls[s] * (double)(m * (m - 1)) * ps[s];
+                    ps[s] *= es[s];
+                }
+        }
         A[m][M] = r * ih2;
     }
+#pragma unroll
     for (int col = 0; col < M; ++col) {
         int piv = col;
+        double best = fabs(A[col][col]);
+#pragma unroll
         for (int r = col + 1; r < M; ++r)
-            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
-        if (A[piv][col] == 0.0) return false;
-        if (piv != col)
-            for (int q = 0; q <= M; ++q) {
-                const double t = A[col][q];
-                A[col][q] = A[piv][q];
-                A[piv][q] = t;
+            if (fabs(A[r][col]) > best) {
+                best = fabs(A[r][col]);
+                piv = r;
             }
+        if (best == 0.0) return false;
+#pragma unroll
+        for (int r = col + 1; r < M; ++r)
+            if (r == piv)
+#pragma unroll
+                for (int q = 0; q <= M; ++q) {
+                    const double t = A[col][q];
+                    A[col][q] = A[r][q];
+                    A[r][q] = t;
+                }
         const double ip = 1.0 / A[col][col];
+#pragma unroll
         for (int r = col + 1; r < M; ++r) {
             const double f = A[r][col] * ip;
+#pragma unroll
             for (int q = col; q <= M; ++q) A[r][q] -= f * A[col][q];
         }
     }
+#pragma unroll
     for (int r = M - 1; r >= 0; --r) {
         double s = A[r][M];
+#pragma unroll
         for (int q = r + 1; q < M; ++q) s -= A[r][q] * c[q];
         c[r] = s / A[r][r];
     }
     return true;
+}
+
+__device__ bool moment_solve(int M, const double* xi, double xe, int ns, const double* xs, const double* Ls,
+                             double hs, double* c) {
+    switch (M) {
+        case 3: return moment_solve_m<3>(xi, xe, ns, xs, Ls, hs, c);
+        case 4: return moment_solve_m<4>(xi, xe, ns, xs, Ls, hs, c);
+        case 5: return moment_solve_m<5>(xi, xe, ns, xs, Ls, hs, c);
+        case 6: return moment_solve_m<6>(xi, xe, ns, xs, Ls, hs, c);
+        default: return false;
+    }
 }
 
 struct RowCtx {
