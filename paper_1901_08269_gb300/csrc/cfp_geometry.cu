@@ -341,46 +341,29 @@ __global__ void k_ibi_roots(IrrArgs a, GeoArgs g, const int32_t* src, int64_t n_
 }
 
 // ------------------------------------------------------------- side list
-constexpr int kMaxCorr = 192;
+constexpr int kMaxRaw = 320;   // correction adds per row before merging (27 lines x <= 11)
 constexpr int kMaxBib = 64;
 
-// Merged correction entries of one row, in first-insertion order.  An
-// open-addressing index (kSlots > kMaxCorr, so an empty slot always exists)
-// finds the entry of an offset in O(1) expected time instead of a scan.
-struct CorrAcc {
-    static constexpr int kSlots = 256;  // power of two
+// Correction adds of one row, appended in order to the row's slice of the
+// global scratch (no merging here: k_side_merge merges them afterwards).
+struct RawAcc {
     int n;
-    int off[kMaxCorr];
-    double val[kMaxCorr];
-    int16_t slot[kSlots];  // entry index + 1, 0 = empty
-    __device__ void clear() {
-        n = 0;
-        for (int q = 0; q < kSlots; ++q) slot[q] = 0;
-    }
+    int32_t* off;
+    double* val;
     __device__ bool add(int o, double v) {
-        unsigned h = ((unsigned)o * 2654435761u) >> 24;
-        for (int probe = 0; probe < kSlots; ++probe) {
-            const int e = slot[h];
-            if (e == 0) break;
-            if (off[e - 1] == o) {
-                val[e - 1] += v;
-                return true;
-            }
-            h = (h + 1) & (kSlots - 1);
-        }
-        if (n == kMaxCorr) return false;
+        if (n == kMaxRaw) return false;
         off[n] = o;
         val[n] = v;
-        slot[h] = (int16_t)(n + 1);
         ++n;
         return true;
     }
 };
 
+// IBI weights of one row, appended to its scratch slice.
 struct BibAcc {
     int n;
-    int idx[kMaxBib];
-    double val[kMaxBib];
+    int32_t* idx;
+    double* val;
     __device__ bool add(int i, double v) {
         if (n == kMaxBib) return false;
         idx[n] = i;
@@ -508,7 +491,7 @@ struct RowCtx {
     int idx[3];
     int64_t lin;
     int64_t st[3];
-    CorrAcc* corr;
+    RawAcc* corr;
     BibAcc* bib;
     int ndeg;
     int err;
@@ -645,20 +628,19 @@ __device__ void record_error(DevError* e, int code, int lin, int detail) {
     }
 }
 
-// Builds the row of every irregular point once: its merged correction
-// entries and IBI weights go to a fixed-capacity scratch (kMaxCorr / kMaxBib
-// per slot) with their counts, its K row to krow.  A later kernel compacts
-// the scratch into CSR order.
+// Builds the row of every irregular point once: its correction adds (in the
+// order of the lines) and IBI weights go to fixed-capacity slices of the
+// scratch (kMaxRaw / kMaxBib per slot) with their counts, its K row to krow.
+// k_side_merge then merges equal offsets and a last kernel compacts the
+// scratch into CSR order.
 __global__ void __launch_bounds__(64) k_side(SideArgs S, int* ccount, int* bcount, int32_t* toff, double* tval,
                                              int32_t* tbidx, double* tbval, double* krow,
                                              unsigned long long* ndeg, DevError* err) {
     const int nx = S.a.n[0], ny = S.a.n[1];
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S.a.n_irr;
          s += (int64_t)gridDim.x * blockDim.x) {
-        CorrAcc corr;
-        BibAcc bib;
-        corr.clear();
-        bib.n = 0;
+        RawAcc corr{0, toff + s * kMaxRaw, tval + s * kMaxRaw};
+        BibAcc bib{0, tbidx + s * kMaxBib, tbval + s * kMaxBib};
         RowCtx R;
         R.lin = S.a.irr_lin[s];
         R.idx[0] = (int)(R.lin % nx);
@@ -681,14 +663,6 @@ __global__ void __launch_bounds__(64) k_side(SideArgs S, int* ccount, int* bcoun
         ccount[s] = corr.n;
         bcount[s] = bib.n;
         if (R.ndeg) atomicAdd(ndeg, (unsigned long long)R.ndeg);
-        for (int q = 0; q < corr.n; ++q) {
-            toff[s * kMaxCorr + q] = corr.off[q];
-            tval[s * kMaxCorr + q] = corr.val[q];
-        }
-        for (int q = 0; q < bib.n; ++q) {
-            tbidx[s * kMaxBib + q] = bib.idx[q];
-            tbval[s * kMaxBib + q] = bib.val[q];
-        }
         // Shortley-Weller row of K (Eqs. 2ndorder_coef_mod, A7_mod): the IBI
         // distance replaces the spacing on a solid side, whose term is dropped.
         double kr[7];
@@ -713,6 +687,67 @@ __global__ void __launch_bounds__(64) k_side(SideArgs S, int* ccount, int* bcoun
     }
 }
 
+// Merges each row's correction adds in place, in their order: an offset
+// seen before adds its value to that entry, a new offset opens the next
+// entry (the order of first appearance).  One warp per row; lane 0 walks the
+// adds through an open-addressing index in shared memory (kMergeSlots >
+// kMaxRaw, so an empty slot always exists), then the warp writes the merged
+// entries back to the front of the row's slice.
+constexpr int kMergeWarps = 4;
+constexpr int kMergeSlots = 512;
+
+__global__ void __launch_bounds__(32 * kMergeWarps) k_side_merge(int64_t n_irr, int* ccount, int32_t* toff,
+                                                                 double* tval) {
+    __shared__ int32_t soff[kMergeWarps][kMaxRaw];
+    __shared__ double sval[kMergeWarps][kMaxRaw];
+    __shared__ int16_t sslot[kMergeWarps][kMergeSlots];
+    __shared__ int smerged[kMergeWarps];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = warp; s < n_irr; s += nwarps) {
+        const int nraw = ccount[s];
+        int32_t* off = toff + s * kMaxRaw;
+        double* val = tval + s * kMaxRaw;
+        for (int q = lane; q < kMergeSlots; q += 32) sslot[wl][q] = 0;
+        __syncwarp();
+        if (lane == 0) {
+            int n = 0;
+            for (int e = 0; e < nraw; ++e) {
+                const int o = off[e];
+                const double v = val[e];
+                unsigned h = ((unsigned)o * 2654435761u) >> 23;  // 9 bits
+                bool merged = false;
+                for (int probe = 0; probe < kMergeSlots; ++probe) {
+                    const int x = sslot[wl][h];
+                    if (x == 0) break;
+                    if (soff[wl][x - 1] == o) {
+                        sval[wl][x - 1] += v;
+                        merged = true;
+                        break;
+                    }
+                    h = (h + 1) & (kMergeSlots - 1);
+                }
+                if (!merged) {
+                    soff[wl][n] = o;
+                    sval[wl][n] = v;
+                    sslot[wl][h] = (int16_t)(n + 1);
+                    ++n;
+                }
+            }
+            smerged[wl] = n;
+        }
+        __syncwarp();
+        const int n = smerged[wl];
+        for (int q = lane; q < n; q += 32) {
+            off[q] = soff[wl][q];
+            val[q] = sval[wl][q];
+        }
+        if (lane == 0) ccount[s] = n;
+        __syncwarp();
+    }
+}
+
 // scratch -> CSR (one warp per irregular point), with the FP32 copies
 __global__ void k_side_compact(int64_t n_irr, const int* ccount, const int* bcount, const int32_t* toff,
                                const double* tval, const int32_t* tbidx, const double* tbval,
@@ -724,8 +759,8 @@ __global__ void k_side_compact(int64_t n_irr, const int* ccount, const int* bcou
     for (int64_t s = warp; s < n_irr; s += nwarps) {
         const int c0 = corr_ptr[s], nc = ccount[s];
         for (int q = lane; q < nc; q += 32) {
-            const double v = tval[s * kMaxCorr + q];
-            corr_off[c0 + q] = toff[s * kMaxCorr + q];
+            const double v = tval[s * kMaxRaw + q];
+            corr_off[c0 + q] = toff[s * kMaxRaw + q];
             corr_val[c0 + q] = v;
             corr_val32[c0 + q] = (float)v;
         }
@@ -863,14 +898,21 @@ cfp_status classify(cfp_ctx* c) {
     CFP_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(DevError), c->stream));
     CFP_CUDA(cudaMemsetAsync(c->dtotal + 4, 0, sizeof(long long), c->stream));
     unsigned long long* ndeg = reinterpret_cast<unsigned long long*>(c->dtotal + 4);
-    int32_t* toff = nullptr;
-    double* tval = nullptr;
-    int32_t* tbidx = nullptr;
-    double* tbval = nullptr;
-    CFP_CUDA(cudaMalloc(&toff, sizeof(int32_t) * kMaxCorr * std::max<int64_t>(nirr, 1)));
-    CFP_CUDA(cudaMalloc(&tval, sizeof(double) * kMaxCorr * std::max<int64_t>(nirr, 1)));
-    CFP_CUDA(cudaMalloc(&tbidx, sizeof(int32_t) * kMaxBib * std::max<int64_t>(nirr, 1)));
-    CFP_CUDA(cudaMalloc(&tbval, sizeof(double) * kMaxBib * std::max<int64_t>(nirr, 1)));
+    // per-slot scratch slices, kept by the context across classifications
+    const int64_t nsl = std::max<int64_t>(nirr, 1);
+    const size_t need = (size_t)nsl * (kMaxRaw * (sizeof(int32_t) + sizeof(double)) +
+                                       kMaxBib * (sizeof(int32_t) + sizeof(double)));
+    if (c->side_scratch_bytes < need) {
+        if (c->side_scratch) cudaFree(c->side_scratch);
+        c->side_scratch = nullptr;
+        c->side_scratch_bytes = 0;
+        CFP_CUDA(cudaMalloc(&c->side_scratch, need));
+        c->side_scratch_bytes = need;
+    }
+    double* tval = static_cast<double*>(c->side_scratch);
+    double* tbval = tval + (size_t)nsl * kMaxRaw;
+    int32_t* toff = reinterpret_cast<int32_t*>(tbval + (size_t)nsl * kMaxBib);
+    int32_t* tbidx = toff + (size_t)nsl * kMaxRaw;
     CFP_CUDA(cudaMalloc(&c->krow, sizeof(double) * 7 * std::max<int64_t>(nirr, 1)));
     CFP_CUDA(cudaMalloc(&c->krow32, sizeof(float) * 7 * std::max<int64_t>(nirr, 1)));
     if (nirr)
@@ -878,6 +920,11 @@ cfp_status classify(cfp_ctx* c) {
                                                         c->derr);
     if (nirr) c->launches += 1;
     CFP_CUDA(cudaGetLastError());
+    if (nirr) {
+        k_side_merge<<<grid_for(32 * nirr, 32 * kMergeWarps), 32 * kMergeWarps, 0, c->stream>>>(nirr, cnt, toff, tval);
+        c->launches += 1;
+        CFP_CUDA(cudaGetLastError());
+    }
     DevError he;
     long long hdeg = 0;
     CFP_CUDA(cudaMemcpyAsync(&he, c->derr, sizeof(DevError), cudaMemcpyDeviceToHost, c->stream));
@@ -887,10 +934,6 @@ cfp_status classify(cfp_ctx* c) {
     if (he.code) {
         cudaFree(cnt);
         cudaFree(cnt2);
-        cudaFree(toff);
-        cudaFree(tval);
-        cudaFree(tbidx);
-        cudaFree(tbval);
         const int i = he.lin % nx, j = (he.lin / nx) % ny, k = he.lin / (nx * ny);
         const char* why = he.detail == DETAIL_BOXIBI ? "a modified stencil needs an IBI at a box node"
                         : he.detail == DETAIL_FEWPOINTS ? "fewer than three points for a modified operator"
@@ -925,10 +968,6 @@ cfp_status classify(cfp_ctx* c) {
     CFP_CUDA(cudaStreamSynchronize(c->stream));
     cudaFree(cnt);
     cudaFree(cnt2);
-    cudaFree(toff);
-    cudaFree(tval);
-    cudaFree(tbidx);
-    cudaFree(tbval);
     c->classified = true;
     c->class_status = CFP_OK;
     return CFP_OK;

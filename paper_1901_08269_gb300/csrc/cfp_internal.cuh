@@ -178,6 +178,10 @@ struct cfp_ctx {
     double* krow = nullptr;
     float* krow32 = nullptr;
 
+    // side-list build scratch (per-slot slices), kept across classifications
+    void* side_scratch = nullptr;
+    size_t side_scratch_bytes = 0;
+
     // scan scratch
     int* scan_bsum = nullptr;
     int64_t scan_cap = 0;
