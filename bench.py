@@ -411,6 +411,8 @@ def main():
         hgi = gi.cpu().pin_memory()
         hu = torch.zeros(w.N, dtype=torch.float64).pin_memory()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # one untimed call: the first allocates the context's device copies of the host buffers
+        ctx.solve_host(hf, hg, hgi, hu, tol=args.tol, opts=opts)
         torch.cuda.synchronize()
         a.record(stream)
         ctx.classify_points()
