@@ -308,7 +308,9 @@ enum { CFP_KERNEL_APPLY = 0,    /* B x with the fused (r_hat0, v) dot, as in
        CFP_KERNEL_MG_SWEEP = 3  /* one red half-sweep on the fine level of the
                                    multigrid preconditioner (CFP_PRECOND_MG),
                                    red and black nodes stored in separate
-                                   arrays                                    */ };
+                                   arrays; includes the follow-up launch that
+                                   applies the Shortley-Weller rows of the
+                                   irregular nodes                           */ };
 
 /*
  * Profiling aid: time `reps` >= 1 back-to-back launches of one kernel of the

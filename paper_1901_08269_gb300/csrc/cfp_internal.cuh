@@ -256,12 +256,6 @@ void launch_rbgs_half(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s);
 template <class T>
 void launch_half_sweep(const Grid<T>& G, const Side<T>& S, const uint8_t* type, const T* rho, T* phi, int colour,
                        bool first, cudaStream_t s);
-template <class T>
-T* precond_tmp(cfp_ctx* c);
-template <>
-double* precond_tmp<double>(cfp_ctx* c);
-template <>
-float* precond_tmp<float>(cfp_ctx* c);
 
 // multigrid (cfp_mg.cu)
 cfp_status ensure_mg(cfp_ctx* c, int prec);  // prec: 0 FP64 vectors, 1 FP32 vectors

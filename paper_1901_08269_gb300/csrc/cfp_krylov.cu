@@ -399,8 +399,8 @@ cfp_status ensure_work(cfp_ctx* c, bool need32) {
         CFP_CUDA(cudaMemsetAsync(c->v64, 0, sizeof(double) * N * kNV64, c->stream));
     }
     if (need32 && !c->v32) {
-        CFP_CUDA(cudaMalloc(&c->v32, sizeof(float) * N * (kNV32 + 2)));
-        CFP_CUDA(cudaMemsetAsync(c->v32, 0, sizeof(float) * N * (kNV32 + 2), c->stream));
+        CFP_CUDA(cudaMalloc(&c->v32, sizeof(float) * N * (kNV32 + 1)));  // + the FP32 right-hand side
+        CFP_CUDA(cudaMemsetAsync(c->v32, 0, sizeof(float) * N * (kNV32 + 1), c->stream));
     }
     const int64_t need = 2 * (int64_t)std::max(apply_blocks(c), kUpdBlocks);
     if (c->partial_cap < need) {

@@ -574,10 +574,6 @@ void launch_apply(cfp_ctx* c, const T* x, T* y, const T* d0, int dotmode, double
     if (nblocks_out) *nblocks_out = nmain + ncorr;
 }
 
-template <>
-double* precond_tmp<double>(cfp_ctx* c) { return c->v64 + (int64_t)V_TMP2 * c->N; }
-template <>
-float* precond_tmp<float>(cfp_ctx* c) { return c->v32 + (int64_t)(kNV32 + 1) * c->N; }
 
 // `sweeps` red-black sweeps from phi = 0 (sweeps = 0: masked copy).
 template <class T>
