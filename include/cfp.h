@@ -301,8 +301,9 @@ int64_t cfp_launch_count(const cfp_ctx* ctx);
 enum { CFP_KERNEL_APPLY = 0,    /* B x with the fused (r_hat0, v) dot, as in
                                    Algorithm 1 line 5                        */
        CFP_KERNEL_RBGS = 1,     /* one red half-sweep of red-black Gauss-Seidel
-                                   on K (Eq. A7), natural node order: the
-                                   inner iterations of Sec. 3.3              */
+                                   on K (Eq. A7), the inner iterations of
+                                   Sec. 3.3; the same split-layout kernel as
+                                   CFP_KERNEL_MG_SWEEP                       */
        CFP_KERNEL_UPDATE = 2,   /* the fused x/r update with two dots (lines
                                    11-12)                                    */
        CFP_KERNEL_MG_SWEEP = 3  /* one red half-sweep on the fine level of the

@@ -242,6 +242,7 @@ cfp_status cfp_precondition(cfp_ctx* c, int sweeps, const double* rho, double* p
     if (rho == phi) return fail(CFP_EINVAL, "rho and phi must not overlap");
     CFP_TRY(ensure_work(c, false));
     if (phi == c->v64 + (int64_t)V_TMP2 * c->N) return fail(CFP_EINVAL, "phi aliases the context's work space");
+    if (sweeps > 0) CFP_TRY(ensure_mg(c, 0));
     CFP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * c->N, c->stream));
     c->precond_kind = CFP_PRECOND_RBGS;
     launch_precond<double>(c, sweeps, rho, phi, c->stream);
@@ -265,7 +266,8 @@ cfp_status cfp_precondition_ex(cfp_ctx* c, const cfp_opts* o, const double* rho,
     c->precond_kind = opts.precond;
     c->mg_smooth = std::max(1, opts.mg_smooth);
     c->mg_post = opts.mg_post > 0 ? opts.mg_post : c->mg_smooth;
-    if (c->precond_kind == CFP_PRECOND_MG) CFP_TRY(ensure_mg(c, 0));
+    if (c->precond_kind == CFP_PRECOND_MG || (c->precond_kind == CFP_PRECOND_RBGS && opts.sweeps > 0))
+        CFP_TRY(ensure_mg(c, 0));
     if (c->precond_kind == CFP_PRECOND_ILU) CFP_TRY(ensure_ilu(c, 0));
     CFP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * c->N, c->stream));
     launch_precond<double>(c, opts.sweeps, rho, phi, c->stream);

@@ -251,11 +251,6 @@ void launch_apply(cfp_ctx* c, const T* x, T* y, const T* d0, int dotmode, double
                   cudaStream_t s, int* nblocks_out);
 template <class T>
 void launch_precond(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s);
-template <class T>
-void launch_rbgs_half(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s);
-template <class T>
-void launch_half_sweep(const Grid<T>& G, const Side<T>& S, const uint8_t* type, const T* rho, T* phi, int colour,
-                       bool first, cudaStream_t s);
 
 // multigrid (cfp_mg.cu)
 cfp_status ensure_mg(cfp_ctx* c, int prec);  // prec: 0 FP64 vectors, 1 FP32 vectors
@@ -267,6 +262,10 @@ cfp_status ensure_ilu(cfp_ctx* c, int prec);  // prec: 0 FP64, 1 FP32 (and FP64 
 void free_ilu(cfp_ctx* c);
 template <class T>
 void launch_precond_ilu(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s);
+// red-black sweeps from zero on the fine level's split vectors (the inner
+// iterations of CFP_PRECOND_RBGS)
+template <class T>
+void launch_rbgs_split(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s);
 // one plain red half-sweep on the fine level's split vectors (timing aid)
 template <class T>
 void launch_mg_half_sweep(cfp_ctx* c, cudaStream_t s);

@@ -424,8 +424,7 @@ cfp_status time_kernel_t(cfp_ctx* c, int prec, int kernel, int reps, double* ms,
     const int64_t nint = (int64_t)(c->n[0] - 2) * (c->n[1] - 2) * (c->n[2] - 2);
     auto launch = [&]() {
         if (kernel == CFP_KERNEL_APPLY) launch_apply<T>(c, V.ph, V.v, V.rh, 1, c->partial, c->stream, nullptr);
-        else if (kernel == CFP_KERNEL_RBGS) launch_rbgs_half<T>(c, V.p, V.ph, c->stream);
-        else if (kernel == CFP_KERNEL_MG_SWEEP) launch_mg_half_sweep<T>(c, c->stream);
+        else if (kernel == CFP_KERNEL_RBGS || kernel == CFP_KERNEL_MG_SWEEP) launch_mg_half_sweep<T>(c, c->stream);
         else
             k_update_xr<T><<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(V.x, V.r, V.ph, V.sh, V.s, V.t, V.rh, st,
                                                                       c->partial, c->N);
@@ -457,7 +456,7 @@ cfp_status time_kernel(cfp_ctx* c, int kernel, int prec, int reps, double* ms, d
     if (kernel < CFP_KERNEL_APPLY || kernel > CFP_KERNEL_MG_SWEEP || reps < 1 || !ms)
         return fail(CFP_EINVAL, "bad kernel id, reps or output pointer");
     CFP_TRY(ensure_work(c, prec == CFP_PREC_MIXED));
-    if (kernel == CFP_KERNEL_MG_SWEEP) CFP_TRY(ensure_mg(c, prec == CFP_PREC_MIXED ? 1 : 0));
+    if (kernel == CFP_KERNEL_MG_SWEEP || kernel == CFP_KERNEL_RBGS) CFP_TRY(ensure_mg(c, prec == CFP_PREC_MIXED ? 1 : 0));
     return prec == CFP_PREC_MIXED ? time_kernel_t<float>(c, 1, kernel, reps, ms, bytes)
                                   : time_kernel_t<double>(c, 0, kernel, reps, ms, bytes);
 }
@@ -486,7 +485,9 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
     c->mg_smooth = std::max(1, opts.mg_smooth);
     c->mg_post = opts.mg_post > 0 ? opts.mg_post : c->mg_smooth;
     const bool mixed = opts.precision == CFP_PREC_MIXED;
-    if (c->precond_kind == CFP_PRECOND_MG) CFP_TRY(ensure_mg(c, mixed ? 1 : 0));
+    // the multigrid option and the red-black sweeps (on the fine level's split arrays)
+    if (c->precond_kind == CFP_PRECOND_MG || (c->precond_kind == CFP_PRECOND_RBGS && opts.sweeps > 0))
+        CFP_TRY(ensure_mg(c, mixed ? 1 : 0));
     if (c->precond_kind == CFP_PRECOND_ILU) CFP_TRY(ensure_ilu(c, mixed ? 1 : 0));
     CFP_TRY(ensure_work(c, mixed));
     const int64_t N = c->N;

@@ -743,6 +743,11 @@ void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
 }
 
 template <class T>
+void launch_rbgs_split(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s) {
+    smooth<T>(c, 0, side_view<T>(c), sweeps, 2, 3, rho, phi, s);
+}
+
+template <class T>
 void launch_mg_half_sweep(cfp_ctx* c, cudaStream_t s) {
     const SLev<T> L = slev<T>(c, 0);
     half_sweep<T>(c, 0, L, side_view<T>(c), 0, 0, (const T*)nullptr, (T*)nullptr, s);
@@ -751,6 +756,8 @@ void launch_mg_half_sweep(cfp_ctx* c, cudaStream_t s) {
 template void launch_precond_mg<double>(cfp_ctx*, const double*, double*, cudaStream_t);
 template void launch_precond_mg<float>(cfp_ctx*, const float*, float*, cudaStream_t);
 template void launch_mg_half_sweep<double>(cfp_ctx*, cudaStream_t);
+template void launch_rbgs_split<double>(cfp_ctx*, int, const double*, double*, cudaStream_t);
+template void launch_rbgs_split<float>(cfp_ctx*, int, const float*, float*, cudaStream_t);
 template void launch_mg_half_sweep<float>(cfp_ctx*, cudaStream_t);
 
 }  // namespace cfp

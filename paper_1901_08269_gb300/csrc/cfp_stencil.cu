@@ -317,51 +317,6 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// One red-black Gauss-Seidel half-sweep on K phi = rho over the points of
-// one colour ((i+j+k) % 2 == colour), in place.  FIRST: phi = 0 on entry, so
-// the neighbour sum vanishes.  Only unknowns are written; phi must be zero at
-// box and solid nodes.  Launch: x over the colour points of a row, y = j-1,
-// z = k-1 (no integer division per point).  Used on every multigrid level
-// (coarse levels have no irregular points).
-constexpr int kRbgsThreads = 128;
-
-template <class T, bool FIRST>
-__global__ void __launch_bounds__(kRbgsThreads)
-    k_rbgs(Grid<T> G, Side<T> S, const uint8_t* __restrict__ type, const T* __restrict__ rho,
-           T* __restrict__ phi, int colour) {
-    const int nx = G.nx, ny = G.ny;
-    const int j = 1 + blockIdx.y, k = 1 + blockIdx.z;
-    const int i = 1 + ((1 + j + k + colour) & 1) + 2 * (int)(blockIdx.x * kRbgsThreads + threadIdx.x);
-    if (i > nx - 2) return;
-    const int64_t sy = nx, sz = (int64_t)nx * ny;
-    const int64_t l = (int64_t)k * sz + (int64_t)j * sy + i;
-    const uint8_t t = type[l];
-    if (t != CFP_REGULAR && t != CFP_IRREGULAR) return;
-    T dg, cxm, cxp, cym, cyp, czm, czp;
-    if (t == CFP_IRREGULAR) {
-        const T* kr = S.krow + 7 * (int64_t)S.slot[l];
-        dg = kr[0];
-        cxm = kr[1];
-        cxp = kr[2];
-        cym = kr[3];
-        cyp = kr[4];
-        czm = kr[5];
-        czp = kr[6];
-    } else {
-        dg = G.ax[0].kb[i] + G.ax[1].kb[j] + G.ax[2].kb[k];
-        cxm = G.ax[0].ka[i];
-        cxp = G.ax[0].kc[i];
-        cym = G.ax[1].ka[j];
-        cyp = G.ax[1].kc[j];
-        czm = G.ax[2].ka[k];
-        czp = G.ax[2].kc[k];
-    }
-    T v = rho[l];
-    if (!FIRST)
-        v -= (cxm * phi[l - 1] + cxp * phi[l + 1]) + (cym * phi[l - sy] + cyp * phi[l + sy]) +
-             (czm * phi[l - sz] + czp * phi[l + sz]);
-    phi[l] = v / dg;
-}
 
 template <class T>
 __global__ void k_mask_copy(const uint8_t* __restrict__ type, const T* __restrict__ in, T* __restrict__ out,
@@ -502,23 +457,6 @@ unsigned flat_grid(int64_t n) {
 
 }  // namespace
 
-// colour points per row: ceil((nx - 2) / 2) = (nx - 1) / 2
-dim3 rbgs_grid(int nx, int ny, int nz) {
-    const int nh = (nx - 1) / 2;
-    return dim3((unsigned)((nh + kRbgsThreads - 1) / kRbgsThreads), (unsigned)(ny - 2), (unsigned)(nz - 2));
-}
-
-template <class T>
-void launch_half_sweep(const Grid<T>& G, const Side<T>& S, const uint8_t* type, const T* rho, T* phi, int colour,
-                       bool first, cudaStream_t s) {
-    const dim3 nb = rbgs_grid(G.nx, G.ny, G.nz);
-    if (first) k_rbgs<T, true><<<nb, kRbgsThreads, 0, s>>>(G, S, type, rho, phi, colour);
-    else k_rbgs<T, false><<<nb, kRbgsThreads, 0, s>>>(G, S, type, rho, phi, colour);
-}
-template void launch_half_sweep<double>(const Grid<double>&, const Side<double>&, const uint8_t*, const double*,
-                                        double*, int, bool, cudaStream_t);
-template void launch_half_sweep<float>(const Grid<float>&, const Side<float>&, const uint8_t*, const float*, float*,
-                                       int, bool, cudaStream_t);
 
 namespace {
 
@@ -575,20 +513,18 @@ void launch_apply(cfp_ctx* c, const T* x, T* y, const T* d0, int dotmode, double
 }
 
 
-// `sweeps` red-black sweeps from phi = 0 (sweeps = 0: masked copy).
+// `sweeps` red-black sweeps from phi = 0 (sweeps = 0: masked copy).  The
+// sweeps run on the fine level's red/black split arrays of the multigrid
+// hierarchy (the first red half-sweep reads rho, the last black one writes
+// phi at every interior node), which ensure_mg provides.
 template <class T>
 void launch_precond_rbgs(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s) {
-    const Grid<T> G = grid_view<T>(c);
-    const Side<T> S = side_view<T>(c);
-    c->launches += sweeps <= 0 ? 1 : 2 * sweeps;
     if (sweeps <= 0) {
+        c->launches += 1;
         k_mask_copy<T><<<flat_grid(c->N), 256, 0, s>>>(c->type, rho, phi, c->N);
         return;
     }
-    for (int sw = 0; sw < sweeps; ++sw) {
-        launch_half_sweep<T>(G, S, c->type, rho, phi, 0, sw == 0, s);
-        launch_half_sweep<T>(G, S, c->type, rho, phi, 1, false, s);
-    }
+    launch_rbgs_split<T>(c, sweeps, rho, phi, s);
 }
 
 template <class T>
@@ -598,15 +534,6 @@ void launch_precond(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_t s
     else launch_precond_rbgs<T>(c, sweeps, rho, phi, s);
 }
 
-// one half-sweep (not the first), for timing
-template <class T>
-void launch_rbgs_half(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
-    launch_half_sweep<T>(grid_view<T>(c), side_view<T>(c), c->type, rho, phi, 0, false, s);
-    c->launches += 1;
-}
-
-template void launch_rbgs_half<double>(cfp_ctx*, const double*, double*, cudaStream_t);
-template void launch_rbgs_half<float>(cfp_ctx*, const float*, float*, cudaStream_t);
 // y = B gb for the boundary lift gb (zero away from the box), FP64
 void launch_apply_lift(cfp_ctx* c, const double* gb, double* y, cudaStream_t s) {
     cudaMemsetAsync(y, 0, sizeof(double) * c->N, s);

@@ -1,9 +1,10 @@
 """Time single kernels of the solve through cfp_time_kernel.
 
 Builds a context on the config-3 geometry at n^3, classifies it, and times
-the red-black half-sweep (natural layout, and the multigrid fine-level one
-in the split layout), the apply (with its fused dot) and the x/r update in
-the requested precision.  Small launch count, so it is the command used
+the red-black half-sweep on the fine level's red/black split arrays (the
+kernel of both the multigrid smoother and the plain red-black inner
+iterations), the apply (with its fused dot) and the x/r update in the
+requested precision.  Small launch count, so it is the command used
 for ncu captures of those kernels:
 
     python -m paper_1901_08269_gb300.kernel_probe --n 385 --precision mixed --reps 3
@@ -17,7 +18,7 @@ def main():
     ap.add_argument("--n", type=int, default=385)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--kernels", default="rbgs,mg_sweep,apply,update")
+    ap.add_argument("--kernels", default="mg_sweep,apply,update")
     a = ap.parse_args()
     import torch
 
