@@ -7,7 +7,9 @@
 // stays valid, and its quality does not degrade with the grid size.
 //
 // Levels: vertex-centred coarsening per axis, coarse node I sits on fine node
-// map(I) = min(2I, n-1), n_c = (n + 2) / 2, while every axis has >= 9 nodes.
+// map(I) = min(2I, n-1), n_c = (n + 2) / 2, while every axis has >= 17 nodes
+// (so the coarsest level has 9 to 16 nodes on its shortest axis: 10^3 below
+// 513^3; one level more or less was slower there).
 // Coarse K is the 7-point operator rediscretised on the coarse coordinates
 // (Eq. 2ndorder_coef); a coarse node is solid if its fine node is solid, and
 // its solid neighbours enter with value zero (Dirichlet at the node, no
@@ -567,7 +569,7 @@ cfp_status build_levels(cfp_ctx* c) {
         F0.X[d] = c->X[d];
     }
     F0.N = c->N;
-    while (std::min({levels.back().n[0], levels.back().n[1], levels.back().n[2]}) >= 9) {
+    while (std::min({levels.back().n[0], levels.back().n[1], levels.back().n[2]}) >= 17) {
         MgLevel Cn;
         const MgLevel& Fp = levels.back();
         for (int d = 0; d < 3; ++d) {

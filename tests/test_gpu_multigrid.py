@@ -7,7 +7,7 @@ approximate solve of the same system K phi = rho.  The definition checked
 here, step by step on whole arrays in natural node order:
 
   levels      n_c = (n + 2) // 2 per axis while every axis of the finer level
-              has >= 9 nodes; coarse node I sits on fine node min(2I, n - 1)
+              has >= 17 nodes; coarse node I sits on fine node min(2I, n - 1)
   types       injected from the fine node (irregular becomes regular)
   K           the fine level's K is the oracle's (Eq. A7 and the
               Shortley-Weller rows); a coarse K is the 7-point operator of
@@ -71,7 +71,7 @@ def interpolation(Xf, Xc, n):
 def build_levels(x, y, z, otype, K0):
     n = (len(x), len(y), len(z))
     levels = [dict(n=n, X=[np.asarray(x), np.asarray(y), np.asarray(z)], type=otype, K=K0)]
-    while min(levels[-1]["n"]) >= 9:
+    while min(levels[-1]["n"]) >= 17:
         F = levels[-1]
         nc = tuple((m + 2) // 2 for m in F["n"])
         idx = [np.minimum(2 * np.arange(nc[d]), F["n"][d] - 1) for d in range(3)]
