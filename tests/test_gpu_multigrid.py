@@ -134,6 +134,9 @@ CASES = {
                                        [W.torus((0.02, 0.01, -0.03), 0.45, 0.16, W.rot_euler(0.1, 0.5, 0.3))],
                                        W._c3_u, W._c3_f),
     "interior-sphere": lambda: W.interior_sphere(41),
+    "even-48": lambda: W.Workload("even", W.tanh_grid(-1, 1, 48, 1.2), W.uniform_grid(-1, 1, 34),
+                                  W.tanh_grid(-1, 1, 40, 0.8), [W.sphere((0.04, -0.02, 0.03), 0.35)],
+                                  W._c2_u, W._c2_f),
     "tiny-one-level": lambda: W.Workload("tiny", W.uniform_grid(-1, 1, 8), W.uniform_grid(-1, 1, 11),
                                          W.uniform_grid(-1, 1, 9), [W.sphere((0.1, 0.0, 0.05), 0.4)],
                                          W._c2_u, W._c2_f),

@@ -41,6 +41,12 @@ CASES = {
     "random-3": lambda: W.random_problem(3, sizes=(33, 49)),
     "interior-sphere": lambda: W.interior_sphere(41),
     "random-8": lambda: W.random_problem(8, sizes=(33, 49)),
+    # even sizes, n_x / 2 a multiple of 8: rows of the red/black split arrays
+    # without padding (the speculative x+ load of a row's last pair reads the
+    # next row)
+    "even-48": lambda: W.Workload("even", W.tanh_grid(-1, 1, 48, 1.2), W.uniform_grid(-1, 1, 34),
+                                  W.tanh_grid(-1, 1, 40, 0.8), [W.sphere((0.04, -0.02, 0.03), 0.35)],
+                                  W._c2_u, W._c2_f),
 }
 
 
