@@ -192,7 +192,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "config3-%d^3-ellipsoid+torus" % args.n, "n": args.n, "precision": "fp64"},
+            "config": dict(workload_config(args, 1), precision="fp64", precond="rbgs", sweeps=8),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -275,6 +275,26 @@ def batch_arm(args):
     return 0
 
 
+def workload_config(args, world):
+    """The workload part of the JSON line's config, shared by both arms."""
+    return {"workload": "config3-%d^3-ellipsoid+torus" % args.n, "n": args.n,
+            "grid": "tanh (2.0, 1.2, 1.2) on [-1,1]^3", "tol": args.tol,
+            "l2": "no flush: every field (%.2f GB at %d^3) exceeds the 129 MB L2" % (8e-9 * args.n ** 3, args.n),
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+def job_time(ms, steps, world, dist=None, device="cpu"):
+    """Timed region of the whole job: the maximum over ranks of each rank's
+    ms (every rank runs its own replica), ms per step, and the whole-job
+    seconds per solve (all ranks' solves in that time)."""
+    import torch
+    if dist is not None and world > 1:
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, ms / steps, ms / 1000.0 / (steps * world)
+
+
 # --------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -344,13 +364,7 @@ def main():
         dist.barrier()
     launches = ctx.launch_count() - l0
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_per_step = ms / args.steps
-    value = ms / 1000.0 / (args.steps * world)
+    ms, ms_per_step, value = job_time(e0.elapsed_time(e1), args.steps, world, dist, "cuda")
 
     X, Y, Z = w.mesh(torch, "cuda")
     ue = w.u(X, Y, Z, torch).reshape(-1)
@@ -438,13 +452,9 @@ def main():
                 "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64" if prec == cfp.PREC_MIXED else "f64", "data": "synthetic",
-                "config": {"workload": "config3-%d^3-ellipsoid+torus" % args.n, "n": args.n,
-                           "grid": "tanh (2.0, 1.2, 1.2) on [-1,1]^3", "precision": args.precision,
-                           "tol": args.tol, "inner_tol": args.inner_tol, "sweeps": args.sweeps,
-                           "precond": args.precond, "mg_smooth": args.mg_smooth, "mg_post": args.mg_post or args.mg_smooth,
-                           "l2": "no flush: every field (1.08 GB at 513^3) exceeds the 129 MB L2",
-                           "parallelism": "replicas" if world > 1 else "single",
-                           "graph": not args.no_graph},
+                "config": dict(workload_config(args, world), precision=args.precision, inner_tol=args.inner_tol,
+                               sweeps=args.sweeps, precond=args.precond, mg_smooth=args.mg_smooth,
+                               mg_post=args.mg_post or args.mg_smooth, graph=not args.no_graph),
                 "result": result, "phases": phases, "fp64": fp64, "kernels": kern, "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
