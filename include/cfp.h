@@ -126,7 +126,8 @@ const char* cfp_last_error(void);
 /*
  * Create a context on the current CUDA device (Sec. 2 grid).
  *   x, y, z  host arrays of nx, ny, nz >= 3 strictly increasing coordinates
- *            (a_1 = x_1 < x_2 < ... < x_nx = a_2); copied.
+ *            (a_1 = x_1 < x_2 < ... < x_nx = a_2); copied.  N = nx*ny*nz
+ *            must be below 2^31 (larger grids do not fit the GPU anyway).
  *   bodies   host array of nbodies >= 0 bodies; copied.
  *   fluid_inside  0: the fluid is outside the bodies (Omega^+ of Sec. 1);
  *            1: the fluid is the inside (interior problems, Problem 4).
@@ -208,7 +209,7 @@ cfp_status cfp_precondition(cfp_ctx* ctx, int sweeps, const double* rho_dev,
 
 /*
  * phi = P(rho) with the preconditioner chosen in opts (precond, sweeps,
- * mg_smooth; NULL: defaults), as applied inside cfp_solve.  Fields, no
+ * mg_smooth, mg_post; NULL: defaults), as applied inside cfp_solve.  Fields, no
  * overlap; phi is 0 at box and solid nodes.  Errors as cfp_precondition.
  */
 cfp_status cfp_precondition_ex(cfp_ctx* ctx, const cfp_opts* opts,
