@@ -236,9 +236,12 @@ def batch_arm(args):
     nmax = max(tuned)
     opts = tuned[nmax]
 
+    from concurrent.futures import ThreadPoolExecutor
+    pool = ThreadPoolExecutor(16)  # contexts classify independently (the C calls release the GIL)
+
     def step():
+        list(pool.map(lambda p: p[1].classify_points(), probs))
         for w, ctx, f, g, gi, u in probs:
-            ctx.classify_points()
             u.zero_()
         torch.cuda.synchronize()
         return cfp.solve_batch([p[1] for p in probs], [p[2] for p in probs], [p[3] for p in probs],
@@ -270,6 +273,7 @@ def batch_arm(args):
                        "tol": args.batch_tol},
             "sequential_s": seq, "iterations": [i.iterations for i in infos[:8]], "gpu_launches": None}
     print(json.dumps(line), flush=True)
+    pool.shutdown()
     for p in probs:
         p[1].close()
     return 0
