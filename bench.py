@@ -407,8 +407,13 @@ def main():
     peak, psrc = hbm_peak()
     tname = "float" if kprec == cfp.PREC_MIXED else "double"
     # both the multigrid smoother and the plain red-black inner iterations run
-    # this half-sweep (red and black nodes in separate arrays)
-    dom, kname, src = kern["rb_half"], "k_sweep_split<%s> half-sweep" % tname, "cfp_mg.cu"
+    # this half-sweep (red and black nodes in separate arrays); in FP32 on rows
+    # of >= 192 nodes it is the TMA-fed kernel
+    if kprec == cfp.PREC_MIXED and args.n // 2 >= 96:
+        kname = "k_sweep_tma half-sweep"
+    else:
+        kname = "k_sweep_split<%s> half-sweep" % tname
+    dom, src = kern["rb_half"], "cfp_mg.cu"
     roofline = {"bound": "hbm", "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
                 "frac": dom["gbs"] / peak, "traffic": None, "kernel": kname, "peak_source": psrc}
     tr = os.path.join(ROOT, "profiles", "traffic.json")

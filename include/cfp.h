@@ -96,6 +96,12 @@ typedef struct {
                           (default 2)                                       */
     int mg_post;       /* CFP_PRECOND_MG: sweeps after the coarse correction;
                           0 (default): mg_smooth                            */
+    int mg_tma;        /* 1 (default): the FP32 red-black half-sweeps of the
+                          multigrid levels (and of the fine level's sweeps)
+                          with at least 192 nodes per row stream their tiles
+                          through shared memory with TMA bulk-tensor copies;
+                          0: plain loads.  Same arithmetic, bitwise equal
+                          results                                          */
 } cfp_opts;
 
 typedef struct {
@@ -209,8 +215,13 @@ cfp_status cfp_precondition(cfp_ctx* ctx, int sweeps, const double* rho_dev,
 
 /*
  * phi = P(rho) with the preconditioner chosen in opts (precond, sweeps,
- * mg_smooth, mg_post; NULL: defaults), as applied inside cfp_solve.  Fields, no
- * overlap; phi is 0 at box and solid nodes.  Errors as cfp_precondition.
+ * mg_smooth, mg_post, mg_tma; NULL: defaults), as applied inside cfp_solve.
+ * opts->precision CFP_PREC_FP64: in FP64; CFP_PREC_MIXED: in FP32, as the
+ * mixed solve's inner iterations apply it (rho rounded to FP32, phi widened;
+ * rho must lie within the FP32 range), and the call synchronises.  Fields,
+ * no overlap; phi is 0 at box and solid nodes.  Errors as cfp_precondition,
+ * and CFP_ECUDA if a bounded pipeline wait of a kernel timed out (one second;
+ * the results are then not valid).
  */
 cfp_status cfp_precondition_ex(cfp_ctx* ctx, const cfp_opts* opts,
                                const double* rho_dev, double* phi_dev);
@@ -312,7 +323,10 @@ enum { CFP_KERNEL_APPLY = 0,    /* B x with the fused (r_hat0, v) dot, as in
                                    red and black nodes stored in separate
                                    arrays; includes the follow-up launch that
                                    applies the Shortley-Weller rows of the
-                                   irregular nodes                           */ };
+                                   irregular nodes.  In FP32 on a fine level
+                                   of >= 192 nodes per row, the TMA-fed
+                                   kernel (unless the last solve or
+                                   preconditioner call set mg_tma = 0)      */ };
 
 /*
  * Profiling aid: time `reps` >= 1 back-to-back launches of one kernel of the

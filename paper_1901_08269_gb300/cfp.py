@@ -32,7 +32,7 @@ class Body(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("sweeps", C.c_int), ("maxit", C.c_int), ("max_restarts", C.c_int),
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("use_graph", C.c_int),
-                ("precond", C.c_int), ("mg_smooth", C.c_int), ("mg_post", C.c_int)]
+                ("precond", C.c_int), ("mg_smooth", C.c_int), ("mg_post", C.c_int), ("mg_tma", C.c_int)]
 
 
 class Info(C.Structure):

@@ -71,6 +71,7 @@ void cfp_default_opts(cfp_opts* o) {
     o->precond = CFP_PRECOND_RBGS;
     o->mg_smooth = 2;
     o->mg_post = 0;
+    o->mg_tma = 1;
 }
 
 const char* cfp_last_error(void) { return g_last_error.c_str(); }
@@ -128,6 +129,8 @@ cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny, cons
     chk(cudaMalloc(&c->slot, sizeof(int32_t) * (size_t)N), "cudaMalloc");
     chk(cudaMalloc(&c->dtotal, sizeof(long long) * 8), "cudaMalloc");
     chk(cudaMalloc(&c->derr, sizeof(DevError)), "cudaMalloc");
+    chk(cudaMalloc(&c->dwait, sizeof(int)), "cudaMalloc");
+    if (c->dwait) chk(cudaMemsetAsync(c->dwait, 0, sizeof(int), c->stream), "cudaMemsetAsync");
     chk(cudaMalloc(&c->kst, sizeof(KState) * 2), "cudaMalloc");
     chk(cudaMallocHost(&c->hkst, sizeof(KState) * 2), "cudaMallocHost");
     if (st == CFP_OK) {
@@ -173,7 +176,7 @@ void cfp_ctx_destroy(cfp_ctx* c) {
     free_ilu(c);
     void* ptrs[] = {c->dcoef64, c->dcoef32, c->dX[0], c->dX[1], c->dX[2], c->dbodies, c->dbound2, c->type, c->slot, c->irr_lin,
                     c->ibi_off, c->ibi_xyz, c->corr_ptr, c->corr_off, c->corr_val, c->corr_val32, c->bib_ptr,
-                    c->bib_idx, c->bib_val, c->krow, c->krow32, c->side_scratch, c->scan_bsum, c->dtotal, c->derr, c->v64, c->v32,
+                    c->bib_idx, c->bib_val, c->krow, c->krow32, c->side_scratch, c->scan_bsum, c->dtotal, c->derr, c->dwait, c->v64, c->v32,
                     c->partial, c->kst, c->hs_f, c->hs_g, c->hs_u, c->hs_gi};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -260,20 +263,31 @@ cfp_status cfp_precondition_ex(cfp_ctx* c, const cfp_opts* o, const double* rho,
     if (opts.sweeps < 0 ||
         (opts.precond != CFP_PRECOND_RBGS && opts.precond != CFP_PRECOND_MG && opts.precond != CFP_PRECOND_ILU))
         return fail(CFP_EINVAL, "bad sweeps or preconditioner");
+    if (opts.precision != CFP_PREC_FP64 && opts.precision != CFP_PREC_MIXED) return fail(CFP_EINVAL, "bad precision");
     if (rho == phi) return fail(CFP_EINVAL, "rho and phi must not overlap");
-    CFP_TRY(ensure_work(c, false));
+    const int prec = opts.precision == CFP_PREC_MIXED ? 1 : 0;
+    CFP_TRY(ensure_work(c, prec == 1));
     if (phi == c->v64 + (int64_t)V_TMP2 * c->N) return fail(CFP_EINVAL, "phi aliases the context's work space");
     c->precond_kind = opts.precond;
     c->mg_smooth = std::max(1, opts.mg_smooth);
     c->mg_post = opts.mg_post > 0 ? opts.mg_post : c->mg_smooth;
+    c->mg_tma = opts.mg_tma != 0;
+    cfp_status st = CFP_OK;
     if (c->precond_kind == CFP_PRECOND_MG || (c->precond_kind == CFP_PRECOND_RBGS && opts.sweeps > 0))
-        CFP_TRY(ensure_mg(c, 0));
-    if (c->precond_kind == CFP_PRECOND_ILU) CFP_TRY(ensure_ilu(c, 0));
-    CFP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * c->N, c->stream));
-    launch_precond<double>(c, opts.sweeps, rho, phi, c->stream);
+        st = ensure_mg(c, prec);
+    if (st == CFP_OK && c->precond_kind == CFP_PRECOND_ILU) st = ensure_ilu(c, prec);
+    if (st == CFP_OK) {
+        if (prec == 1) {
+            st = precondition32(c, opts.sweeps, rho, phi);
+            if (st == CFP_OK) st = check_waits(c);
+        } else {
+            CFP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * c->N, c->stream));
+            launch_precond<double>(c, opts.sweeps, rho, phi, c->stream);
+            CFP_CUDA(cudaGetLastError());
+        }
+    }
     c->precond_kind = CFP_PRECOND_RBGS;
-    CFP_CUDA(cudaGetLastError());
-    return CFP_OK;
+    return st;
 }
 
 cfp_status cfp_solve(cfp_ctx* c, const double* f, const double* g, const double* gi, double* u, double tol,

@@ -1,6 +1,7 @@
 // Internal declarations of the CUDA library behind include/cfp.h.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (types only; the encoder is fetched from the driver at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -127,7 +128,8 @@ struct MgLevel {
     uint8_t* type = nullptr;   // natural layout (levels >= 1; level 0 uses the context's)
     // red-black split layout: node (i, j, k) of colour (i + j + k) & 1 sits at
     // entry (k * n[1] + j) * hp + (i >> 1) of its colour's array
-    int hp = 0;                // entries per row of one colour, padded to 8
+    int hp = 0;                // entries per row of one colour, padded to 16 (16-byte rows of
+                               // the byte-wide split type, as the TMA tensor maps require)
     int64_t Nh = 0;            // entries per colour array: hp * n[1] * n[2]
     uint8_t* stype = nullptr;  // split type, colour c at stype + c * Nh
     double* s64 = nullptr;     // split e0 e1 b0 b1 r0 (Nh each), FP64
@@ -138,6 +140,12 @@ struct MgLevel {
     int64_t off[3] = {0, 0, 0};
     double* w64 = nullptr;
     float* w32 = nullptr;
+    // TMA-fed FP32 half-sweep (levels with at least kTmaMinPairs pairs per
+    // row): per colour c, maps of the other colour's e, of b and of the type
+    // at tm32[3 c + 0 .. 2]; grid = persistent CTAs (resident CTAs x SMs)
+    int tma = 0;
+    int tma_grid = 0;
+    CUtensorMap tm32[6];
 };
 
 }  // namespace cfp
@@ -210,6 +218,8 @@ struct cfp_ctx {
     int precond_kind = CFP_PRECOND_RBGS;
     int mg_smooth = 2;
     int mg_post = 2;
+    int mg_tma = 1;            // 1: TMA-fed FP32 half-sweeps where a level supports them
+    int* dwait = nullptr;      // device word: nonzero once a bounded pipeline wait timed out
     std::vector<cfp::MgLevel> mg;
     // ILU(0) of K (CFP_PRECOND_ILU): [pivots | work field], FP64 and FP32
     double* ilu64 = nullptr;
@@ -282,5 +292,13 @@ void launch_metrics(cfp_ctx* c);  // Eq. app_xxx and Eq. 2ndorder_coef per axis
 // Krylov (cfp_krylov.cu)
 cfp_status ensure_work(cfp_ctx* c, bool need32);
 cfp_status time_kernel(cfp_ctx* c, int kernel, int prec, int reps, double* ms, double* bytes);
+// phi = P(rho) in FP32 (the mixed solve's inner preconditioner) for FP64
+// fields: rho rounded to FP32, phi widened back; phi zeroed first
+cfp_status precondition32(cfp_ctx* c, int sweeps, const double* rho, double* phi);
+// the graph-cache key of the multigrid settings
+int mg_key(const cfp_ctx* c);
+// CFP_ECUDA (and the device word cleared) if a bounded pipeline wait of a
+// kernel timed out since the last check; synchronises the stream
+cfp_status check_waits(cfp_ctx* c);
 
 }  // namespace cfp

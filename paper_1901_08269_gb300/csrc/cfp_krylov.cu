@@ -275,7 +275,7 @@ int64_t body_launches(cfp_ctx* c) { return c->body_launches; }
 template <class T>
 cfp_status build_graph(cfp_ctx* c, int prec, int sweeps) {
     if (c->gexec[prec] && c->gsweeps[prec] == sweeps && c->gprecond[prec] == c->precond_kind &&
-        c->gmgs[prec] == c->mg_smooth * 1000 + c->mg_post)
+        c->gmgs[prec] == mg_key(c))
         return CFP_OK;
     if (c->gexec[prec]) {
         cudaGraphExecDestroy(c->gexec[prec]);
@@ -316,7 +316,7 @@ cfp_status build_graph(cfp_ctx* c, int prec, int sweeps) {
     c->gexec[prec] = exec;
     c->gsweeps[prec] = sweeps;
     c->gprecond[prec] = c->precond_kind;
-    c->gmgs[prec] = c->mg_smooth * 1000 + c->mg_post;
+    c->gmgs[prec] = mg_key(c);
     return CFP_OK;
 }
 
@@ -457,8 +457,36 @@ cfp_status time_kernel(cfp_ctx* c, int kernel, int prec, int reps, double* ms, d
         return fail(CFP_EINVAL, "bad kernel id, reps or output pointer");
     CFP_TRY(ensure_work(c, prec == CFP_PREC_MIXED));
     if (kernel == CFP_KERNEL_MG_SWEEP || kernel == CFP_KERNEL_RBGS) CFP_TRY(ensure_mg(c, prec == CFP_PREC_MIXED ? 1 : 0));
-    return prec == CFP_PREC_MIXED ? time_kernel_t<float>(c, 1, kernel, reps, ms, bytes)
-                                  : time_kernel_t<double>(c, 0, kernel, reps, ms, bytes);
+    CFP_TRY(prec == CFP_PREC_MIXED ? time_kernel_t<float>(c, 1, kernel, reps, ms, bytes)
+                                   : time_kernel_t<double>(c, 0, kernel, reps, ms, bytes));
+    return check_waits(c);
+}
+
+int mg_key(const cfp_ctx* c) { return c->mg_smooth * 1000 + c->mg_post + (c->mg_tma ? 1000000 : 0); }
+
+cfp_status check_waits(cfp_ctx* c) {
+    int w = 0;
+    CFP_CUDA(cudaMemcpyAsync(&w, c->dwait, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CFP_CUDA(cudaStreamSynchronize(c->stream));
+    if (w == 0) return CFP_OK;
+    CFP_CUDA(cudaMemsetAsync(c->dwait, 0, sizeof(int), c->stream));
+    CFP_CUDA(cudaStreamSynchronize(c->stream));
+    return fail(CFP_ECUDA, "a shared-memory pipeline wait of the multigrid smoother timed out (code " +
+                               std::to_string(w) + "); the results of that call are not valid");
+}
+
+cfp_status precondition32(cfp_ctx* c, int sweeps, const double* rho, double* phi) {
+    const int64_t N = c->N;
+    float* rho32 = c->v32 + (int64_t)V_R * N;
+    float* phi32 = c->v32 + (int64_t)V_PH * N;
+    k_to32<<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(rho, rho32, 1.0, N);
+    k_zero<float><<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(phi32, N);
+    launch_precond<float>(c, sweeps, rho32, phi32, c->stream);
+    CFP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * N, c->stream));
+    k_add32<<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(phi, phi32, 1.0, N);
+    c->launches += 3;
+    CFP_CUDA(cudaGetLastError());
+    return CFP_OK;
 }
 
 cfp_status solve_impl(cfp_ctx* c, const double* f, const double* g, const double* gi, double* u, double tol,
@@ -484,6 +512,7 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
     c->precond_kind = opts.precond;
     c->mg_smooth = std::max(1, opts.mg_smooth);
     c->mg_post = opts.mg_post > 0 ? opts.mg_post : c->mg_smooth;
+    c->mg_tma = opts.mg_tma != 0;
     const bool mixed = opts.precision == CFP_PREC_MIXED;
     // the multigrid option and the red-black sweeps (on the fine level's split arrays)
     if (c->precond_kind == CFP_PRECOND_MG || (c->precond_kind == CFP_PRECOND_RBGS && opts.sweeps > 0))
@@ -565,6 +594,7 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
     CFP_CUDA(cudaGetLastError());
     CFP_CUDA(cudaStreamSynchronize(c->stream));
     const auto t3 = clk::now();
+    CFP_TRY(check_waits(c));
     if (info) {
         info->status = status;
         info->iterations = total;

@@ -20,9 +20,11 @@
 // coarsest level.
 //
 // Storage: every level keeps its vectors in a red-black split layout (each
-// colour in its own array, rows of (n_x + 1) / 2 entries padded to 8), so a
+// colour in its own array, rows of (n_x + 1) / 2 entries padded to 16), so a
 // half-sweep reads the other colour and writes its own without moving the
-// unused half of each cache line.  The fine level converts on the way in
+// unused half of each cache line.  On the large levels the FP32 half-sweeps
+// stream tiles of the other colour (with a one-node halo), of b and of the
+// type through shared memory with TMA bulk-tensor copies (k_sweep_tma).  The fine level converts on the way in
 // (the first red half-sweep reads rho in the natural layout and stores both
 // colours of it) and on the way out (the last black half-sweep writes both
 // colours of phi in the natural layout).
@@ -34,6 +36,8 @@
 // coarse correction is only added to the black nodes.
 #include <algorithm>
 #include <vector>
+
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
 
 #include "cfp_internal.cuh"
 
@@ -101,9 +105,17 @@ enum { kSplitVecs = 5 };  // e0 e1 b0 b1 r0
 
 __device__ __forceinline__ bool is_unknown(uint8_t t) { return t == CFP_REGULAR || t == CFP_IRREGULAR; }
 
-// x * (1 / d) with a correctly rounded reciprocal: two roundings instead of
-// the division's one, several times cheaper than an IEEE division.
-__device__ __forceinline__ float times_rcp(float x, float d) { return x * __frcp_rn(d); }
+// x * (1 / d).  FP64: a correctly rounded reciprocal (two roundings instead
+// of the division's one, several times cheaper than an IEEE division).  FP32:
+// the hardware reciprocal approximation (rcp.approx.ftz.f32, within 1 ulp of
+// 1 / d; the diagonal of K is a normal number), a single instruction where the
+// correctly rounded one costs a short sequence: the FP32 smoother is the inner
+// preconditioner of the mixed solve, whose FP64 refinement removes the error.
+__device__ __forceinline__ float times_rcp(float x, float d) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    return x * r;
+}
 __device__ __forceinline__ double times_rcp(double x, double d) { return x * __drcp_rn(d); }
 
 // One red-black half-sweep of colour `colour` on a split level, with K's
@@ -186,6 +198,207 @@ __global__ void __launch_bounds__(kSplitThreads)
         } else if (live[q]) {
             H.eown[o] = val[q];
         }
+    }
+}
+
+// ---------------------------------------------------------------- TMA path
+// The FP32 plain half-sweep (MODE 0) of a large level as a pipeline: per CTA
+// one producer thread streams planes of a tile through a ring of shared-memory
+// stages with cp.async.bulk.tensor (completion counted on an mbarrier per
+// stage), and kTmaRows consumer warps update the tile's nodes from shared
+// memory and release each plane through a second mbarrier.  A tile is
+// kTmaTX pairs x kTmaRows rows x kTmaPlanes planes of colour `colour`; a
+// stage holds, for one plane k, the other colour's pairs m0 - 4 .. m0 +
+// kTmaTX + 3 of rows j0 - 1 .. j0 + kTmaRows (the one-node halo in x and y;
+// the x start is a multiple of 4 entries, 16 bytes), b and the type of the
+// tile's own rows; the output of plane k reads the stages of planes k - 1,
+// k, k + 1.  Copies outside the array (row j0 + kTmaRows past the last, pair
+// -4 .. -1) fill zeros and feed only nodes that are not updated.  The CTAs
+// are persistent: CTA q takes tiles q, q + grid, ... with the x tile varying
+// fastest, then y, then the z chunk, so the CTAs at work at one time share
+// their halo rows through L2.  Same arithmetic as k_sweep_split<float, 0>:
+// the results are bitwise equal.
+constexpr int kTmaTX = 128;     // pairs per tile row: one consumer thread each
+constexpr int kTmaRows = 8;     // rows per tile: consumer warps 0-3 take rows 0-3, warps 4-7 rows 4-7
+constexpr int kTmaPlanes = 32;  // output planes per tile
+constexpr int kTmaStages = 6;   // planes in the shared-memory ring
+constexpr int kTmaMinPairs = 96;  // levels with fewer pairs per row use k_sweep_split
+constexpr int kTmaOX = kTmaTX + 8;                                   // other-colour row in a stage
+constexpr int kTmaOBytes = kTmaOX * (kTmaRows + 2) * 4;              // other-colour tile
+constexpr int kTmaOPad = (kTmaOBytes + 127) / 128 * 128;
+constexpr int kTmaBBytes = kTmaTX * kTmaRows * 4;                    // b of the tile
+constexpr int kTmaTBytes = kTmaTX * kTmaRows;                        // type of the tile
+constexpr int kTmaStage = kTmaOPad + kTmaBBytes + kTmaTBytes;
+constexpr int kTmaThreads = 32 * (kTmaRows + 1);                     // + the producer warp
+constexpr int kTmaSmem = kTmaStages * kTmaStage + 2 * kTmaStages * 8 + 128;  // + barriers, alignment
+static_assert(kTmaStage % 128 == 0 && kTmaBBytes % 128 == 0, "stage buffers stay 128-byte aligned");
+static_assert(kTmaRows % 4 == 0, "rows come in groups of four per 128 consumer threads");
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of parity `parity` of barrier b to complete, for one
+// second at most (a healthy wait takes microseconds); false if it did not.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+    if (mbar_try_wait(b, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int q = 0; q < 32; ++q)
+            if (mbar_try_wait(b, parity)) return true;
+        if (global_ns() - t0 > 1000000000ull) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+// A wait that runs out (1 s) records a code in *wait_err (1: producer, stage
+// free; 2: producer, final drain; 3, 4: consumer, stage filled) and that
+// thread stops waiting: every index stays in bounds whatever the stages
+// hold, so the launch still ends, and the host reports the error.
+__global__ void __launch_bounds__(kTmaThreads)
+    k_sweep_tma(const __grid_constant__ CUtensorMap t_oth, const __grid_constant__ CUtensorMap t_b,
+                const __grid_constant__ CUtensorMap t_ty, SLev<float> L, float* __restrict__ eown, int colour,
+                int ntx, int nty, int ntz, int* __restrict__ wait_err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    uint64_t* full = (uint64_t*)(base + kTmaStages * kTmaStage);  // stage filled (tx bytes landed)
+    uint64_t* empty = full + kTmaStages;                           // stage released by every consumer warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kTmaStages; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], kTmaRows);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const int ntiles = ntx * nty * ntz;
+    if (warp == kTmaRows) {  // producer
+        if (lane != 0) return;
+        unsigned g = 0;  // planes issued by this CTA; plane g uses stage g % kTmaStages
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int tx = tile % ntx, rest = tile / ntx, tyi = rest % nty, tz = rest / nty;
+            const int m0 = tx * kTmaTX, j0 = 1 + tyi * kTmaRows, k0 = 1 + tz * kTmaPlanes;
+            const int k1 = min(k0 + kTmaPlanes, nz - 1);
+            for (int k = k0 - 1; k <= k1; ++k, ++g) {
+                const int st = g % kTmaStages;
+                if (g >= kTmaStages && ok && !mbar_wait(&empty[st], ((g / kTmaStages) - 1) & 1)) {
+                    ok = false;
+                    atomicExch(wait_err, 1);
+                }
+                unsigned char* buf = base + st * kTmaStage;
+                mbar_arrive_expect_tx(&full[st], kTmaOBytes + kTmaBBytes + kTmaTBytes);
+                tma_load_3d(buf, &t_oth, &full[st], m0 - 4, j0 - 1, k);
+                tma_load_3d(buf + kTmaOPad, &t_b, &full[st], m0, j0, k);
+                tma_load_3d(buf + kTmaOPad + kTmaBBytes, &t_ty, &full[st], m0, j0, k);
+            }
+        }
+        // every copy has landed before the CTA may end
+        for (unsigned q = g > (unsigned)kTmaStages ? g - kTmaStages : 0; q < g && ok; ++q)
+            if (!mbar_wait(&full[q % kTmaStages], (q / kTmaStages) & 1)) {
+                ok = false;
+                atomicExch(wait_err, 2);
+            }
+        return;
+    }
+    // consumers: thread (lx, group) owns pair m0 + lx of the rows r0 .. r0 + 3
+    const int lx = threadIdx.x & (kTmaTX - 1), r0 = 4 * (threadIdx.x / kTmaTX);
+    const unsigned hs = L.hs;
+    const int hp = L.hp;
+    unsigned g = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int tx = tile % ntx, rest = tile / ntx, tyi = rest % nty, tz = rest / nty;
+        const int m = tx * kTmaTX + lx, j0 = 1 + tyi * kTmaRows + r0, k0 = 1 + tz * kTmaPlanes;
+        const int nk = min(k0 + kTmaPlanes, nz - 1) - k0;
+        // the pair's two nodes: coefficients and whether each is an interior column
+        const float4 c0 = L.cx[min(2 * m, nx - 1)], c1 = L.cx[min(2 * m + 1, nx - 1)];
+        const bool in0 = 2 * m >= 1 && 2 * m <= nx - 2, in1 = 2 * m + 1 <= nx - 2;
+        float cya[4], cyb[4], cyc[4];
+        bool jin[4];
+#pragma unroll
+        for (int ly = 0; ly < 4; ++ly) {
+            const float4 cy = L.cy[min(j0 + ly, ny - 1)];
+            cya[ly] = cy.x;
+            cyb[ly] = cy.y;
+            cyc[ly] = cy.z;
+            jin[ly] = j0 + ly <= ny - 2;
+        }
+        for (int q = 0; q < 2; ++q)
+            if (ok && !mbar_wait(&full[(g + q) % kTmaStages], ((g + q) / kTmaStages) & 1)) {
+                ok = false;
+                atomicExch(wait_err, 3);
+            }
+        for (int kk = 0; kk < nk; ++kk) {
+            const unsigned gp = g + kk;  // stage of plane k - 1
+            if (ok && !mbar_wait(&full[(gp + 2) % kTmaStages], ((gp + 2) / kTmaStages) & 1)) {
+                ok = false;
+                atomicExch(wait_err, 4);
+            }
+            const int at = (r0 + 1) * kTmaOX + lx + 4;  // the thread's first row, centre entry
+            const unsigned char* s0 = base + ((gp + 1) % kTmaStages) * kTmaStage;
+            const float* Om = (const float*)(base + (gp % kTmaStages) * kTmaStage) + at;
+            const float* O0 = (const float*)s0 + at;
+            const float* Op = (const float*)(base + ((gp + 2) % kTmaStages) * kTmaStage) + at;
+            const float* Bs = (const float*)(s0 + kTmaOPad) + r0 * kTmaTX + lx;
+            const uint8_t* Ts = s0 + kTmaOPad + kTmaBBytes + r0 * kTmaTX + lx;
+            const int k = k0 + kk;
+            const float4 cz = L.cz[k];
+            const int p0 = (colour + j0 + k) & 1;  // parity of row r0; rows alternate
+            const float4 ce = p0 ? c1 : c0, co = p0 ? c0 : c1;
+            const bool ine = p0 ? in1 : in0, ino = p0 ? in0 : in1;
+            float* ep = eown + ((unsigned)k * hs + (unsigned)(j0 * hp + m));
+#pragma unroll
+            for (int ly = 0; ly < 4; ++ly) {
+                const int par = p0 ^ (ly & 1);
+                const float4 cx = (ly & 1) ? co : ce;
+                const int o = ly * kTmaOX;
+                const float xm = O0[o - 1 + par], xp = O0[o + par], ym = O0[o - kTmaOX], yp = O0[o + kTmaOX];
+                const float zm = Om[o], zp = Op[o];
+                const float b = Bs[ly * kTmaTX];
+                const uint8_t t = Ts[ly * kTmaTX];
+                const float dg = cx.y + (cyb[ly] + cz.y);
+                float v = b;
+                v -= (cx.x * xm + cx.z * xp) + (cya[ly] * ym + cyc[ly] * yp) + (cz.x * zm + cz.z * zp);
+                if (((ly & 1) ? ino : ine) && jin[ly] && is_unknown(t)) ep[ly * hp] = times_rcp(v, dg);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[gp % kTmaStages]);
+        }
+        __syncwarp();
+        if (lane == 0) {  // the tile's last two planes
+            mbar_arrive(&empty[(g + nk) % kTmaStages]);
+            mbar_arrive(&empty[(g + nk + 1) % kTmaStages]);
+        }
+        g += nk + 2;
     }
 }
 
@@ -509,13 +722,28 @@ Transfer<float> transfer<float>(MgLevel& F) {
     return X;
 }
 
+// the TMA-fed half-sweep where it applies (FP32, MODE 0, a level with maps)
+bool sweep_tma(cfp_ctx*, int, const SLev<double>&, int, cudaStream_t) { return false; }
+bool sweep_tma(cfp_ctx* c, int l, const SLev<float>& L, int colour, cudaStream_t s) {
+    const MgLevel& M = c->mg[l];
+    if (!M.tma || !c->mg_tma) return false;
+    const int ntx = (M.n[0] / 2 + kTmaTX - 1) / kTmaTX, nty = (M.n[1] - 2 + kTmaRows - 1) / kTmaRows;
+    const int ntz = (M.n[2] - 2 + kTmaPlanes - 1) / kTmaPlanes;
+    k_sweep_tma<<<(unsigned)M.tma_grid, kTmaThreads, kTmaSmem, s>>>(M.tm32[3 * colour], M.tm32[3 * colour + 1],
+                                                                     M.tm32[3 * colour + 2], L, L.e[colour], colour,
+                                                                     ntx, nty, ntz, c->dwait);
+    return true;
+}
+
 template <class T>
 void half_sweep(cfp_ctx* c, int l, const SLev<T>& L, const Side<T>& S, int colour, int mode, const T* rho, T* phi,
                 cudaStream_t s) {
     const dim3 g = plane_grid(c->mg[l].n);
     const Half<T> H{L.ty[colour], L.e[colour], L.e[1 - colour], L.b[colour], L.b[1 - colour]};
     switch (mode) {
-        case 0: k_sweep_split<T, 0><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
+        case 0:
+            if (!sweep_tma(c, l, L, colour, s)) k_sweep_split<T, 0><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi);
+            break;
         case 1: k_sweep_split<T, 1><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
         case 2: k_sweep_split<T, 2><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
         default: k_sweep_split<T, 3><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
@@ -626,7 +854,7 @@ cfp_status build_levels(cfp_ctx* c) {
             CFP_CUDA(cudaMemcpy(L.w64, wv.data(), sizeof(double) * wv.size(), cudaMemcpyHostToDevice));
             CFP_CUDA(cudaMemcpy(L.w32, wf.data(), sizeof(float) * wf.size(), cudaMemcpyHostToDevice));
         }
-        L.hp = ((L.n[0] + 1) / 2 + 7) / 8 * 8;
+        L.hp = ((L.n[0] + 1) / 2 + 15) / 16 * 16;
         L.Nh = (int64_t)L.hp * L.n[1] * L.n[2];
         if (L.Nh >= (int64_t(1) << 31))
             return fail(CFP_EINVAL, "grid too large for the multigrid preconditioner (2^31 entries per colour)");
@@ -678,6 +906,68 @@ cfp_status build_levels(cfp_ctx* c) {
 
 }  // namespace
 
+namespace {
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (the library does not link libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// 3D map (x = entry in a row of hp, y = row, z = plane) of one colour array
+// with a box of bx x by x 1 elements; out-of-array elements read as zero
+cfp_status tile_map(CUtensorMap* m, CUtensorMapDataType dt, int esize, const void* base, const MgLevel& L, int bx,
+                    int by) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return fail(CFP_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[3] = {(cuuint64_t)L.hp, (cuuint64_t)L.n[1], (cuuint64_t)L.n[2]};
+    const cuuint64_t strides[2] = {(cuuint64_t)L.hp * esize, (cuuint64_t)L.hp * L.n[1] * esize};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(m, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(CFP_ECUDA, "cuTensorMapEncodeTiled failed for a multigrid level");
+    return CFP_OK;
+}
+
+// maps and persistent grid of the TMA half-sweep on the levels wide enough
+cfp_status setup_tma(cfp_ctx* c) {
+    static_assert(kTmaSmem <= 227 * 1024, "shared memory per CTA");
+    CFP_CUDA(cudaFuncSetAttribute(k_sweep_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem));
+    int per = 0, nsm = 0;
+    CFP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_tma, kTmaThreads, kTmaSmem));
+    CFP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+    for (MgLevel& L : c->mg) {
+        L.tma = 0;
+        if (L.n[0] / 2 < kTmaMinPairs || per < 1) continue;
+        for (int col = 0; col < 2; ++col) {
+            const float* e_oth = L.s32 + (int64_t)(1 - col) * L.Nh;
+            const float* b_own = L.s32 + (int64_t)(2 + col) * L.Nh;
+            const uint8_t* ty = L.stype + (int64_t)col * L.Nh;
+            CFP_TRY(tile_map(&L.tm32[3 * col], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, e_oth, L, kTmaOX, kTmaRows + 2));
+            CFP_TRY(tile_map(&L.tm32[3 * col + 1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b_own, L, kTmaTX, kTmaRows));
+            CFP_TRY(tile_map(&L.tm32[3 * col + 2], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, ty, L, kTmaTX, kTmaRows));
+        }
+        const int64_t tiles = (int64_t)((L.n[0] / 2 + kTmaTX - 1) / kTmaTX) * ((L.n[1] - 2 + kTmaRows - 1) / kTmaRows) *
+                              ((L.n[2] - 2 + kTmaPlanes - 1) / kTmaPlanes);
+        L.tma_grid = (int)std::min<int64_t>(tiles, (int64_t)per * nsm);
+        L.tma = 1;
+    }
+    return CFP_OK;
+}
+
+}  // namespace
+
 // Build the hierarchy if needed and the split vectors of precision `prec`
 // (0: FP64, 1: FP32), zero-filled: entries that are never written (the
 // non-unknowns, the box, the black residuals) must read as zero.
@@ -689,6 +979,7 @@ cfp_status ensure_mg(cfp_ctx* c, int prec) {
             return st;
         }
     }
+    bool fresh32 = false;
     for (MgLevel& L : c->mg) {
         const size_t n = (size_t)kSplitVecs * L.Nh;
         if (prec == 0 && !L.s64) {
@@ -698,8 +989,10 @@ cfp_status ensure_mg(cfp_ctx* c, int prec) {
         if (prec == 1 && !L.s32) {
             CFP_CUDA(cudaMalloc(&L.s32, sizeof(float) * n));
             CFP_CUDA(cudaMemsetAsync(L.s32, 0, sizeof(float) * n, c->stream));
+            fresh32 = true;
         }
     }
+    if (fresh32) CFP_TRY(setup_tma(c));
     CFP_CUDA(cudaStreamSynchronize(c->stream));
     return CFP_OK;
 }

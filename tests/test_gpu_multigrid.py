@@ -176,6 +176,56 @@ def test_vcycle_matches_definition(name, nu, post):
     ctx.close()
 
 
+# levels of >= 192 nodes per row run their FP32 half-sweeps through the
+# TMA-fed kernel: one x tile (257), a ragged second x tile with an even row
+# (300), two such levels (513, then 257); ragged y tiles and z chunks in all
+WIDE = {
+    "wide-257": lambda: W.Workload("wide-257", W.tanh_grid(-1, 1, 257, 1.1), W.uniform_grid(-1, 1, 27),
+                                   W.tanh_grid(-1, 1, 45, 0.8), [W.sphere((0.03, -0.02, 0.01), 0.4)],
+                                   W._c2_u, W._c2_f),
+    "wide-300": lambda: W.Workload("wide-300", W.uniform_grid(-1, 1, 300), W.tanh_grid(-1, 1, 21, 0.6),
+                                   W.uniform_grid(-1, 1, 70), [W.sphere((-0.05, 0.02, 0.04), 0.42)],
+                                   W._c2_u, W._c2_f),
+    "wide-513": lambda: W.Workload("wide-513", W.tanh_grid(-1, 1, 513, 1.4), W.uniform_grid(-1, 1, 18),
+                                   W.uniform_grid(-1, 1, 18), [W.sphere((0.01, 0.02, -0.03), 0.45)],
+                                   W._c2_u, W._c2_f),
+}
+
+
+@pytest.mark.parametrize("name", list(WIDE))
+def test_fp32_vcycle_tma_smoother(name):
+    """The FP32 V-cycle (the mixed solve's inner preconditioner) with the
+    TMA-fed half-sweeps: bitwise equal to the plain-load half-sweeps (same
+    arithmetic), and the numpy V-cycle in FP64 to FP32 accuracy."""
+    w = WIDE[name]()
+    P = O.Problem(w.x, w.y, w.z, w.bodies, w.fluid_inside)
+    otype = P.classify()
+    P.ibi()
+    P.assemble()
+    levels = build_levels(w.x, w.y, w.z, otype, P.export(O.MAT_K))
+    rng = np.random.default_rng(5)
+    rho = np.where(levels[0]["unk"], rng.standard_normal(w.N), 0.0)
+    want = vcycle(levels, rho, 2, post=2)
+    ctx = cfp.Context(w.x, w.y, w.z, w.bodies, w.fluid_inside)
+    ctx.classify_points()
+    rho_t = torch.as_tensor(rho, device="cuda")
+    got = {}
+    for tma in (1, 0, 1):
+        phi = torch.full((w.N,), 7.0, dtype=torch.float64, device="cuda")
+        ctx.precondition_ex(rho_t, phi, precond=cfp.PRECOND_MG, mg_smooth=2, mg_post=2,
+                            precision=cfp.PREC_MIXED, mg_tma=tma)
+        if tma in got:
+            assert torch.equal(phi, got[tma])  # repeatable
+        got[tma] = phi
+    assert torch.equal(got[1], got[0])
+    g = got[1].cpu().numpy()
+    u = levels[0]["unk"]
+    assert np.all(g[~u] == 0.0)
+    err = np.max(np.abs(g[u] - want[u])) / np.max(np.abs(want[u]))
+    assert err <= 1e-5, err
+    ctx.close()
+
+
 def test_kernel_timer_covers_every_kernel():
     w = W.config2(33)
     ctx = cfp.Context(w.x, w.y, w.z, w.bodies)
