@@ -51,8 +51,8 @@ def parse():
                          "residual of only 1e-14 .. 2e-13 in FP64, the oracle's included)")
     ap.add_argument("--sweeps", type=int, default=8)
     ap.add_argument("--precond", default="mg", choices=["mg", "rbgs"])
-    ap.add_argument("--mg-smooth", type=int, default=3)
-    ap.add_argument("--mg-post", type=int, default=0, help="post-smoothing sweeps (0: as --mg-smooth)")
+    ap.add_argument("--mg-smooth", type=int, default=4)
+    ap.add_argument("--mg-post", type=int, default=3, help="post-smoothing sweeps (0: as --mg-smooth)")
     ap.add_argument("--no-graph", action="store_true",
                     help="plain launches instead of the CUDA graph (ncu cannot profile kernel nodes of graphs "
                          "with conditional nodes)")
