@@ -53,13 +53,13 @@ __device__ void sum_partials(const double* partial, int nb, double& a, double& b
 #define GRID_STRIDE(l, N) \
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < (N); l += (int64_t)gridDim.x * blockDim.x)
 
-// r = b - v, r_hat0 = r, p = r; partial (r, r)
+// r = b - v (v = B x; NULL for x = 0: r = b), r_hat0 = r, p = r; partial (r, r)
 template <class T>
 __global__ void k_init_r(const T* __restrict__ b, const T* __restrict__ v, T* __restrict__ r, T* __restrict__ rh,
                          T* __restrict__ p, double* __restrict__ partial, int64_t N) {
     DotAcc<T> aa;
     GRID_STRIDE(l, N) {
-        const T x = b[l] - v[l];
+        const T x = v ? b[l] - v[l] : b[l];
         r[l] = x;
         rh[l] = x;
         p[l] = x;
@@ -321,10 +321,11 @@ cfp_status build_graph(cfp_ctx* c, int prec, int sweeps) {
 }
 
 // Solve B x = b (b and x zero off the unknowns) until ||r||^2 <= stop2 or
-// maxit iterations; x holds the initial guess.  Returns the final flag.
+// maxit iterations; x holds the initial guess (x_zero: the caller knows it is
+// zero, so r0 = b without applying B).  Returns the final flag.
 template <class T>
 cfp_status run_bicgstab(cfp_ctx* c, int prec, const T* b, double stop2, int maxit, int sweeps, bool use_graph,
-                        int* flag, int* used, double* rr) {
+                        bool x_zero, int* flag, int* used, double* rr) {
     Vecs<T> V = vecs<T>(c);
     KState* st = c->kst + prec;
     KState* hs = c->hkst + prec;
@@ -333,8 +334,8 @@ cfp_status run_bicgstab(cfp_ctx* c, int prec, const T* b, double stop2, int maxi
     hs->stop2 = stop2;
     hs->maxit = std::max(1, maxit);
     CFP_CUDA(cudaMemcpyAsync(st, hs, sizeof(KState), cudaMemcpyHostToDevice, c->stream));
-    launch_apply<T>(c, V.x, V.v, nullptr, 0, nullptr, c->stream, nullptr);
-    k_init_r<T><<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(b, V.v, V.r, V.rh, V.p, c->partial, N);
+    if (!x_zero) launch_apply<T>(c, V.x, V.v, nullptr, 0, nullptr, c->stream, nullptr);
+    k_init_r<T><<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(b, x_zero ? nullptr : V.v, V.r, V.rh, V.p, c->partial, N);
     k_fin_init<<<1, 256, 0, c->stream>>>(st, c->partial, kUpdBlocks);
     c->launches += 2;
     CFP_CUDA(cudaGetLastError());
@@ -527,8 +528,10 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
     cfp_status st = cfp_assemble_rhs(c, f, g, gi, rhs);
     if (st) return st;
     launch_mask_unknowns(c, u, X, c->stream);
-    double b2 = 0.0;
+    double b2 = 0.0, x2 = 0.0;
     CFP_TRY(dot_host(c, rhs, rhs, &b2));
+    CFP_TRY(dot_host(c, X, X, &x2));
+    bool x_zero = x2 == 0.0;  // a zero initial guess: the first residual is rhs
     const auto t2 = clk::now();
     int total = 0, restarts = 0, refinements = 0;
     double rel = 0.0;
@@ -543,7 +546,8 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
             int flag = 0, used = 0;
             double rr = 0.0;
             CFP_TRY(run_bicgstab<double>(c, 0, rhs, tol * tol * b2, opts.maxit - total, opts.sweeps,
-                                         opts.use_graph != 0, &flag, &used, &rr));
+                                         opts.use_graph != 0, x_zero, &flag, &used, &rr));
+            x_zero = false;
             total += used;
             double r2 = 0.0;
             CFP_TRY(true_residual(c, rhs, X, tmp, &r2));
@@ -559,28 +563,33 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
         // FP32 correction solve, FP64 update.
         float* b32 = c->v32 + kNV32 * N;
         float* e32 = c->v32;  // the x vector of the FP32 run
-        double r2 = 0.0;
-        CFP_TRY(true_residual(c, rhs, X, tmp, &r2));
+        double r2 = b2;
+        const double* res = rhs;  // the current residual
+        if (!x_zero) {
+            CFP_TRY(true_residual(c, rhs, X, tmp, &r2));
+            res = tmp;
+        }
         rel = sqrt(r2 / b2);
         double prev = INFINITY;
         int stall = 0;
         while (rel > tol && isfinite(rel)) {
             if (refinements >= opts.max_refine || total >= opts.maxit) { status = CFP_ENOCONV; break; }
             const double scale = 1.0 / sqrt(r2);
-            k_to32<<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(tmp, b32, scale, N);
+            k_to32<<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(res, b32, scale, N);
             k_zero<float><<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(e32, N);
             c->launches += 2;
             int flag = 0, used = 0;
             double rr = 0.0;
             const double it2 = opts.inner_tol * opts.inner_tol;
-            CFP_TRY(run_bicgstab<float>(c, 1, b32, it2, opts.maxit - total, opts.sweeps, opts.use_graph != 0, &flag,
-                                        &used, &rr));
+            CFP_TRY(run_bicgstab<float>(c, 1, b32, it2, opts.maxit - total, opts.sweeps, opts.use_graph != 0, true,
+                                        &flag, &used, &rr));
             total += used;
             ++refinements;
             if (flag == FLAG_NAN) { status = CFP_ENAN; break; }
             k_add32<<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(X, e32, 1.0 / scale, N);
             c->launches += 1;
             CFP_TRY(true_residual(c, rhs, X, tmp, &r2));
+            res = tmp;
             rel = sqrt(r2 / b2);
             if (!(rel < 0.9 * prev)) {
                 if (++stall > opts.max_restarts) { status = status_of(flag); break; }

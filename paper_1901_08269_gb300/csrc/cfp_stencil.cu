@@ -114,12 +114,13 @@ __global__ void __launch_bounds__(kAX, sizeof(T) == 4 ? 8 : 1)
     const int k1 = min(k0 + kApplyKC, nz - 1);
     const bool iin = i <= nx - 2;
     const int ic = iin ? i : 1;  // clamped: every load stays inside the grid
-    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    // node offsets fit in 32 bits: contexts hold fewer than 2^31 nodes
+    const unsigned sy = (unsigned)nx, sz = (unsigned)nx * (unsigned)ny;
     const T ax = G.ax[0].a[ic], cx = G.ax[0].c[ic];
     const T arx = G.ax[0].ar[ic], brx = G.ax[0].br[ic], crx = G.ax[0].cr[ic];
     T ay[TY], cy[TY], ary[TY], bry[TY], cry[TY];
     bool jin[TY];
-    int64_t lout0[TY];
+    unsigned lout0[TY];
 #pragma unroll
     for (int t = 0; t < TY; ++t) {
         jin[t] = j0 + t <= ny - 2;
@@ -129,12 +130,12 @@ __global__ void __launch_bounds__(kAX, sizeof(T) == 4 ? 8 : 1)
         ary[t] = G.ax[1].ar[jc];
         bry[t] = G.ax[1].br[jc];
         cry[t] = G.ax[1].cr[jc];
-        lout0[t] = (int64_t)k0 * sz + (int64_t)jc * sy + ic;
+        lout0[t] = (unsigned)k0 * sz + (unsigned)jc * sy + (unsigned)ic;
     }
-    int64_t roff[R];
+    unsigned roff[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) roff[r] = (int64_t)min(j0 - 1 + r, ny - 1) * sy;
-    const T* p = x + (int64_t)(k0 - 1) * sz + ic;
+    for (int r = 0; r < R; ++r) roff[r] = (unsigned)min(j0 - 1 + r, ny - 1) * sy;
+    const T* p = x + ((unsigned)(k0 - 1) * sz + (unsigned)ic);
     T n[3 * R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(kAX, sizeof(T) == 4 ? 8 : 1)
         if (kk >= k0 + 1 && kk < k1) {
 #pragma unroll
             for (int t = 0; t < TY; ++t) {
-                const int64_t ln = lout0[t] + (int64_t)(kk - k0) * sz;
+                const unsigned ln = lout0[t] + (unsigned)(kk - k0) * sz;
                 t_next[t] = type[ln];
                 if (DOT) d_next[t] = d0[ln];
             }
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kAX, sizeof(T) == 4 ? 8 : 1)
             for (int t = 0; t < TY; ++t) {
                 if (!jin[t]) continue;
                 T v = az * Pm[t] + P0[t] + cz * Pp[t] + (arz * Qm[t] + brz * Q0[t] + crz * Qp[t]);
-                const int64_t l = (int64_t)k * sz + (int64_t)(j0 + t) * sy + i;
+                const unsigned l = (unsigned)k * sz + (unsigned)(j0 + t) * sy + (unsigned)i;
                 if (t_cur[t] == CFP_SOLID) v = 0;  // irregular rows: k_apply_corr adds their corrections
                 y[l] = v;
                 if (DOT >= 1) dacc0.add(d_cur[t], v);
