@@ -105,7 +105,7 @@ def test_full_size_mixed_multigrid_solve_reaches_fp64_error(full):
     for name, prec in (("fp64", cfp.PREC_FP64), ("mixed", cfp.PREC_MIXED)):
         u = torch.zeros(w.N, dtype=torch.float64, device="cuda")
         info = ctx.solve(f, g, gi, u, tol=1e-15, precision=prec, precond=cfp.PRECOND_MG, mg_smooth=4,
-                         mg_post=3, inner_tol=1e-3)
+                         mg_post=3, inner_tol=2e-3)
         assert info.status == 0 and info.rel_residual <= 1e-15, (name, info.as_dict())
         errs[name] = float((u - ue)[fluid].abs().max())
     # fourth-order scheme at 513^3 on this geometry: E* of a few 1e-9
