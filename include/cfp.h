@@ -345,6 +345,18 @@ enum { CFP_KERNEL_APPLY = 0,    /* B x with the fused (r_hat0, v) dot, as in
 cfp_status cfp_time_kernel(cfp_ctx* ctx, int kernel, int precision, int reps,
                            double* ms_per_launch, double* bytes_per_launch);
 
+/*
+ * Diagnostic of the bounded waits of the TMA-fed smoother: launches one CTA
+ * that waits on an mbarrier phase that nothing completes, with the same
+ * one-second bound as the smoother's pipeline waits.  The wait gives up,
+ * records code 5 in the context's wait word, and the call returns CFP_ECUDA
+ * after about one second (cfp_last_error names the code), the status a
+ * timed-out wait gives any call; no kernel is left running and the context
+ * stays usable.  Synchronises.  Errors: CFP_EINVAL (NULL context),
+ * CFP_ECUDA (the expected outcome).
+ */
+cfp_status cfp_diag_bounded_wait(cfp_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,7 +52,7 @@ _D = C.POINTER(C.c_double)
 EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_destroy", "cfp_classify_points",
            "cfp_ibi_points", "cfp_assemble_rhs", "cfp_apply", "cfp_precondition", "cfp_solve", "cfp_solve_host",
            "cfp_time_kernel", "cfp_launch_count", "cfp_assemble_rhs_noalloc", "cfp_precondition_ex",
-           "cfp_solve_batch", "cfp_autotune"]
+           "cfp_solve_batch", "cfp_autotune", "cfp_diag_bounded_wait"]
 KERNEL_APPLY, KERNEL_RBGS, KERNEL_UPDATE, KERNEL_MG_SWEEP = 0, 1, 2, 3
 
 
@@ -88,6 +88,7 @@ def lib(build_if_missing=True):
         L.cfp_autotune.argtypes = [_P, _P, _P, _P, _P, C.c_double, C.POINTER(Opts), _D]
         L.cfp_launch_count.argtypes = [_P]
         L.cfp_launch_count.restype = C.c_int64
+        L.cfp_diag_bounded_wait.argtypes = [_P]
         for name in EXPORTS[2:]:
             if name not in ("cfp_ctx_destroy", "cfp_launch_count"):
                 getattr(L, name).restype = C.c_int
@@ -172,6 +173,12 @@ class Context:
         _check(st, "cfp_ctx_create")
         self._h = h
         self.n_irregular = self.n_ibi = None
+
+    def diag_bounded_wait(self):
+        """(status, message) of cfp_diag_bounded_wait: CFP_ECUDA after about one
+        second when the wait bound holds."""
+        st = lib().cfp_diag_bounded_wait(self._h)
+        return st, last_error()
 
     def close(self):
         if getattr(self, "_h", None):

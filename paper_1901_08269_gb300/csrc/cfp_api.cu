@@ -337,4 +337,9 @@ cfp_status cfp_time_kernel(cfp_ctx* c, int kernel, int precision, int reps, doub
     return time_kernel(c, kernel, precision, reps, ms, bytes);
 }
 
+cfp_status cfp_diag_bounded_wait(cfp_ctx* c) {
+    if (!c) return fail(CFP_EINVAL, "null context");
+    return diag_bounded_wait(c);
+}
+
 }  // extern "C"

@@ -300,5 +300,7 @@ int mg_key(const cfp_ctx* c);
 // CFP_ECUDA (and the device word cleared) if a bounded pipeline wait of a
 // kernel timed out since the last check; synchronises the stream
 cfp_status check_waits(cfp_ctx* c);
+// one CTA whose bounded mbarrier wait runs out (code 5), then check_waits
+cfp_status diag_bounded_wait(cfp_ctx* c);
 
 }  // namespace cfp

@@ -402,6 +402,19 @@ __global__ void __launch_bounds__(kTmaThreads)
     }
 }
 
+// The bounded wait on its own: one thread waits on the first phase of a
+// barrier that expects one arrival that never comes; mbar_wait gives up after
+// one second and the kernel records code 5.  No copy is in flight.
+__global__ void k_wait_diag(int* __restrict__ wait_err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0)) atomicExch(wait_err, 5);
+}
+
 // The half-sweep's update at the fine level's irregular nodes of colour
 // `colour`, with their Shortley-Weller rows (Eq. A7_mod); one thread per
 // irregular point.  Runs right after k_sweep_split of the same colour and
@@ -1046,6 +1059,13 @@ template <class T>
 void launch_mg_half_sweep(cfp_ctx* c, cudaStream_t s) {
     const SLev<T> L = slev<T>(c, 0);
     half_sweep<T>(c, 0, L, side_view<T>(c), 0, 0, (const T*)nullptr, (T*)nullptr, s);
+}
+
+cfp_status diag_bounded_wait(cfp_ctx* c) {
+    k_wait_diag<<<1, 32, 0, c->stream>>>(c->dwait);
+    c->launches += 1;
+    CFP_CUDA(cudaGetLastError());
+    return check_waits(c);
 }
 
 template void launch_precond_mg<double>(cfp_ctx*, const double*, double*, cudaStream_t);

@@ -239,3 +239,25 @@ def test_kernel_timer_covers_every_kernel():
     with pytest.raises(cfp.CfpError):
         ctx.time_kernel(4, cfp.PREC_FP64, reps=1)
     ctx.close()
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """The pipeline waits of the TMA-fed smoother are bounded: a wait on an
+    mbarrier phase that nothing completes gives up after one second, the call
+    reports CFP_ECUDA with the recorded code, the wait word is cleared, and
+    the same context then solves normally."""
+    import time
+    w = W.config2(33)
+    ctx = cfp.Context(w.x, w.y, w.z, w.bodies)
+    ctx.classify_points()
+    t0 = time.perf_counter()
+    st, msg = ctx.diag_bounded_wait()
+    dt = time.perf_counter() - t0
+    assert st == cfp.ECUDA and "code 5" in msg, (st, msg)
+    assert 0.9 <= dt < 30.0, dt
+    f, g = w.fields(torch, "cuda")
+    gi = w.g_at(ctx.ibi_points(), torch)
+    u = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+    info = ctx.solve(f, g, gi, u, tol=1e-10, precision=cfp.PREC_MIXED, precond=cfp.PRECOND_MG)
+    assert info.status == 0 and info.rel_residual <= 1e-10
+    ctx.close()
