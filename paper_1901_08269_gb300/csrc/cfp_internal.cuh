@@ -136,10 +136,16 @@ struct MgLevel {
     float* s32 = nullptr;      // the same in FP32
     void* pk64 = nullptr;      // packed (ka, kb, kc, 0) per index, x then y then z, FP64
     void* pk32 = nullptr;      // the same in FP32
-    int* ilo[3] = {nullptr, nullptr, nullptr};  // interpolation from the next coarser level
+    // transfers with the next coarser level, FP64 and FP32 copies: per fine
+    // index of each axis (entries from off[d]) the packed interpolation
+    // (wlo, whi, ilo), per coarse index of each axis (entries from coff[d])
+    // the restriction weights of fine nodes 2I - 1, 2I, 2I + 1
     int64_t off[3] = {0, 0, 0};
-    double* w64 = nullptr;
-    float* w32 = nullptr;
+    int64_t coff[3] = {0, 0, 0};
+    void* ip64 = nullptr;
+    void* ip32 = nullptr;
+    void* rw64 = nullptr;
+    void* rw32 = nullptr;
     // TMA-fed FP32 half-sweep (levels with at least kTmaMinPairs pairs per
     // row): per colour c, maps of the other colour's e, of b and of the type
     // at tm32[3 c + 0 .. 2]; grid = persistent CTAs (resident CTAs x SMs)

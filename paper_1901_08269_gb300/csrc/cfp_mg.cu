@@ -46,16 +46,31 @@ namespace {
 
 constexpr int kSplitThreads = 128;
 
+// per fine index of an axis: fine node i = wlo * coarse[ilo] + whi * coarse[ilo + 1],
+// one wide load
 template <class T>
-struct Interp {  // per axis: fine node i = wlo * coarse[ilo] + whi * coarse[ilo + 1]
-    const int* ilo;
-    const T* wlo;
-    const T* whi;
+struct IpPk;
+template <>
+struct __align__(16) IpPk<float> {
+    float wlo, whi;
+    int ilo, pad;
+};
+template <>
+struct __align__(32) IpPk<double> {
+    double wlo, whi;
+    int ilo, pad[3];
+};
+// per coarse index I of an axis: the interpolation weights of fine nodes
+// 2I - 1, 2I, 2I + 1 to coarse node I (the rows of P^T)
+template <class T>
+struct __align__(4 * sizeof(T)) RwPk {
+    T w[4];
 };
 
 template <class T>
 struct Transfer {
-    Interp<T> ax[3];
+    const IpPk<T>* ip[3];
+    const RwPk<T>* rw[3];
 };
 
 // (ka, kb, kc) of one index of one axis, packed for a single wide load
@@ -500,12 +515,6 @@ __global__ void k_resid_fix(SLev<T> L, Side<T> S, const int32_t* __restrict__ ir
     }
 }
 
-template <class T>
-__device__ __forceinline__ T weight_to(const Interp<T>& A, int i, int I) {
-    const int lo = A.ilo[i];
-    return (lo == I ? A.wlo[i] : T(0)) + (lo + 1 == I ? A.whi[i] : T(0));
-}
-
 // b_c = (P^T r_f) / (P^T 1) at the coarse unknowns; r_f is the fine red
 // residual (zero on black nodes).  One thread per coarse node (I, J, K);
 // interior coarse nodes sit on fine node (2I, 2J, 2K).
@@ -520,12 +529,10 @@ __global__ void k_restrict_split(Transfer<T> X, SLev<T> F, SLev<T> C) {
     if (!is_unknown((cc ? C.ty[1] : C.ty[0])[oc])) return;
     const int nfy = F.ny;
     const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
-    T wx[3], wy[3], wz[3];
-    for (int q = 0; q < 3; ++q) {
-        wx[q] = weight_to(X.ax[0], fi - 1 + q, I);
-        wy[q] = weight_to(X.ax[1], fj - 1 + q, J);
-        wz[q] = weight_to(X.ax[2], fk - 1 + q, K);
-    }
+    const RwPk<T> rx = X.rw[0][I], ry = X.rw[1][J], rz = X.rw[2][K];
+    const T* wx = rx.w;
+    const T* wy = ry.w;
+    const T* wz = rz.w;
     const T* __restrict__ r0 = F.r0;
     T s = 0, w = 0;
     for (int c = 0; c < 3; ++c) {
@@ -554,8 +561,9 @@ __global__ void __launch_bounds__(kSplitThreads) k_prolong_split(Transfer<T> X, 
     const int j = 1 + blockIdx.y, k0 = 1 + kSweepPlanes * blockIdx.z;
     if (2 * m > nx - 2) return;
     const unsigned hc = (unsigned)C.hp;
-    const int J = X.ax[1].ilo[j];
-    const T ay0 = X.ax[1].wlo[j], ay1 = X.ax[1].whi[j];
+    const IpPk<T> py = X.ip[1][j];
+    const int J = py.ilo;
+    const T ay0 = py.wlo, ay1 = py.whi;
     T* __restrict__ e1 = F.e[1];
     T val[kSweepPlanes];
     bool live[kSweepPlanes];
@@ -568,9 +576,10 @@ __global__ void __launch_bounds__(kSplitThreads) k_prolong_split(Transfer<T> X, 
         const int ic = i <= nx - 2 ? i : nx - 2;  // every load stays inside the tables and the level
         const unsigned o = (unsigned)k * F.hs + (unsigned)(j * F.hp + m);
         const uint8_t t = F.ty[1][o];
-        const int I = X.ax[0].ilo[ic], K = X.ax[2].ilo[k];
-        const T ax0 = X.ax[0].wlo[ic], ax1 = X.ax[0].whi[ic];
-        const T az0 = X.ax[2].wlo[k], az1 = X.ax[2].whi[k];
+        const IpPk<T> px = X.ip[0][ic], pz = X.ip[2][k];
+        const int I = px.ilo, K = pz.ilo;
+        const T ax0 = px.wlo, ax1 = px.whi;
+        const T az0 = pz.wlo, az1 = pz.whi;
         // coarse (I + a, J + b, K + c): colour (I + a + J + b + K + c) & 1,
         // entry ((K + c) * ncy + J + b) * hc + (I + a) >> 1
         const int p = (I + J + K) & 1;
@@ -725,13 +734,19 @@ Transfer<T> transfer(MgLevel& F);
 template <>
 Transfer<double> transfer<double>(MgLevel& F) {
     Transfer<double> X;
-    for (int d = 0; d < 3; ++d) X.ax[d] = Interp<double>{F.ilo[d], F.w64 + 2 * F.off[d], F.w64 + 2 * F.off[d] + F.n[d]};
+    for (int d = 0; d < 3; ++d) {
+        X.ip[d] = static_cast<const IpPk<double>*>(F.ip64) + F.off[d];
+        X.rw[d] = static_cast<const RwPk<double>*>(F.rw64) + F.coff[d];
+    }
     return X;
 }
 template <>
 Transfer<float> transfer<float>(MgLevel& F) {
     Transfer<float> X;
-    for (int d = 0; d < 3; ++d) X.ax[d] = Interp<float>{F.ilo[d], F.w32 + 2 * F.off[d], F.w32 + 2 * F.off[d] + F.n[d]};
+    for (int d = 0; d < 3; ++d) {
+        X.ip[d] = static_cast<const IpPk<float>*>(F.ip32) + F.off[d];
+        X.rw[d] = static_cast<const RwPk<float>*>(F.rw32) + F.coff[d];
+    }
     return X;
 }
 
@@ -791,7 +806,7 @@ void smooth(cfp_ctx* c, int l, const Side<T>& S, int sweeps, int first_red, int 
 void free_mg(cfp_ctx* c) {
     for (MgLevel& L : c->mg) {
         void* ptrs[] = {L.coef64, L.coef32, L.type, L.stype, L.s64, L.s32, L.pk64, L.pk32,
-                        L.ilo[0], L.ilo[1], L.ilo[2], L.w64, L.w32};
+                        L.ip64, L.ip32, L.rw64, L.rw32};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     }
@@ -831,12 +846,17 @@ cfp_status build_levels(cfp_ctx* c) {
         // interpolation tables from level l + 1 (per fine index of level l)
         if (l + 1 < nl) {
             const MgLevel& Cn = c->mg[l + 1];
-            int64_t tot = 0;
+            int64_t tot = 0, ctot = 0;
             for (int d = 0; d < 3; ++d) {
                 L.off[d] = tot;
                 tot += L.n[d];
+                L.coff[d] = ctot;
+                ctot += Cn.n[d];
             }
-            std::vector<double> wv(2 * tot);
+            std::vector<IpPk<double>> ipd(tot);
+            std::vector<IpPk<float>> ipf(tot);
+            std::vector<RwPk<double>> rwd(ctot);
+            std::vector<RwPk<float>> rwf(ctot);
             for (int d = 0; d < 3; ++d) {
                 const int n = L.n[d], nc = Cn.n[d];
                 std::vector<int> lo(n);
@@ -854,18 +874,34 @@ cfp_status build_levels(cfp_ctx* c) {
                         wh = (xi - xa) / (xb - xa);
                     }
                     lo[i] = I;
-                    wv[2 * L.off[d] + i] = wl;
-                    wv[2 * L.off[d] + n + i] = wh;
+                    ipd[L.off[d] + i] = IpPk<double>{wl, wh, I, {0, 0, 0}};
+                    ipf[L.off[d] + i] = IpPk<float>{(float)wl, (float)wh, I, 0};
                 }
-                CFP_CUDA(cudaMalloc(&L.ilo[d], sizeof(int) * n));
-                CFP_CUDA(cudaMemcpy(L.ilo[d], lo.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+                // weight of fine node i to coarse node I: the interpolation
+                // weight that names I (at most one of the two does), else 0
+                for (int I = 0; I < nc; ++I)
+                    for (int q = 0; q < 4; ++q) {
+                        const int i = 2 * I - 1 + q;
+                        double wd = 0.0;
+                        float wfl = 0.f;
+                        if (q < 3 && i >= 0 && i < n) {
+                            const IpPk<double>& a = ipd[L.off[d] + i];
+                            const IpPk<float>& b = ipf[L.off[d] + i];
+                            wd = (a.ilo == I ? a.wlo : 0.0) + (a.ilo + 1 == I ? a.whi : 0.0);
+                            wfl = (b.ilo == I ? b.wlo : 0.f) + (b.ilo + 1 == I ? b.whi : 0.f);
+                        }
+                        rwd[L.coff[d] + I].w[q] = wd;
+                        rwf[L.coff[d] + I].w[q] = wfl;
+                    }
             }
-            // layout per axis d: [wlo (n_d) | whi (n_d)] starting at 2 * off[d]
-            std::vector<float> wf(wv.begin(), wv.end());
-            CFP_CUDA(cudaMalloc(&L.w64, sizeof(double) * wv.size()));
-            CFP_CUDA(cudaMalloc(&L.w32, sizeof(float) * wf.size()));
-            CFP_CUDA(cudaMemcpy(L.w64, wv.data(), sizeof(double) * wv.size(), cudaMemcpyHostToDevice));
-            CFP_CUDA(cudaMemcpy(L.w32, wf.data(), sizeof(float) * wf.size(), cudaMemcpyHostToDevice));
+            CFP_CUDA(cudaMalloc(&L.ip64, sizeof(IpPk<double>) * tot));
+            CFP_CUDA(cudaMalloc(&L.ip32, sizeof(IpPk<float>) * tot));
+            CFP_CUDA(cudaMalloc(&L.rw64, sizeof(RwPk<double>) * ctot));
+            CFP_CUDA(cudaMalloc(&L.rw32, sizeof(RwPk<float>) * ctot));
+            CFP_CUDA(cudaMemcpy(L.ip64, ipd.data(), sizeof(IpPk<double>) * tot, cudaMemcpyHostToDevice));
+            CFP_CUDA(cudaMemcpy(L.ip32, ipf.data(), sizeof(IpPk<float>) * tot, cudaMemcpyHostToDevice));
+            CFP_CUDA(cudaMemcpy(L.rw64, rwd.data(), sizeof(RwPk<double>) * ctot, cudaMemcpyHostToDevice));
+            CFP_CUDA(cudaMemcpy(L.rw32, rwf.data(), sizeof(RwPk<float>) * ctot, cudaMemcpyHostToDevice));
         }
         L.hp = ((L.n[0] + 1) / 2 + 15) / 16 * 16;
         L.Nh = (int64_t)L.hp * L.n[1] * L.n[2];
