@@ -146,12 +146,14 @@ struct MgLevel {
     void* ip32 = nullptr;
     void* rw64 = nullptr;
     void* rw32 = nullptr;
-    // TMA-fed FP32 half-sweep (levels with at least kTmaMinPairs pairs per
-    // row): per colour c, maps of the other colour's e, of b and of the type
-    // at tm32[3 c + 0 .. 2]; grid = persistent CTAs (resident CTAs x SMs)
+    // TMA-fed FP32 passes (levels with at least kTmaMinPairs pairs per row):
+    // per colour c, maps of the other colour's e, of b and of the type at
+    // tm32[3 c + 0 .. 2], the red e at tm32[6]; per pass kind (half-sweep,
+    // red residual, last black half-sweep) the persistent grid (resident
+    // CTAs x SMs)
     int tma = 0;
-    int tma_grid = 0;
-    CUtensorMap tm32[6];
+    int tma_grid[3] = {0, 0, 0};
+    CUtensorMap tm32[7];
 };
 
 }  // namespace cfp

@@ -217,7 +217,13 @@ __global__ void __launch_bounds__(kSplitThreads)
 }
 
 // ---------------------------------------------------------------- TMA path
-// The FP32 plain half-sweep (MODE 0) of a large level as a pipeline: per CTA
+// Three FP32 passes of a large level with the access pattern of a half-sweep
+// (a node of one colour reads its six neighbours of the other colour, its b
+// and its type), run as a pipeline.  KIND 0: the plain half-sweep (MODE 0)
+// into e of its colour; KIND 1: the red residual r0 = b0 - K e (k_resid_split;
+// the stage also holds the red e of the tile); KIND 2: the fine level's last
+// black half-sweep into the natural-layout phi, both nodes of each pair
+// (MODE 3).  Per CTA
 // one producer thread streams planes of a tile through a ring of shared-memory
 // stages with cp.async.bulk.tensor (completion counted on an mbarrier per
 // stage), and kTmaRows consumer warps update the tile's nodes from shared
@@ -236,17 +242,24 @@ __global__ void __launch_bounds__(kSplitThreads)
 constexpr int kTmaTX = 128;     // pairs per tile row: one consumer thread each
 constexpr int kTmaRows = 8;     // rows per tile: consumer warps 0-3 take rows 0-3, warps 4-7 rows 4-7
 constexpr int kTmaPlanes = 32;  // output planes per tile
-constexpr int kTmaStages = 6;   // planes in the shared-memory ring
 constexpr int kTmaMinPairs = 96;  // levels with fewer pairs per row use k_sweep_split
 constexpr int kTmaOX = kTmaTX + 8;                                   // other-colour row in a stage
 constexpr int kTmaOBytes = kTmaOX * (kTmaRows + 2) * 4;              // other-colour tile
 constexpr int kTmaOPad = (kTmaOBytes + 127) / 128 * 128;
 constexpr int kTmaBBytes = kTmaTX * kTmaRows * 4;                    // b of the tile
 constexpr int kTmaTBytes = kTmaTX * kTmaRows;                        // type of the tile
-constexpr int kTmaStage = kTmaOPad + kTmaBBytes + kTmaTBytes;
 constexpr int kTmaThreads = 32 * (kTmaRows + 1);                     // + the producer warp
-constexpr int kTmaSmem = kTmaStages * kTmaStage + 2 * kTmaStages * 8 + 128;  // + barriers, alignment
-static_assert(kTmaStage % 128 == 0 && kTmaBBytes % 128 == 0, "stage buffers stay 128-byte aligned");
+// a stage: [other colour with halo | b | type | (KIND 1) own e]; KIND 1 has
+// a larger stage and one stage fewer, so three CTAs still fit an SM
+__host__ __device__ constexpr int tma_stage(int kind) {
+    return kTmaOPad + kTmaBBytes + kTmaTBytes + (kind == 1 ? kTmaBBytes : 0);
+}
+__host__ __device__ constexpr int tma_stages(int kind) { return kind == 1 ? 5 : 6; }
+__host__ __device__ constexpr int tma_smem(int kind) {
+    return tma_stages(kind) * tma_stage(kind) + 2 * tma_stages(kind) * 8 + 128;  // + barriers, alignment
+}
+static_assert(tma_stage(0) % 128 == 0 && tma_stage(1) % 128 == 0 && kTmaBBytes % 128 == 0,
+              "stage buffers stay 128-byte aligned");
 static_assert(kTmaRows % 4 == 0, "rows come in groups of four per 128 consumer threads");
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -295,10 +308,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
 // free; 2: producer, final drain; 3, 4: consumer, stage filled) and that
 // thread stops waiting: every index stays in bounds whatever the stages
 // hold, so the launch still ends, and the host reports the error.
+// out: e of `colour` (KIND 0), r0 (KIND 1, colour 0), phi (KIND 2, colour 1).
+template <int KIND>
 __global__ void __launch_bounds__(kTmaThreads)
     k_sweep_tma(const __grid_constant__ CUtensorMap t_oth, const __grid_constant__ CUtensorMap t_b,
-                const __grid_constant__ CUtensorMap t_ty, SLev<float> L, float* __restrict__ eown, int colour,
-                int ntx, int nty, int ntz, int* __restrict__ wait_err) {
+                const __grid_constant__ CUtensorMap t_ty, const __grid_constant__ CUtensorMap t_own, SLev<float> L,
+                float* __restrict__ out, int colour, int ntx, int nty, int ntz, int* __restrict__ wait_err) {
+    constexpr int kTmaStages = tma_stages(KIND), kTmaStage = tma_stage(KIND);
+    constexpr int kEOff = kTmaOPad + kTmaBBytes + kTmaTBytes;  // KIND 1: own e of the tile
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     uint64_t* full = (uint64_t*)(base + kTmaStages * kTmaStage);  // stage filled (tx bytes landed)
@@ -330,10 +347,11 @@ __global__ void __launch_bounds__(kTmaThreads)
                     atomicExch(wait_err, 1);
                 }
                 unsigned char* buf = base + st * kTmaStage;
-                mbar_arrive_expect_tx(&full[st], kTmaOBytes + kTmaBBytes + kTmaTBytes);
+                mbar_arrive_expect_tx(&full[st], kTmaOBytes + kTmaBBytes + kTmaTBytes + (KIND == 1 ? kTmaBBytes : 0));
                 tma_load_3d(buf, &t_oth, &full[st], m0 - 4, j0 - 1, k);
                 tma_load_3d(buf + kTmaOPad, &t_b, &full[st], m0, j0, k);
                 tma_load_3d(buf + kTmaOPad + kTmaBBytes, &t_ty, &full[st], m0, j0, k);
+                if (KIND == 1) tma_load_3d(buf + kEOff, &t_own, &full[st], m0, j0, k);
             }
         }
         // every copy has landed before the CTA may end
@@ -385,12 +403,15 @@ __global__ void __launch_bounds__(kTmaThreads)
             const float* Op = (const float*)(base + ((gp + 2) % kTmaStages) * kTmaStage) + at;
             const float* Bs = (const float*)(s0 + kTmaOPad) + r0 * kTmaTX + lx;
             const uint8_t* Ts = s0 + kTmaOPad + kTmaBBytes + r0 * kTmaTX + lx;
+            const float* Es = (const float*)(s0 + kEOff) + r0 * kTmaTX + lx;  // KIND 1 only
             const int k = k0 + kk;
             const float4 cz = L.cz[k];
             const int p0 = (colour + j0 + k) & 1;  // parity of row r0; rows alternate
             const float4 ce = p0 ? c1 : c0, co = p0 ? c0 : c1;
             const bool ine = p0 ? in1 : in0, ino = p0 ? in0 : in1;
-            float* ep = eown + ((unsigned)k * hs + (unsigned)(j0 * hp + m));
+            float* ep = out + ((unsigned)k * hs + (unsigned)(j0 * hp + m));  // KIND 0, 1
+            // KIND 2: natural-layout row of (j0, k) and the pair's first node
+            float* pp = out + ((unsigned)k * (unsigned)ny + (unsigned)j0) * (unsigned)nx + 2u * (unsigned)m;
 #pragma unroll
             for (int ly = 0; ly < 4; ++ly) {
                 const int par = p0 ^ (ly & 1);
@@ -401,9 +422,26 @@ __global__ void __launch_bounds__(kTmaThreads)
                 const float b = Bs[ly * kTmaTX];
                 const uint8_t t = Ts[ly * kTmaTX];
                 const float dg = cx.y + (cyb[ly] + cz.y);
-                float v = b;
-                v -= (cx.x * xm + cx.z * xp) + (cya[ly] * ym + cyc[ly] * yp) + (cz.x * zm + cz.z * zp);
-                if (((ly & 1) ? ino : ine) && jin[ly] && is_unknown(t)) ep[ly * hp] = times_rcp(v, dg);
+                const bool in = (ly & 1) ? ino : ine;  // the node of this colour is an interior column
+                if (KIND == 1) {
+                    const float e0 = Es[ly * kTmaTX];
+                    const float ke =
+                        dg * e0 + (cx.x * xm + cx.z * xp) + (cya[ly] * ym + cyc[ly] * yp) + (cz.x * zm + cz.z * zp);
+                    if (in && jin[ly] && is_unknown(t)) ep[ly * hp] = b - ke;
+                } else {
+                    float v = b;
+                    v -= (cx.x * xm + cx.z * xp) + (cya[ly] * ym + cyc[ly] * yp) + (cz.x * zm + cz.z * zp);
+                    if (KIND == 0) {
+                        if (in && jin[ly] && is_unknown(t)) ep[ly * hp] = times_rcp(v, dg);
+                    } else if (jin[ly]) {
+                        // this colour's node i = 2m + par gets its new value (0 off
+                        // the unknowns), the pair's other node keeps the other colour's
+                        float* row = pp + (unsigned)ly * (unsigned)nx;
+                        const bool ino2 = (ly & 1) ? ine : ino;  // the other node is an interior column
+                        if (in) row[par] = is_unknown(t) ? times_rcp(v, dg) : 0.f;
+                        if (ino2) row[1 - par] = par ? xm : xp;
+                    }
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[gp % kTmaStages]);
@@ -750,16 +788,26 @@ Transfer<float> transfer<float>(MgLevel& F) {
     return X;
 }
 
-// the TMA-fed half-sweep where it applies (FP32, MODE 0, a level with maps)
-bool sweep_tma(cfp_ctx*, int, const SLev<double>&, int, cudaStream_t) { return false; }
-bool sweep_tma(cfp_ctx* c, int l, const SLev<float>& L, int colour, cudaStream_t s) {
+// The TMA-fed pass where it applies (FP32, a level with maps): kind 0 the
+// plain half-sweep of `colour`, kind 1 the red residual, kind 2 the last
+// black half-sweep into phi (natural layout).  False: use the plain kernel.
+bool sweep_tma(cfp_ctx*, int, const SLev<double>&, int, int, double*, cudaStream_t) { return false; }
+bool sweep_tma(cfp_ctx* c, int l, const SLev<float>& L, int kind, int colour, float* phi, cudaStream_t s) {
     const MgLevel& M = c->mg[l];
     if (!M.tma || !c->mg_tma) return false;
     const int ntx = (M.n[0] / 2 + kTmaTX - 1) / kTmaTX, nty = (M.n[1] - 2 + kTmaRows - 1) / kTmaRows;
     const int ntz = (M.n[2] - 2 + kTmaPlanes - 1) / kTmaPlanes;
-    k_sweep_tma<<<(unsigned)M.tma_grid, kTmaThreads, kTmaSmem, s>>>(M.tm32[3 * colour], M.tm32[3 * colour + 1],
-                                                                     M.tm32[3 * colour + 2], L, L.e[colour], colour,
-                                                                     ntx, nty, ntz, c->dwait);
+    const CUtensorMap* t = M.tm32 + 3 * colour;  // other colour's e, b, type of `colour`
+    const unsigned grid = (unsigned)M.tma_grid[kind];
+    if (kind == 0)
+        k_sweep_tma<0><<<grid, kTmaThreads, tma_smem(0), s>>>(t[0], t[1], t[2], t[0], L, L.e[colour], colour, ntx,
+                                                               nty, ntz, c->dwait);
+    else if (kind == 1)
+        k_sweep_tma<1><<<grid, kTmaThreads, tma_smem(1), s>>>(t[0], t[1], t[2], M.tm32[6], L, L.r0, 0, ntx, nty,
+                                                               ntz, c->dwait);
+    else
+        k_sweep_tma<2><<<grid, kTmaThreads, tma_smem(2), s>>>(t[0], t[1], t[2], t[0], L, phi, 1, ntx, nty, ntz,
+                                                               c->dwait);
     return true;
 }
 
@@ -770,11 +818,15 @@ void half_sweep(cfp_ctx* c, int l, const SLev<T>& L, const Side<T>& S, int colou
     const Half<T> H{L.ty[colour], L.e[colour], L.e[1 - colour], L.b[colour], L.b[1 - colour]};
     switch (mode) {
         case 0:
-            if (!sweep_tma(c, l, L, colour, s)) k_sweep_split<T, 0><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi);
+            if (!sweep_tma(c, l, L, 0, colour, phi, s))
+                k_sweep_split<T, 0><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi);
             break;
         case 1: k_sweep_split<T, 1><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
         case 2: k_sweep_split<T, 2><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
-        default: k_sweep_split<T, 3><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
+        default:  // the last black half-sweep of the fine level
+            if (colour != 1 || !sweep_tma(c, l, L, 2, colour, phi, s))
+                k_sweep_split<T, 3><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi);
+            break;
     }
     c->launches += 1;
     if (l == 0 && c->n_irr > 0) {  // the Shortley-Weller rows of the irregular nodes
@@ -989,16 +1041,24 @@ cfp_status tile_map(CUtensorMap* m, CUtensorMapDataType dt, int esize, const voi
     return CFP_OK;
 }
 
-// maps and persistent grid of the TMA half-sweep on the levels wide enough
+// maps and persistent grids of the TMA passes on the levels wide enough
+template <int KIND>
+cfp_status tma_occupancy(int* per) {
+    static_assert(tma_smem(KIND) <= 227 * 1024, "shared memory per CTA");
+    CFP_CUDA(cudaFuncSetAttribute(k_sweep_tma<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, tma_smem(KIND)));
+    CFP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_sweep_tma<KIND>, kTmaThreads, tma_smem(KIND)));
+    return CFP_OK;
+}
+
 cfp_status setup_tma(cfp_ctx* c) {
-    static_assert(kTmaSmem <= 227 * 1024, "shared memory per CTA");
-    CFP_CUDA(cudaFuncSetAttribute(k_sweep_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem));
-    int per = 0, nsm = 0;
-    CFP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_tma, kTmaThreads, kTmaSmem));
+    int per[3] = {0, 0, 0}, nsm = 0;
+    CFP_TRY(tma_occupancy<0>(&per[0]));
+    CFP_TRY(tma_occupancy<1>(&per[1]));
+    CFP_TRY(tma_occupancy<2>(&per[2]));
     CFP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
     for (MgLevel& L : c->mg) {
         L.tma = 0;
-        if (L.n[0] / 2 < kTmaMinPairs || per < 1) continue;
+        if (L.n[0] / 2 < kTmaMinPairs || per[0] < 1 || per[1] < 1 || per[2] < 1) continue;
         for (int col = 0; col < 2; ++col) {
             const float* e_oth = L.s32 + (int64_t)(1 - col) * L.Nh;
             const float* b_own = L.s32 + (int64_t)(2 + col) * L.Nh;
@@ -1007,9 +1067,10 @@ cfp_status setup_tma(cfp_ctx* c) {
             CFP_TRY(tile_map(&L.tm32[3 * col + 1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b_own, L, kTmaTX, kTmaRows));
             CFP_TRY(tile_map(&L.tm32[3 * col + 2], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, ty, L, kTmaTX, kTmaRows));
         }
+        CFP_TRY(tile_map(&L.tm32[6], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.s32, L, kTmaTX, kTmaRows));  // red e
         const int64_t tiles = (int64_t)((L.n[0] / 2 + kTmaTX - 1) / kTmaTX) * ((L.n[1] - 2 + kTmaRows - 1) / kTmaRows) *
                               ((L.n[2] - 2 + kTmaPlanes - 1) / kTmaPlanes);
-        L.tma_grid = (int)std::min<int64_t>(tiles, (int64_t)per * nsm);
+        for (int q = 0; q < 3; ++q) L.tma_grid[q] = (int)std::min<int64_t>(tiles, (int64_t)per[q] * nsm);
         L.tma = 1;
     }
     return CFP_OK;
@@ -1064,7 +1125,7 @@ void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
         const Side<T>& S = l == 0 ? S0 : Sc;
         smooth<T>(c, l, S, nu, l == 0 ? 2 : 1, 0, rho, phi, s);
         const SLev<T> F = slev<T>(c, l), C = slev<T>(c, l + 1);
-        k_resid_split<T><<<plane_grid(c->mg[l].n), kSplitThreads, 0, s>>>(F);
+        if (!sweep_tma(c, l, F, 1, 0, phi, s)) k_resid_split<T><<<plane_grid(c->mg[l].n), kSplitThreads, 0, s>>>(F);
         if (l == 0 && c->n_irr > 0) {
             k_resid_fix<T><<<(unsigned)std::min<int64_t>((c->n_irr + 255) / 256, 152 * 8), 256, 0, s>>>(
                 F, S, c->irr_lin, c->n_irr);
