@@ -100,6 +100,13 @@ template <class T>
 struct ApplyRows {
     static constexpr int value = 2;
 };
+// FP64 is arithmetic-bound: four rows per thread share each x-pass among
+// more output rows (7.5 instead of 10 FP64 operations per node for it)
+template <>
+struct ApplyRows<double> {
+    static constexpr int value = 4;
+};
+constexpr int kQfRows = 2;  // rows per thread of k_qf
 
 template <class T, int DOT>
 __global__ void __launch_bounds__(kAX, sizeof(T) == 4 ? 8 : 1)
@@ -337,7 +344,7 @@ __global__ void k_mask_copy(const uint8_t* __restrict__ type, const T* __restric
 // planes for the z-pass out = Lz Q.  Interior non-unknowns get 0.
 __global__ void __launch_bounds__(kAX) k_qf(Grid<double> G, const uint8_t* __restrict__ type,
                                             const double* __restrict__ f, double* __restrict__ out) {
-    constexpr int TY = 2, R = TY + 2;
+    constexpr int TY = kQfRows, R = TY + 2;
     const int nx = G.nx, ny = G.ny, nz = G.nz;
     const int i = 1 + blockIdx.x * kAX + threadIdx.x;
     const int j0 = 1 + blockIdx.y * TY;
@@ -461,11 +468,14 @@ unsigned flat_grid(int64_t n) {
 
 namespace {
 
+dim3 rows_grid(const cfp_ctx* c, int rows) {
+    return dim3((unsigned)((c->n[0] - 2 + kAX - 1) / kAX), (unsigned)((c->n[1] - 2 + rows - 1) / rows),
+                (unsigned)((c->n[2] - 2 + kApplyKC - 1) / kApplyKC));
+}
+
 template <class T>
 dim3 apply_grid(const cfp_ctx* c) {
-    constexpr int TY = ApplyRows<T>::value;
-    return dim3((unsigned)((c->n[0] - 2 + kAX - 1) / kAX), (unsigned)((c->n[1] - 2 + TY - 1) / TY),
-                (unsigned)((c->n[2] - 2 + kApplyKC - 1) / kApplyKC));
+    return rows_grid(c, ApplyRows<T>::value);
 }
 
 }  // namespace
@@ -555,7 +565,7 @@ template void launch_precond<float>(cfp_ctx*, int, const float*, float*, cudaStr
 
 void launch_qf(cfp_ctx* c, const double* f, double* out, cudaStream_t s) {
     c->launches += 1;
-    k_qf<<<apply_grid<double>(c), kAX, 0, s>>>(grid_view<double>(c), c->type, f, out);
+    k_qf<<<rows_grid(c, kQfRows), kAX, 0, s>>>(grid_view<double>(c), c->type, f, out);
 }
 
 void launch_rhs_finish(cfp_ctx* c, const double* qf, const double* bg, const double* g_ibi, double* rhs,
