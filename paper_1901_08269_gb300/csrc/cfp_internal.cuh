@@ -154,6 +154,10 @@ struct MgLevel {
     int tma = 0;
     int tma_grid[3] = {0, 0, 0};
     CUtensorMap tm32[7];
+    // level 0: the irregular nodes of each colour (natural index, split
+    // offset, slot, parity), colour c at fix + c * n_irr, nfix[c] of them
+    void* fix = nullptr;
+    int64_t nfix[2] = {0, 0};
 };
 
 }  // namespace cfp

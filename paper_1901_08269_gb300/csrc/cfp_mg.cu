@@ -156,9 +156,9 @@ template <class T, int MODE>
 __global__ void __launch_bounds__(kSplitThreads)
     k_sweep_split(SLev<T> L, Half<T> H, int colour, const T* __restrict__ rho, T* __restrict__ phi) {
     const int nx = L.nx;
-    const int m = blockIdx.x * kSplitThreads + threadIdx.x;
-    const int j = 1 + blockIdx.y, k0 = 1 + kSweepPlanes * blockIdx.z;
-    if (2 * m > nx - 2) return;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y, k0 = 1 + kSweepPlanes * blockIdx.z;
+    if (2 * m > nx - 2 || j > L.ny - 2) return;
     const int hp = L.hp;
     const unsigned hs = L.hs;
     const T* __restrict__ eoth = H.eoth;
@@ -468,21 +468,39 @@ __global__ void k_wait_diag(int* __restrict__ wait_err) {
     if (threadIdx.x == 0 && !mbar_wait(&bar, 0)) atomicExch(wait_err, 5);
 }
 
-// The half-sweep's update at the fine level's irregular nodes of colour
-// `colour`, with their Shortley-Weller rows (Eq. A7_mod); one thread per
-// irregular point.  Runs right after k_sweep_split of the same colour and
-// mode, overwriting what it stored there.
-template <class T, int MODE>
-__global__ void k_sweep_fix(SLev<T> L, Side<T> S, Half<T> H, const int32_t* __restrict__ irr_lin, int64_t n_irr,
-                            int colour, T* __restrict__ phi) {
-    const int nx = L.nx, ny = L.ny;
+// An irregular node of the fine level, for the follow-up kernels: natural
+// index, offset in its colour's split array, slot (its K row), parity of i.
+struct __align__(16) FixPt {
+    int lin;
+    unsigned o;
+    int slot;
+    int par;
+};
+
+// the per-colour lists of FixPt (entries are independent: any order)
+__global__ void k_fix_list(const int32_t* __restrict__ irr_lin, int64_t n_irr, int nx, int ny, int hp,
+                           unsigned hs, FixPt* __restrict__ out, int* __restrict__ count) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_irr; s += (int64_t)gridDim.x * blockDim.x) {
         const int64_t l = irr_lin[s];
         const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((int64_t)nx * ny));
-        if (((i + j + k) & 1) != colour) continue;
-        const int par = i & 1;
-        const unsigned o = (unsigned)k * L.hs + (unsigned)(j * L.hp + (i >> 1));
-        const T* kr = S.krow + 7 * s;
+        const int c = (i + j + k) & 1;
+        const int q = atomicAdd(&count[c], 1);
+        out[c * n_irr + q] = FixPt{(int)l, (unsigned)k * hs + (unsigned)(j * hp + (i >> 1)), (int)s, i & 1};
+    }
+}
+
+// The half-sweep's update at the fine level's irregular nodes of colour
+// `colour` (the list of that colour), with their Shortley-Weller rows
+// (Eq. A7_mod); one thread per node.  Runs right after the half-sweep of the
+// same colour and mode, overwriting what it stored there.
+template <class T, int MODE>
+__global__ void k_sweep_fix(SLev<T> L, Side<T> S, Half<T> H, const FixPt* __restrict__ list, int64_t n,
+                            T* __restrict__ phi) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const FixPt p = list[q];
+        const int par = p.par;
+        const unsigned o = p.o;
+        const T* kr = S.krow + 7 * (int64_t)p.slot;
         T v = H.bown[o];
         if (MODE == 0 || MODE == 3) {
             const T* __restrict__ eoth = H.eoth;
@@ -490,7 +508,7 @@ __global__ void k_sweep_fix(SLev<T> L, Side<T> S, Half<T> H, const int32_t* __re
                  (kr[5] * eoth[o - L.hs] + kr[6] * eoth[o + L.hs]);
         }
         v = times_rcp(v, kr[0]);
-        if (MODE == 3) phi[l] = v;
+        if (MODE == 3) phi[p.lin] = v;
         else H.eown[o] = v;
     }
 }
@@ -502,9 +520,9 @@ __global__ void k_sweep_fix(SLev<T> L, Side<T> S, Half<T> H, const int32_t* __re
 template <class T>
 __global__ void __launch_bounds__(kSplitThreads) k_resid_split(SLev<T> L) {
     const int nx = L.nx;
-    const int m = blockIdx.x * kSplitThreads + threadIdx.x;
-    const int j = 1 + blockIdx.y, k0 = 1 + kSweepPlanes * blockIdx.z;
-    if (2 * m > nx - 2) return;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y, k0 = 1 + kSweepPlanes * blockIdx.z;
+    if (2 * m > nx - 2 || j > L.ny - 2) return;
     const int hp = L.hp;
     const unsigned hs = L.hs;
     const T* __restrict__ e1 = L.e[1];
@@ -537,15 +555,12 @@ __global__ void __launch_bounds__(kSplitThreads) k_resid_split(SLev<T> L) {
 // the red residual at the fine level's irregular red nodes with their
 // Shortley-Weller rows (after k_resid_split)
 template <class T>
-__global__ void k_resid_fix(SLev<T> L, Side<T> S, const int32_t* __restrict__ irr_lin, int64_t n_irr) {
-    const int nx = L.nx, ny = L.ny;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_irr; s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t l = irr_lin[s];
-        const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((int64_t)nx * ny));
-        if (((i + j + k) & 1) != 0) continue;
-        const int par = i & 1;
-        const unsigned o = (unsigned)k * L.hs + (unsigned)(j * L.hp + (i >> 1));
-        const T* kr = S.krow + 7 * s;
+__global__ void k_resid_fix(SLev<T> L, Side<T> S, const FixPt* __restrict__ red, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const FixPt p = red[q];
+        const int par = p.par;
+        const unsigned o = p.o;
+        const T* kr = S.krow + 7 * (int64_t)p.slot;
         const T* __restrict__ e1 = L.e[1];
         const T ke = kr[0] * L.e[0][o] + (kr[1] * e1[o - 1 + par] + kr[2] * e1[o + par]) +
                      (kr[3] * e1[o - L.hp] + kr[4] * e1[o + L.hp]) + (kr[5] * e1[o - L.hs] + kr[6] * e1[o + L.hs]);
@@ -595,9 +610,9 @@ __global__ void k_restrict_split(Transfer<T> X, SLev<T> F, SLev<T> C) {
 template <class T>
 __global__ void __launch_bounds__(kSplitThreads) k_prolong_split(Transfer<T> X, SLev<T> F, SLev<T> C) {
     const int nx = F.nx;
-    const int m = blockIdx.x * kSplitThreads + threadIdx.x;
-    const int j = 1 + blockIdx.y, k0 = 1 + kSweepPlanes * blockIdx.z;
-    if (2 * m > nx - 2) return;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y, k0 = 1 + kSweepPlanes * blockIdx.z;
+    if (2 * m > nx - 2 || j > F.ny - 2) return;
     const unsigned hc = (unsigned)C.hp;
     const IpPk<T> py = X.ip[1][j];
     const int J = py.ilo;
@@ -688,11 +703,18 @@ __global__ void k_split_type(const uint8_t* __restrict__ nat, int nx, int ny, in
 
 unsigned flat_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
 
-// threads over the pairs m = 0 .. (n_x - 2) / 2 and the interior rows j;
-// blocks over groups of kSweepPlanes interior planes
+// Threads over the pairs m = 0 .. (n_x - 2) / 2 (x) and the interior rows j
+// (y), blocks over groups of kSweepPlanes interior planes (z).  A block is
+// kSplitThreads threads: as many pairs as the row has, rounded up to a warp
+// and at most kSplitThreads, times as many rows as fill it, so that the
+// narrow coarse levels do not leave most lanes idle.
+dim3 plane_block(const int n[3]) {
+    const int bx = std::min(kSplitThreads, (n[0] / 2 + 31) / 32 * 32);
+    return dim3((unsigned)bx, (unsigned)(kSplitThreads / bx));
+}
 dim3 plane_grid(const int n[3]) {
-    const int pairs = n[0] / 2;
-    return dim3((unsigned)((pairs + kSplitThreads - 1) / kSplitThreads), (unsigned)(n[1] - 2),
+    const dim3 b = plane_block(n);
+    return dim3((unsigned)((n[0] / 2 + b.x - 1) / b.x), (unsigned)((n[1] - 2 + b.y - 1) / b.y),
                 (unsigned)((n[2] - 2 + kSweepPlanes - 1) / kSweepPlanes));
 }
 
@@ -814,28 +836,31 @@ bool sweep_tma(cfp_ctx* c, int l, const SLev<float>& L, int kind, int colour, fl
 template <class T>
 void half_sweep(cfp_ctx* c, int l, const SLev<T>& L, const Side<T>& S, int colour, int mode, const T* rho, T* phi,
                 cudaStream_t s) {
-    const dim3 g = plane_grid(c->mg[l].n);
+    const dim3 g = plane_grid(c->mg[l].n), blk = plane_block(c->mg[l].n);
     const Half<T> H{L.ty[colour], L.e[colour], L.e[1 - colour], L.b[colour], L.b[1 - colour]};
     switch (mode) {
         case 0:
             if (!sweep_tma(c, l, L, 0, colour, phi, s))
-                k_sweep_split<T, 0><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi);
+                k_sweep_split<T, 0><<<g, blk, 0, s>>>(L, H, colour, rho, phi);
             break;
-        case 1: k_sweep_split<T, 1><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
-        case 2: k_sweep_split<T, 2><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi); break;
+        case 1: k_sweep_split<T, 1><<<g, blk, 0, s>>>(L, H, colour, rho, phi); break;
+        case 2: k_sweep_split<T, 2><<<g, blk, 0, s>>>(L, H, colour, rho, phi); break;
         default:  // the last black half-sweep of the fine level
             if (colour != 1 || !sweep_tma(c, l, L, 2, colour, phi, s))
-                k_sweep_split<T, 3><<<g, kSplitThreads, 0, s>>>(L, H, colour, rho, phi);
+                k_sweep_split<T, 3><<<g, blk, 0, s>>>(L, H, colour, rho, phi);
             break;
     }
     c->launches += 1;
-    if (l == 0 && c->n_irr > 0) {  // the Shortley-Weller rows of the irregular nodes
-        const unsigned nb = (unsigned)std::min<int64_t>((c->n_irr + 255) / 256, 152 * 8);
+    const MgLevel& M0 = c->mg[0];
+    if (l == 0 && M0.nfix[colour] > 0) {  // the Shortley-Weller rows of the irregular nodes
+        const int64_t n = M0.nfix[colour];
+        const FixPt* list = static_cast<const FixPt*>(M0.fix) + colour * c->n_irr;
+        const unsigned nb = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8);
         switch (mode) {
-            case 0: k_sweep_fix<T, 0><<<nb, 256, 0, s>>>(L, S, H, c->irr_lin, c->n_irr, colour, phi); break;
-            case 1: k_sweep_fix<T, 1><<<nb, 256, 0, s>>>(L, S, H, c->irr_lin, c->n_irr, colour, phi); break;
-            case 2: k_sweep_fix<T, 2><<<nb, 256, 0, s>>>(L, S, H, c->irr_lin, c->n_irr, colour, phi); break;
-            default: k_sweep_fix<T, 3><<<nb, 256, 0, s>>>(L, S, H, c->irr_lin, c->n_irr, colour, phi); break;
+            case 0: k_sweep_fix<T, 0><<<nb, 256, 0, s>>>(L, S, H, list, n, phi); break;
+            case 1: k_sweep_fix<T, 1><<<nb, 256, 0, s>>>(L, S, H, list, n, phi); break;
+            case 2: k_sweep_fix<T, 2><<<nb, 256, 0, s>>>(L, S, H, list, n, phi); break;
+            default: k_sweep_fix<T, 3><<<nb, 256, 0, s>>>(L, S, H, list, n, phi); break;
         }
         c->launches += 1;
     }
@@ -858,7 +883,7 @@ void smooth(cfp_ctx* c, int l, const Side<T>& S, int sweeps, int first_red, int 
 void free_mg(cfp_ctx* c) {
     for (MgLevel& L : c->mg) {
         void* ptrs[] = {L.coef64, L.coef32, L.type, L.stype, L.s64, L.s32, L.pk64, L.pk32,
-                        L.ip64, L.ip32, L.rw64, L.rw32};
+                        L.ip64, L.ip32, L.rw64, L.rw32, L.fix};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     }
@@ -1001,6 +1026,22 @@ cfp_status build_levels(cfp_ctx* c) {
         k_pack_coefs<float><<<pb, 128, 0, c->stream>>>(level_grid_view<float>(c, L, l), static_cast<float4*>(L.pk32));
         CFP_CUDA(cudaGetLastError());
     }
+    // the fine level's irregular nodes split by colour, for the follow-ups
+    MgLevel& L0 = c->mg[0];
+    if (c->n_irr > 0) {
+        CFP_CUDA(cudaMalloc(&L0.fix, sizeof(FixPt) * 2 * c->n_irr));
+        int* count = reinterpret_cast<int*>(c->dtotal + 5);  // scratch of the context
+        CFP_CUDA(cudaMemsetAsync(count, 0, 2 * sizeof(int), c->stream));
+        k_fix_list<<<flat_blocks(c->n_irr), 256, 0, c->stream>>>(c->irr_lin, c->n_irr, L0.n[0], L0.n[1], L0.hp,
+                                                                  (unsigned)((int64_t)L0.hp * L0.n[1]),
+                                                                  static_cast<FixPt*>(L0.fix), count);
+        CFP_CUDA(cudaGetLastError());
+        int hc[2] = {0, 0};
+        CFP_CUDA(cudaMemcpyAsync(hc, count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CFP_CUDA(cudaStreamSynchronize(c->stream));
+        L0.nfix[0] = hc[0];
+        L0.nfix[1] = hc[1];
+    }
     CFP_CUDA(cudaStreamSynchronize(c->stream));
     return CFP_OK;
 }
@@ -1125,10 +1166,11 @@ void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
         const Side<T>& S = l == 0 ? S0 : Sc;
         smooth<T>(c, l, S, nu, l == 0 ? 2 : 1, 0, rho, phi, s);
         const SLev<T> F = slev<T>(c, l), C = slev<T>(c, l + 1);
-        if (!sweep_tma(c, l, F, 1, 0, phi, s)) k_resid_split<T><<<plane_grid(c->mg[l].n), kSplitThreads, 0, s>>>(F);
-        if (l == 0 && c->n_irr > 0) {
-            k_resid_fix<T><<<(unsigned)std::min<int64_t>((c->n_irr + 255) / 256, 152 * 8), 256, 0, s>>>(
-                F, S, c->irr_lin, c->n_irr);
+        if (!sweep_tma(c, l, F, 1, 0, phi, s)) k_resid_split<T><<<plane_grid(c->mg[l].n), plane_block(c->mg[l].n), 0, s>>>(F);
+        if (l == 0 && c->mg[0].nfix[0] > 0) {
+            const int64_t n = c->mg[0].nfix[0];
+            k_resid_fix<T><<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(
+                F, S, static_cast<const FixPt*>(c->mg[0].fix), n);
             c->launches += 1;
         }
         const MgLevel& Cn = c->mg[l + 1];
@@ -1141,7 +1183,7 @@ void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
     // fine level writes phi
     for (int l = nl - 2; l >= 0; --l) {
         const SLev<T> F = slev<T>(c, l), C = slev<T>(c, l + 1);
-        k_prolong_split<T><<<plane_grid(c->mg[l].n), kSplitThreads, 0, s>>>(transfer<T>(c->mg[l]), F, C);
+        k_prolong_split<T><<<plane_grid(c->mg[l].n), plane_block(c->mg[l].n), 0, s>>>(transfer<T>(c->mg[l]), F, C);
         c->launches += 1;
         smooth<T>(c, l, l == 0 ? S0 : Sc, npost, 0, l == 0 ? 3 : 0, rho, phi, s);
     }
