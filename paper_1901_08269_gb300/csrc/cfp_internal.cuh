@@ -128,12 +128,12 @@ struct MgLevel {
     uint8_t* type = nullptr;   // natural layout (levels >= 1; level 0 uses the context's)
     // red-black split layout: node (i, j, k) of colour (i + j + k) & 1 sits at
     // entry (k * n[1] + j) * hp + (i >> 1) of its colour's array
-    int hp = 0;                // entries per row of one colour, padded to 16 (16-byte rows of
-                               // the byte-wide split type, as the TMA tensor maps require)
+    int hp = 0;                // entries per row of one colour, padded to 16 (rows of 64 bytes
+                               // in FP32: TMA tensor maps need 16-byte row strides)
     int64_t Nh = 0;            // entries per colour array: hp * n[1] * n[2]
     uint8_t* stype = nullptr;  // split type, colour c at stype + c * Nh
     double* s64 = nullptr;     // split e0 e1 b0 b1 r0 (Nh each), FP64
-    float* s32 = nullptr;      // the same in FP32
+    float* s32 = nullptr;      // the same in FP32; b holds NaN at every entry that is not an unknown
     void* pk64 = nullptr;      // packed (ka, kb, kc, 0) per index, x then y then z, FP64
     void* pk32 = nullptr;      // the same in FP32
     // transfers with the next coarser level, FP64 and FP32 copies: per fine
@@ -147,13 +147,12 @@ struct MgLevel {
     void* rw64 = nullptr;
     void* rw32 = nullptr;
     // TMA-fed FP32 passes (levels with at least kTmaMinPairs pairs per row):
-    // per colour c, maps of the other colour's e, of b and of the type at
-    // tm32[3 c + 0 .. 2], the red e at tm32[6]; per pass kind (half-sweep,
-    // red residual, last black half-sweep) the persistent grid (resident
-    // CTAs x SMs)
+    // per colour c, maps of the other colour's e and of b at tm32[2 c + 0, 1],
+    // the red e at tm32[4]; per pass kind (half-sweep, red residual, last
+    // black half-sweep) the persistent grid (resident CTAs x SMs)
     int tma = 0;
     int tma_grid[3] = {0, 0, 0};
-    CUtensorMap tm32[7];
+    CUtensorMap tm32[5];
     // level 0: the irregular nodes of each colour (natural index, split
     // offset, slot, parity), colour c at fix + c * n_irr, nfix[c] of them
     void* fix = nullptr;

@@ -23,11 +23,11 @@
 // colour in its own array, rows of (n_x + 1) / 2 entries padded to 16), so a
 // half-sweep reads the other colour and writes its own without moving the
 // unused half of each cache line.  On the large levels the FP32 half-sweeps
-// stream tiles of the other colour (with a one-node halo), of b and of the
-// type through shared memory with TMA bulk-tensor copies (k_sweep_tma).  The fine level converts on the way in
-// (the first red half-sweep reads rho in the natural layout and stores both
-// colours of it) and on the way out (the last black half-sweep writes both
-// colours of phi in the natural layout).
+// stream tiles of the other colour (with a one-node halo) and of b through
+// shared memory with TMA bulk-tensor copies (k_sweep_tma).  The fine level
+// converts on the way in (the first red half-sweep reads rho in the natural
+// layout and stores both colours of it) and on the way out (the last black
+// half-sweep writes both colours of phi in the natural layout).
 //
 // Two exact shortcuts of red-black smoothing: after a sweep ends with the
 // black half, the residual of every black row is zero (that half-sweep just
@@ -109,12 +109,17 @@ struct SLev {
 // the arrays one half-sweep of colour c touches (chosen on the host)
 template <class T>
 struct Half {
-    const uint8_t* ty;  // type of colour c
-    T* eown;            // e of colour c (written)
-    const T* eoth;      // e of the other colour (read)
-    T* bown;            // b of colour c
-    T* both;            // b of the other colour (written in MODE 2)
+    const uint8_t* ty;   // type of colour c
+    T* eown;             // e of colour c (written)
+    const T* eoth;       // e of the other colour (read)
+    T* bown;             // b of colour c
+    T* both;             // b of the other colour (written in MODE 2)
+    const uint8_t* tyo;  // type of the other colour (MODE 2)
 };
+
+// FP32 levels hold NaN in b at every entry that is not an unknown (the TMA
+// passes tell the unknowns by b == b and need not load the type)
+__device__ __forceinline__ float b_mark() { return __int_as_float(0x7fc00000); }
 
 enum { kSplitVecs = 5 };  // e0 e1 b0 b1 r0
 
@@ -175,7 +180,13 @@ __global__ void __launch_bounds__(kSplitThreads)
         const int64_t row = ((int64_t)k * L.ny + j) * nx;
         const uint8_t t = H.ty[o];
         bv[q] = MODE == 2 ? rho[row + i] : H.bown[o];
-        if (MODE == 2) bo[q] = rho[row + io];
+        if (MODE == 2) {
+            bo[q] = rho[row + io];
+            if (sizeof(T) == 4) {  // the NaN marks of the FP32 levels
+                if (!is_unknown(t)) bv[q] = T(b_mark());
+                if (!is_unknown(H.tyo[o])) bo[q] = T(b_mark());
+            }
+        }
         T xm = T(0), xp = T(0), ym = T(0), yp = T(0), zm = T(0), zp = T(0);
         if (MODE == 0 || MODE == 3) {
             xm = eoth[o - 1 + par];
@@ -218,8 +229,8 @@ __global__ void __launch_bounds__(kSplitThreads)
 
 // ---------------------------------------------------------------- TMA path
 // Three FP32 passes of a large level with the access pattern of a half-sweep
-// (a node of one colour reads its six neighbours of the other colour, its b
-// and its type), run as a pipeline.  KIND 0: the plain half-sweep (MODE 0)
+// (a node of one colour reads its six neighbours of the other colour and its
+// b, NaN where the node is not an unknown), run as a pipeline.  KIND 0: the plain half-sweep (MODE 0)
 // into e of its colour; KIND 1: the red residual r0 = b0 - K e (k_resid_split;
 // the stage also holds the red e of the tile); KIND 2: the fine level's last
 // black half-sweep into the natural-layout phi, both nodes of each pair
@@ -231,10 +242,10 @@ __global__ void __launch_bounds__(kSplitThreads)
 // kTmaTX pairs x kTmaRows rows x kTmaPlanes planes of colour `colour`; a
 // stage holds, for one plane k, the other colour's pairs m0 - 4 .. m0 +
 // kTmaTX + 3 of rows j0 - 1 .. j0 + kTmaRows (the one-node halo in x and y;
-// the x start is a multiple of 4 entries, 16 bytes), b and the type of the
-// tile's own rows; the output of plane k reads the stages of planes k - 1,
-// k, k + 1.  Copies outside the array (row j0 + kTmaRows past the last, pair
-// -4 .. -1) fill zeros and feed only nodes that are not updated.  The CTAs
+// the x start is a multiple of 4 entries, 16 bytes) and b of the tile's own
+// rows; the output of plane k reads the stages of planes k - 1, k, k + 1.
+// Copies outside the array (row j0 + kTmaRows past the last, pair -4 .. -1)
+// fill zeros and feed only nodes that are not updated.  The CTAs
 // are persistent: CTA q takes tiles q, q + grid, ... with the x tile varying
 // fastest, then y, then the z chunk, so the CTAs at work at one time share
 // their halo rows through L2.  Same arithmetic as k_sweep_split<float, 0>:
@@ -247,12 +258,12 @@ constexpr int kTmaOX = kTmaTX + 8;                                   // other-co
 constexpr int kTmaOBytes = kTmaOX * (kTmaRows + 2) * 4;              // other-colour tile
 constexpr int kTmaOPad = (kTmaOBytes + 127) / 128 * 128;
 constexpr int kTmaBBytes = kTmaTX * kTmaRows * 4;                    // b of the tile
-constexpr int kTmaTBytes = kTmaTX * kTmaRows;                        // type of the tile
 constexpr int kTmaThreads = 32 * (kTmaRows + 1);                     // + the producer warp
-// a stage: [other colour with halo | b | type | (KIND 1) own e]; KIND 1 has
-// a larger stage and one stage fewer, so three CTAs still fit an SM
+// a stage: [other colour with halo | b | (KIND 1) own e]; KIND 1 has a
+// larger stage and one stage fewer, so three CTAs still fit an SM.  The type
+// is not loaded: b is NaN exactly at the entries that are not unknowns.
 __host__ __device__ constexpr int tma_stage(int kind) {
-    return kTmaOPad + kTmaBBytes + kTmaTBytes + (kind == 1 ? kTmaBBytes : 0);
+    return kTmaOPad + kTmaBBytes + (kind == 1 ? kTmaBBytes : 0);
 }
 __host__ __device__ constexpr int tma_stages(int kind) { return kind == 1 ? 5 : 6; }
 __host__ __device__ constexpr int tma_smem(int kind) {
@@ -312,10 +323,10 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
 template <int KIND>
 __global__ void __launch_bounds__(kTmaThreads)
     k_sweep_tma(const __grid_constant__ CUtensorMap t_oth, const __grid_constant__ CUtensorMap t_b,
-                const __grid_constant__ CUtensorMap t_ty, const __grid_constant__ CUtensorMap t_own, SLev<float> L,
+                const __grid_constant__ CUtensorMap t_own, SLev<float> L,
                 float* __restrict__ out, int colour, int ntx, int nty, int ntz, int* __restrict__ wait_err) {
     constexpr int kTmaStages = tma_stages(KIND), kTmaStage = tma_stage(KIND);
-    constexpr int kEOff = kTmaOPad + kTmaBBytes + kTmaTBytes;  // KIND 1: own e of the tile
+    constexpr int kEOff = kTmaOPad + kTmaBBytes;  // KIND 1: own e of the tile
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     uint64_t* full = (uint64_t*)(base + kTmaStages * kTmaStage);  // stage filled (tx bytes landed)
@@ -347,10 +358,9 @@ __global__ void __launch_bounds__(kTmaThreads)
                     atomicExch(wait_err, 1);
                 }
                 unsigned char* buf = base + st * kTmaStage;
-                mbar_arrive_expect_tx(&full[st], kTmaOBytes + kTmaBBytes + kTmaTBytes + (KIND == 1 ? kTmaBBytes : 0));
+                mbar_arrive_expect_tx(&full[st], kTmaOBytes + kTmaBBytes + (KIND == 1 ? kTmaBBytes : 0));
                 tma_load_3d(buf, &t_oth, &full[st], m0 - 4, j0 - 1, k);
                 tma_load_3d(buf + kTmaOPad, &t_b, &full[st], m0, j0, k);
-                tma_load_3d(buf + kTmaOPad + kTmaBBytes, &t_ty, &full[st], m0, j0, k);
                 if (KIND == 1) tma_load_3d(buf + kEOff, &t_own, &full[st], m0, j0, k);
             }
         }
@@ -402,7 +412,6 @@ __global__ void __launch_bounds__(kTmaThreads)
             const float* O0 = (const float*)s0 + at;
             const float* Op = (const float*)(base + ((gp + 2) % kTmaStages) * kTmaStage) + at;
             const float* Bs = (const float*)(s0 + kTmaOPad) + r0 * kTmaTX + lx;
-            const uint8_t* Ts = s0 + kTmaOPad + kTmaBBytes + r0 * kTmaTX + lx;
             const float* Es = (const float*)(s0 + kEOff) + r0 * kTmaTX + lx;  // KIND 1 only
             const int k = k0 + kk;
             const float4 cz = L.cz[k];
@@ -420,25 +429,25 @@ __global__ void __launch_bounds__(kTmaThreads)
                 const float xm = O0[o - 1 + par], xp = O0[o + par], ym = O0[o - kTmaOX], yp = O0[o + kTmaOX];
                 const float zm = Om[o], zp = Op[o];
                 const float b = Bs[ly * kTmaTX];
-                const uint8_t t = Ts[ly * kTmaTX];
+                const bool unk = b == b;  // not NaN: an unknown
                 const float dg = cx.y + (cyb[ly] + cz.y);
                 const bool in = (ly & 1) ? ino : ine;  // the node of this colour is an interior column
                 if (KIND == 1) {
                     const float e0 = Es[ly * kTmaTX];
                     const float ke =
                         dg * e0 + (cx.x * xm + cx.z * xp) + (cya[ly] * ym + cyc[ly] * yp) + (cz.x * zm + cz.z * zp);
-                    if (in && jin[ly] && is_unknown(t)) ep[ly * hp] = b - ke;
+                    if (in && jin[ly] && unk) ep[ly * hp] = b - ke;
                 } else {
                     float v = b;
                     v -= (cx.x * xm + cx.z * xp) + (cya[ly] * ym + cyc[ly] * yp) + (cz.x * zm + cz.z * zp);
                     if (KIND == 0) {
-                        if (in && jin[ly] && is_unknown(t)) ep[ly * hp] = times_rcp(v, dg);
+                        if (in && jin[ly] && unk) ep[ly * hp] = times_rcp(v, dg);
                     } else if (jin[ly]) {
                         // this colour's node i = 2m + par gets its new value (0 off
                         // the unknowns), the pair's other node keeps the other colour's
                         float* row = pp + (unsigned)ly * (unsigned)nx;
                         const bool ino2 = (ly & 1) ? ine : ino;  // the other node is an interior column
-                        if (in) row[par] = is_unknown(t) ? times_rcp(v, dg) : 0.f;
+                        if (in) row[par] = unk ? times_rcp(v, dg) : 0.f;
                         if (ino2) row[1 - par] = par ? xm : xp;
                     }
                 }
@@ -701,6 +710,13 @@ __global__ void k_split_type(const uint8_t* __restrict__ nat, int nx, int ny, in
     }
 }
 
+// b of both colours (2 Nh entries from b): NaN where the split type is not an
+// unknown (padding entries are typed boundary)
+__global__ void k_mark_b(const uint8_t* __restrict__ st, float* __restrict__ b, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        if (!is_unknown(st[q])) b[q] = b_mark();
+}
+
 unsigned flat_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
 
 // Threads over the pairs m = 0 .. (n_x - 2) / 2 (x) and the interior rows j
@@ -819,16 +835,16 @@ bool sweep_tma(cfp_ctx* c, int l, const SLev<float>& L, int kind, int colour, fl
     if (!M.tma || !c->mg_tma) return false;
     const int ntx = (M.n[0] / 2 + kTmaTX - 1) / kTmaTX, nty = (M.n[1] - 2 + kTmaRows - 1) / kTmaRows;
     const int ntz = (M.n[2] - 2 + kTmaPlanes - 1) / kTmaPlanes;
-    const CUtensorMap* t = M.tm32 + 3 * colour;  // other colour's e, b, type of `colour`
+    const CUtensorMap* t = M.tm32 + 2 * colour;  // other colour's e, b of `colour`
     const unsigned grid = (unsigned)M.tma_grid[kind];
     if (kind == 0)
-        k_sweep_tma<0><<<grid, kTmaThreads, tma_smem(0), s>>>(t[0], t[1], t[2], t[0], L, L.e[colour], colour, ntx,
-                                                               nty, ntz, c->dwait);
-    else if (kind == 1)
-        k_sweep_tma<1><<<grid, kTmaThreads, tma_smem(1), s>>>(t[0], t[1], t[2], M.tm32[6], L, L.r0, 0, ntx, nty,
+        k_sweep_tma<0><<<grid, kTmaThreads, tma_smem(0), s>>>(t[0], t[1], t[0], L, L.e[colour], colour, ntx, nty,
                                                                ntz, c->dwait);
+    else if (kind == 1)
+        k_sweep_tma<1><<<grid, kTmaThreads, tma_smem(1), s>>>(t[0], t[1], M.tm32[4], L, L.r0, 0, ntx, nty, ntz,
+                                                               c->dwait);
     else
-        k_sweep_tma<2><<<grid, kTmaThreads, tma_smem(2), s>>>(t[0], t[1], t[2], t[0], L, phi, 1, ntx, nty, ntz,
+        k_sweep_tma<2><<<grid, kTmaThreads, tma_smem(2), s>>>(t[0], t[1], t[0], L, phi, 1, ntx, nty, ntz,
                                                                c->dwait);
     return true;
 }
@@ -837,7 +853,7 @@ template <class T>
 void half_sweep(cfp_ctx* c, int l, const SLev<T>& L, const Side<T>& S, int colour, int mode, const T* rho, T* phi,
                 cudaStream_t s) {
     const dim3 g = plane_grid(c->mg[l].n), blk = plane_block(c->mg[l].n);
-    const Half<T> H{L.ty[colour], L.e[colour], L.e[1 - colour], L.b[colour], L.b[1 - colour]};
+    const Half<T> H{L.ty[colour], L.e[colour], L.e[1 - colour], L.b[colour], L.b[1 - colour], L.ty[1 - colour]};
     switch (mode) {
         case 0:
             if (!sweep_tma(c, l, L, 0, colour, phi, s))
@@ -1103,12 +1119,10 @@ cfp_status setup_tma(cfp_ctx* c) {
         for (int col = 0; col < 2; ++col) {
             const float* e_oth = L.s32 + (int64_t)(1 - col) * L.Nh;
             const float* b_own = L.s32 + (int64_t)(2 + col) * L.Nh;
-            const uint8_t* ty = L.stype + (int64_t)col * L.Nh;
-            CFP_TRY(tile_map(&L.tm32[3 * col], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, e_oth, L, kTmaOX, kTmaRows + 2));
-            CFP_TRY(tile_map(&L.tm32[3 * col + 1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b_own, L, kTmaTX, kTmaRows));
-            CFP_TRY(tile_map(&L.tm32[3 * col + 2], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, ty, L, kTmaTX, kTmaRows));
+            CFP_TRY(tile_map(&L.tm32[2 * col], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, e_oth, L, kTmaOX, kTmaRows + 2));
+            CFP_TRY(tile_map(&L.tm32[2 * col + 1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b_own, L, kTmaTX, kTmaRows));
         }
-        CFP_TRY(tile_map(&L.tm32[6], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.s32, L, kTmaTX, kTmaRows));  // red e
+        CFP_TRY(tile_map(&L.tm32[4], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.s32, L, kTmaTX, kTmaRows));  // red e
         const int64_t tiles = (int64_t)((L.n[0] / 2 + kTmaTX - 1) / kTmaTX) * ((L.n[1] - 2 + kTmaRows - 1) / kTmaRows) *
                               ((L.n[2] - 2 + kTmaPlanes - 1) / kTmaPlanes);
         for (int q = 0; q < 3; ++q) L.tma_grid[q] = (int)std::min<int64_t>(tiles, (int64_t)per[q] * nsm);
@@ -1140,6 +1154,8 @@ cfp_status ensure_mg(cfp_ctx* c, int prec) {
         if (prec == 1 && !L.s32) {
             CFP_CUDA(cudaMalloc(&L.s32, sizeof(float) * n));
             CFP_CUDA(cudaMemsetAsync(L.s32, 0, sizeof(float) * n, c->stream));
+            k_mark_b<<<flat_blocks(2 * L.Nh), 256, 0, c->stream>>>(L.stype, L.s32 + 2 * L.Nh, 2 * L.Nh);
+            CFP_CUDA(cudaGetLastError());
             fresh32 = true;
         }
     }
