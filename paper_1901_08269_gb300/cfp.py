@@ -52,7 +52,8 @@ _D = C.POINTER(C.c_double)
 EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_destroy", "cfp_classify_points",
            "cfp_ibi_points", "cfp_assemble_rhs", "cfp_apply", "cfp_precondition", "cfp_solve", "cfp_solve_host",
            "cfp_time_kernel", "cfp_launch_count", "cfp_assemble_rhs_noalloc", "cfp_precondition_ex",
-           "cfp_solve_batch", "cfp_autotune", "cfp_diag_bounded_wait"]
+           "cfp_solve_batch", "cfp_autotune", "cfp_diag_bounded_wait", "cfp_nn_pack", "cfp_nn_conv3d",
+           "cfp_nn_conv3d_dgrad", "cfp_nn_conv3d_wgrad", "cfp_nn_mse", "cfp_nn_adam", "cfp_nn_unpack"]
 KERNEL_APPLY, KERNEL_RBGS, KERNEL_UPDATE, KERNEL_MG_SWEEP = 0, 1, 2, 3
 
 
@@ -89,6 +90,13 @@ def lib(build_if_missing=True):
         L.cfp_launch_count.argtypes = [_P]
         L.cfp_launch_count.restype = C.c_int64
         L.cfp_diag_bounded_wait.argtypes = [_P]
+        L.cfp_nn_pack.argtypes = [_P, _P, _P, C.c_double, C.c_double, _P, _P, _P, _D]
+        L.cfp_nn_conv3d.argtypes = [_P, _P, _P, _P, C.c_int, _P, _P]
+        L.cfp_nn_conv3d_dgrad.argtypes = [_P, _P, _P, _P, _P]
+        L.cfp_nn_conv3d_wgrad.argtypes = [_P, _P, _P, _P, _P]
+        L.cfp_nn_mse.argtypes = [_P, _P, _P, _P, C.c_double, _P, _D]
+        L.cfp_nn_adam.argtypes = [_P, C.c_int64, _P, _P, _P, _P, C.c_int, C.c_double, _P]
+        L.cfp_nn_unpack.argtypes = [_P, _P, C.c_double, _P]
         for name in EXPORTS[2:]:
             if name not in ("cfp_ctx_destroy", "cfp_launch_count"):
                 getattr(L, name).restype = C.c_int
@@ -173,6 +181,74 @@ class Context:
         _check(st, "cfp_ctx_create")
         self._h = h
         self.n_irregular = self.n_ibi = None
+
+    # ---- the learned part (include/cfp_nn.h): activations are N x 16 bfloat16,
+    # weights 16 x 27 x 16 bfloat16, all CUDA tensors; argument marshalling only
+    def _nn(self, t, name, dtype, numel):
+        if t is None or not t.is_cuda or t.dtype != dtype or t.numel() != numel:
+            raise ValueError("%s must be a CUDA %s tensor with %d elements" % (name, dtype, numel))
+        return _ptr(t)
+
+    def nn_pack(self, r, e, scale, escale, x, target=None, mask=None):
+        """Returns the scale used (scale <= 0: 1 / max |r| at the unknowns)."""
+        import torch
+        used = C.c_double()
+        _check(lib().cfp_nn_pack(self._h, self._field(r, "r"), None if e is None else self._field(e, "e"),
+                                 float(scale), float(escale), self._nn(x, "x", torch.bfloat16, 16 * self.N),
+                                 None if target is None else self._nn(target, "target", torch.float32, self.N),
+                                 None if mask is None else self._nn(mask, "mask", torch.float32, self.N),
+                                 C.byref(used)), "cfp_nn_pack")
+        return used.value
+
+    def nn_conv3d(self, inp, w, bias, relu, out):
+        import torch
+        bf, f32 = (out, None) if out.dtype == torch.bfloat16 else (None, out)
+        _check(lib().cfp_nn_conv3d(self._h, self._nn(inp, "in", torch.bfloat16, 16 * self.N),
+                                   self._nn(w, "w", torch.bfloat16, 16 * 27 * 16),
+                                   None if bias is None else self._nn(bias, "bias", torch.float32, 16), int(relu),
+                                   None if bf is None else self._nn(bf, "out", torch.bfloat16, 16 * self.N),
+                                   None if f32 is None else self._nn(f32, "out", torch.float32, 16 * self.N)),
+               "cfp_nn_conv3d")
+        return out
+
+    def nn_dgrad(self, dout, w, act, din):
+        import torch
+        _check(lib().cfp_nn_conv3d_dgrad(self._h, self._nn(dout, "dout", torch.bfloat16, 16 * self.N),
+                                         self._nn(w, "w", torch.bfloat16, 16 * 27 * 16),
+                                         None if act is None else self._nn(act, "act", torch.bfloat16, 16 * self.N),
+                                         self._nn(din, "din", torch.bfloat16, 16 * self.N)), "cfp_nn_conv3d_dgrad")
+        return din
+
+    def nn_wgrad(self, inp, dout, dw, db=None):
+        import torch
+        _check(lib().cfp_nn_conv3d_wgrad(self._h, self._nn(inp, "in", torch.bfloat16, 16 * self.N),
+                                         self._nn(dout, "dout", torch.bfloat16, 16 * self.N),
+                                         self._nn(dw, "dw", torch.float32, 16 * 27 * 16),
+                                         None if db is None else self._nn(db, "db", torch.float32, 16)),
+               "cfp_nn_conv3d_wgrad")
+
+    def nn_mse(self, y, target, mask, inv_count, dout):
+        import torch
+        loss = C.c_double()
+        _check(lib().cfp_nn_mse(self._h, self._nn(y, "y", torch.float32, 16 * self.N),
+                                self._nn(target, "target", torch.float32, self.N),
+                                self._nn(mask, "mask", torch.float32, self.N), float(inv_count),
+                                self._nn(dout, "dout", torch.bfloat16, 16 * self.N), C.byref(loss)), "cfp_nn_mse")
+        return loss.value
+
+    def nn_adam(self, w, grad, m, v, step, lr, w_bf16=None):
+        n = w.numel()
+        for t in (grad, m, v):
+            if t.numel() != n or not t.is_cuda:
+                raise ValueError("Adam arrays must be CUDA tensors of equal size")
+        _check(lib().cfp_nn_adam(self._h, n, _ptr(w), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr),
+                                 _ptr(w_bf16)), "cfp_nn_adam")
+
+    def nn_unpack(self, y, inv_scale, u):
+        import torch
+        _check(lib().cfp_nn_unpack(self._h, self._nn(y, "y", torch.float32, 16 * self.N), float(inv_scale),
+                                   self._field(u, "u")), "cfp_nn_unpack")
+        return u
 
     def diag_bounded_wait(self):
         """(status, message) of cfp_diag_bounded_wait: CFP_ECUDA after about one

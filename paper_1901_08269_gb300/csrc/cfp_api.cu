@@ -176,7 +176,7 @@ void cfp_ctx_destroy(cfp_ctx* c) {
     free_ilu(c);
     void* ptrs[] = {c->dcoef64, c->dcoef32, c->dX[0], c->dX[1], c->dX[2], c->dbodies, c->dbound2, c->type, c->slot, c->irr_lin,
                     c->ibi_off, c->ibi_xyz, c->corr_ptr, c->corr_off, c->corr_val, c->corr_val32, c->bib_ptr,
-                    c->bib_idx, c->bib_val, c->krow, c->krow32, c->side_scratch, c->scan_bsum, c->dtotal, c->derr, c->dwait, c->v64, c->v32,
+                    c->bib_idx, c->bib_val, c->krow, c->krow32, c->side_scratch, c->scan_bsum, c->dtotal, c->derr, c->dwait, c->nn_wflip, c->v64, c->v32,
                     c->partial, c->kst, c->hs_f, c->hs_g, c->hs_u, c->hs_gi};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -199,6 +201,7 @@ struct cfp_ctx {
 
     // side-list build scratch (per-slot slices), kept across classifications
     void* side_scratch = nullptr;
+    void* nn_wflip = nullptr;      // learned part: mirrored, transposed weights of a layer
     size_t side_scratch_bytes = 0;
 
     // scan scratch

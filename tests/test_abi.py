@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared():
-    src = open(os.path.join(ROOT, "include", "cfp.h")).read()
+    src = open(os.path.join(ROOT, "include", "cfp.h")).read() + open(os.path.join(ROOT, "include", "cfp_nn.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(cfp_[a-z_0-9]+)\s*\(", src)))
 
