@@ -51,6 +51,11 @@ __global__ void __launch_bounds__(32 * kWarps)
     k_nn_conv(const uint16_t* __restrict__ in, const uint16_t* __restrict__ w, const float* __restrict__ bias,
               const uint16_t* __restrict__ act, int nx, int ny, int nz, uint16_t* __restrict__ out_bf,
               float* __restrict__ out_f) {
+    // the layer's weights, staged once per CTA (16-byte copies)
+    __shared__ __align__(16) uint16_t ws[kC * kTaps * kC];
+    for (int e = threadIdx.x; e < kC * kTaps * kC / 8; e += blockDim.x)
+        reinterpret_cast<uint4*>(ws)[e] = reinterpret_cast<const uint4*>(w)[e];
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int ntx = (nx + 15) / 16;
     const int64_t tile = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -60,6 +65,7 @@ __global__ void __launch_bounds__(32 * kWarps)
     const int g = lane >> 2, q = lane & 3;
     const int x0 = tx * 16;
     float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll 9
     for (int t = 0; t < kTaps; ++t) {
         const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
         const int ys = y + dy, zs = z + dz;
@@ -74,7 +80,7 @@ __global__ void __launch_bounds__(32 * kWarps)
         const uint32_t a2 = va ? ld_pair(pa + 8) : 0u, a3 = vb ? ld_pair(pb + 8) : 0u;
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt) {
-            const uint16_t* pw = w + ((nt * 8 + g) * kTaps + t) * kC + 2 * q;
+            const uint16_t* pw = ws + ((nt * 8 + g) * kTaps + t) * kC + 2 * q;
             mma_bf16(acc[nt], a0, a1, a2, a3, ld_pair(pw), ld_pair(pw + 8));
         }
     }
@@ -123,33 +129,36 @@ __global__ void k_nn_flip(const uint16_t* __restrict__ w, uint16_t* __restrict__
 // dW[co][t][ci] += sum_v dout[v, co] in[v + off(t), ci] for tap t =
 // blockIdx.y: per warp a GEMM with rows co (A = dout^T, 16 x 16 voxels),
 // columns ci (B = the tap's shifted input, 16 voxels x 8, two n-tiles) and
-// k-steps of 16 consecutive voxels; the warp's sums go to dW with atomics.
+// k-steps over the row tiles of the forward kernel (16 consecutive x of one
+// row); the warp's sums go to dW with atomics.
 __global__ void __launch_bounds__(32 * kWarps)
     k_nn_wgrad(const uint16_t* __restrict__ in, const uint16_t* __restrict__ dout, int nx, int ny, int nz,
                float* __restrict__ dw) {
     const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
     const int t = blockIdx.y;
     const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-    const int64_t n = (int64_t)nx * ny * nz;
-    const int64_t steps = (n + 15) / 16;
+    const int ntx = (nx + 15) / 16;
+    const int64_t tiles = (int64_t)ntx * ny * nz;
     float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-    for (int64_t s = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); s < steps; s += (int64_t)gridDim.x * kWarps) {
-        const int64_t v0 = s * 16;
-        // the four voxels of this lane: v0 + 2q + {0, 1, 8, 9}
-        uint16_t d[4][2];      // dout of channels g and g + 8
-        int64_t src[4];        // v + off(t), or -1 outside the grid
+    for (int64_t s = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); s < tiles; s += (int64_t)gridDim.x * kWarps) {
+        const int tx = (int)(s % ntx), row = (int)(s / ntx);
+        const int y = row % ny, z = row / ny;
+        const int ys = y + dy, zs = z + dz;
+        const bool rowin = ys >= 0 && ys < ny && zs >= 0 && zs < nz;
+        const int64_t vrow = ((int64_t)z * ny + y) * nx, srow = ((int64_t)zs * ny + ys) * nx;
+        // the four voxels of this lane: x = 16 tx + 2q + {0, 1, 8, 9}
+        uint16_t d[4][2];  // dout of channels g and g + 8
+        int64_t src[4];    // v + off(t), or -1 outside the grid
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int64_t v = v0 + 2 * q + (u & 1) + 8 * (u >> 1);
+            const int x = 16 * tx + 2 * q + (u & 1) + 8 * (u >> 1);
             src[u] = -1;
             d[u][0] = d[u][1] = 0;
-            if (v < n) {
+            if (x < nx) {
+                const int64_t v = vrow + x;
                 d[u][0] = dout[v * kC + g];
                 d[u][1] = dout[v * kC + g + 8];
-                const int x = (int)(v % nx), yy = (int)((v / nx) % ny), zz = (int)(v / ((int64_t)nx * ny));
-                const int xs = x + dx, ys = yy + dy, zs = zz + dz;
-                if (xs >= 0 && xs < nx && ys >= 0 && ys < ny && zs >= 0 && zs < nz)
-                    src[u] = ((int64_t)zs * ny + ys) * nx + xs;
+                if (rowin && x + dx >= 0 && x + dx < nx) src[u] = srow + x + dx;
             }
         }
         const uint32_t a0 = pack2(d[0][0], d[1][0]), a1 = pack2(d[0][1], d[1][1]);
@@ -330,8 +339,8 @@ cfp_status cfp_nn_conv3d_dgrad(cfp_ctx* c, const uint16_t* dout, const uint16_t*
 cfp_status cfp_nn_conv3d_wgrad(cfp_ctx* c, const uint16_t* in, const uint16_t* dout, float* dw, float* db) {
     if (!c) return fail(CFP_EINVAL, "null context");
     if (!in || !dout || !dw) return fail(CFP_EINVAL, "in, dout and dw are required");
-    const int64_t steps = (c->N + 15) / 16;
-    const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((steps + kWarps - 1) / kWarps, 152 * 2)), kTaps);
+    const int64_t tiles = (int64_t)((c->n[0] + 15) / 16) * c->n[1] * c->n[2];
+    const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((tiles + kWarps - 1) / kWarps, 152 * 2)), kTaps);
     k_nn_wgrad<<<grid, 32 * kWarps, 0, c->stream>>>(in, dout, c->n[0], c->n[1], c->n[2], dw);
     c->launches += 1;
     if (db) {

@@ -13,6 +13,39 @@ import argparse
 import json
 
 
+def nn_time(ctx, name, reps):
+    """One 16 -> 16 channel 3x3x3 layer of the learned part on the context's
+    grid (random BF16 input and weights): event-timed mean of reps launches
+    after two untimed ones; FLOP counted as 2 * 16 * 27 * 16 per node."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(0)
+    n = ctx.N
+    x = torch.randn(n * 16, generator=g, device="cuda").to(torch.bfloat16)
+    dy = torch.randn(n * 16, generator=g, device="cuda").to(torch.bfloat16)
+    w = (0.1 * torch.randn(16 * 27 * 16, generator=g, device="cuda")).to(torch.bfloat16)
+    out = torch.empty(n * 16, dtype=torch.bfloat16, device="cuda")
+    dw = torch.zeros(16 * 27 * 16, dtype=torch.float32, device="cuda")
+
+    def run():
+        if name == "nn_conv":
+            ctx.nn_conv3d(x, w, None, 1, out)
+        else:
+            ctx.nn_wgrad(x, dy, dw)
+
+    for _ in range(2):
+        run()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flop = 2.0 * 16 * 27 * 16 * n
+    return {"ms": ms, "flop": flop, "TFLOPs": flop / ms / 1e9}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=385)
@@ -33,6 +66,9 @@ def main():
            "update": cfp.KERNEL_UPDATE}
     out = {"n": a.n, "precision": a.precision}
     for name in a.kernels.split(","):
+        if name in ("nn_conv", "nn_wgrad"):
+            out[name] = nn_time(ctx, name, a.reps)
+            continue
         ms, by = ctx.time_kernel(ids[name], prec, reps=a.reps)
         out[name] = {"ms": ms, "bytes": by, "GBps": by / ms / 1e6}
     ctx.close()
