@@ -55,3 +55,16 @@ def test_create_rejects_bad_grids_without_a_device():
     st = L.cfp_ctx_create(None, 4, None, 4, None, 4, arr, 0, 0, None, None)
     assert st == cfp.EINVAL
     assert L.cfp_classify_points(None, None, None, None) == cfp.EINVAL
+
+
+def test_learned_part_rejects_a_null_context_without_a_device():
+    L = cfp.lib()
+    e = cfp.EINVAL
+    assert L.cfp_nn_pack(None, None, None, 1.0, 1.0, None, None, None, None) == e
+    assert L.cfp_nn_conv3d(None, None, None, None, 0, None, None) == e
+    assert L.cfp_nn_conv3d_dgrad(None, None, None, None, None) == e
+    assert L.cfp_nn_conv3d_wgrad(None, None, None, None, None) == e
+    assert L.cfp_nn_mse(None, None, None, None, 1.0, None, None) == e
+    assert L.cfp_nn_adam(None, 1, None, None, None, None, 1, 1e-3, None) == e
+    assert L.cfp_nn_unpack(None, None, 1.0, None) == e
+    assert "context" in cfp.last_error()
