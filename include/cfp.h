@@ -346,6 +346,15 @@ cfp_status cfp_time_kernel(cfp_ctx* ctx, int kernel, int precision, int reps,
                            double* ms_per_launch, double* bytes_per_launch);
 
 /*
+ * FP64 vector helpers over all N nodes of two fields, for outer iterations
+ * built on this interface (the learned part's flexible Krylov method):
+ * *out_host = sum a[l] b[l] (synchronises); y = alpha x + beta y (x and y
+ * may be the same field).  Errors: CFP_EINVAL.
+ */
+cfp_status cfp_vec_dot(cfp_ctx* ctx, const double* a_dev, const double* b_dev, double* out_host);
+cfp_status cfp_vec_axpby(cfp_ctx* ctx, double alpha, const double* x_dev, double beta, double* y_dev);
+
+/*
  * Diagnostic of the bounded waits of the TMA-fed smoother: launches one CTA
  * that waits on an mbarrier phase that nothing completes, with the same
  * one-second bound as the smoother's pipeline waits.  The wait gives up,

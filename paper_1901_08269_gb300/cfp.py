@@ -53,7 +53,8 @@ EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_dest
            "cfp_ibi_points", "cfp_assemble_rhs", "cfp_apply", "cfp_precondition", "cfp_solve", "cfp_solve_host",
            "cfp_time_kernel", "cfp_launch_count", "cfp_assemble_rhs_noalloc", "cfp_precondition_ex",
            "cfp_solve_batch", "cfp_autotune", "cfp_diag_bounded_wait", "cfp_nn_pack", "cfp_nn_conv3d",
-           "cfp_nn_conv3d_dgrad", "cfp_nn_conv3d_wgrad", "cfp_nn_mse", "cfp_nn_adam", "cfp_nn_unpack"]
+           "cfp_nn_conv3d_dgrad", "cfp_nn_conv3d_wgrad", "cfp_nn_mse", "cfp_nn_adam", "cfp_nn_unpack",
+           "cfp_vec_dot", "cfp_vec_axpby"]
 KERNEL_APPLY, KERNEL_RBGS, KERNEL_UPDATE, KERNEL_MG_SWEEP = 0, 1, 2, 3
 
 
@@ -97,6 +98,8 @@ def lib(build_if_missing=True):
         L.cfp_nn_mse.argtypes = [_P, _P, _P, _P, C.c_double, _P, _D]
         L.cfp_nn_adam.argtypes = [_P, C.c_int64, _P, _P, _P, _P, C.c_int, C.c_double, _P]
         L.cfp_nn_unpack.argtypes = [_P, _P, C.c_double, _P]
+        L.cfp_vec_dot.argtypes = [_P, _P, _P, _D]
+        L.cfp_vec_axpby.argtypes = [_P, C.c_double, _P, C.c_double, _P]
         for name in EXPORTS[2:]:
             if name not in ("cfp_ctx_destroy", "cfp_launch_count"):
                 getattr(L, name).restype = C.c_int
@@ -249,6 +252,16 @@ class Context:
         _check(lib().cfp_nn_unpack(self._h, self._nn(y, "y", torch.float32, 16 * self.N), float(inv_scale),
                                    self._field(u, "u")), "cfp_nn_unpack")
         return u
+
+    def vec_dot(self, a, b):
+        out = C.c_double()
+        _check(lib().cfp_vec_dot(self._h, self._field(a, "a"), self._field(b, "b"), C.byref(out)), "cfp_vec_dot")
+        return out.value
+
+    def vec_axpby(self, alpha, x, beta, y):
+        _check(lib().cfp_vec_axpby(self._h, float(alpha), self._field(x, "x"), float(beta), self._field(y, "y")),
+               "cfp_vec_axpby")
+        return y
 
     def diag_bounded_wait(self):
         """(status, message) of cfp_diag_bounded_wait: CFP_ECUDA after about one

@@ -337,6 +337,21 @@ cfp_status cfp_time_kernel(cfp_ctx* c, int kernel, int precision, int reps, doub
     return time_kernel(c, kernel, precision, reps, ms, bytes);
 }
 
+cfp_status cfp_vec_dot(cfp_ctx* c, const double* a, const double* b, double* out) {
+    if (!c) return fail(CFP_EINVAL, "null context");
+    if (!out) return fail(CFP_EINVAL, "NULL output");
+    CFP_TRY(need_field(a, "a_dev"));
+    CFP_TRY(need_field(b, "b_dev"));
+    return vec_dot(c, a, b, out);
+}
+
+cfp_status cfp_vec_axpby(cfp_ctx* c, double alpha, const double* x, double beta, double* y) {
+    if (!c) return fail(CFP_EINVAL, "null context");
+    CFP_TRY(need_field(x, "x_dev"));
+    CFP_TRY(need_field(y, "y_dev"));
+    return vec_axpby(c, alpha, x, beta, y);
+}
+
 cfp_status cfp_diag_bounded_wait(cfp_ctx* c) {
     if (!c) return fail(CFP_EINVAL, "null context");
     return diag_bounded_wait(c);

@@ -316,5 +316,8 @@ int mg_key(const cfp_ctx* c);
 cfp_status check_waits(cfp_ctx* c);
 // one CTA whose bounded mbarrier wait runs out (code 5), then check_waits
 cfp_status diag_bounded_wait(cfp_ctx* c);
+// FP64 vector helpers over all N nodes: dot (synchronises), y = alpha x + beta y
+cfp_status vec_dot(cfp_ctx* c, const double* a, const double* b, double* out);
+cfp_status vec_axpby(cfp_ctx* c, double alpha, const double* x, double beta, double* y);
 
 }  // namespace cfp

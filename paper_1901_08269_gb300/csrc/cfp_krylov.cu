@@ -393,6 +393,34 @@ cfp_status status_of(int flag) {
 
 }  // namespace
 
+// y = alpha x + beta y over all nodes (FP64)
+__global__ void k_axpby(double alpha, const double* __restrict__ x, double beta, double* __restrict__ y, int64_t N) {
+    GRID_STRIDE(l, N) y[l] = alpha * x[l] + beta * y[l];
+}
+
+cfp_status ensure_partial(cfp_ctx* c) {
+    const int64_t need = 2 * (int64_t)std::max(apply_blocks(c), kUpdBlocks);
+    if (c->partial_cap < need) {
+        if (c->partial) cudaFree(c->partial);
+        c->partial = nullptr;
+        CFP_CUDA(cudaMalloc(&c->partial, sizeof(double) * need));
+        c->partial_cap = need;
+    }
+    return CFP_OK;
+}
+
+cfp_status vec_dot(cfp_ctx* c, const double* a, const double* b, double* out) {
+    CFP_TRY(ensure_partial(c));
+    return dot_host(c, a, b, out);
+}
+
+cfp_status vec_axpby(cfp_ctx* c, double alpha, const double* x, double beta, double* y) {
+    k_axpby<<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(alpha, x, beta, y, c->N);
+    c->launches += 1;
+    CFP_CUDA(cudaGetLastError());
+    return CFP_OK;
+}
+
 cfp_status ensure_work(cfp_ctx* c, bool need32) {
     const int64_t N = c->N;
     if (!c->v64) {
@@ -403,14 +431,7 @@ cfp_status ensure_work(cfp_ctx* c, bool need32) {
         CFP_CUDA(cudaMalloc(&c->v32, sizeof(float) * N * (kNV32 + 1)));  // + the FP32 right-hand side
         CFP_CUDA(cudaMemsetAsync(c->v32, 0, sizeof(float) * N * (kNV32 + 1), c->stream));
     }
-    const int64_t need = 2 * (int64_t)std::max(apply_blocks(c), kUpdBlocks);
-    if (c->partial_cap < need) {
-        if (c->partial) cudaFree(c->partial);
-        c->partial = nullptr;
-        CFP_CUDA(cudaMalloc(&c->partial, sizeof(double) * need));
-        c->partial_cap = need;
-    }
-    return CFP_OK;
+    return ensure_partial(c);
 }
 
 namespace {

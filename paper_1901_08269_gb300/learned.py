@@ -138,3 +138,95 @@ def train(net, samples, steps, lr=2e-3, log_every=0):
         if log_every and s % log_every == 0:
             print("step %d loss %.4e" % (s, loss))
     return losses
+
+
+def mg_precond(ctx, opts):
+    """z = one multigrid V-cycle on K applied to v (a fixed linear map)."""
+    def apply(v, z):
+        ctx.precondition_ex(v, z, opts=opts)
+    return apply
+
+
+def net_mg_precond(ctx, net, opts, net_steps=1):
+    """For the first net_steps directions of a solve z = z1 + V(v - B z1), z1
+    the network's prediction of B^-1 v (its guess corrected by one multigrid
+    V-cycle on its residual); afterwards the V-cycle alone.  The network is
+    trained on right-hand sides, which the first direction of a solve from
+    x0 = 0 is; the later directions are oscillatory, where its output means
+    nothing.  A preconditioner that changes between steps and is not linear:
+    it needs a flexible Krylov method."""
+    z1 = torch.empty(ctx.N, dtype=torch.float64, device="cuda")
+    r = torch.empty(ctx.N, dtype=torch.float64, device="cuda")
+    calls = [0]
+
+    def apply(v, z):
+        calls[0] += 1
+        if calls[0] > net_steps:
+            ctx.precondition_ex(v, z, opts=opts)
+            return
+        net.guess(ctx, v, z1)
+        ctx.apply(z1, r)
+        ctx.vec_axpby(1.0, v, -1.0, r)
+        ctx.precondition_ex(r, z, opts=opts)
+        ctx.vec_axpby(1.0, z1, 1.0, z)
+    return apply
+
+
+def fgmres(ctx, b, x, precond, m=30, tol=1e-10, maxit=300):
+    """Right-preconditioned flexible GMRES(m) (Saad, SIAM J. Sci. Comput. 14,
+    1993) for B x = b on the unknowns, x holding the initial guess (zero off
+    the unknowns, as b is).  precond(v, z) may change between iterations; the
+    search directions z_j are kept and x += Z y.  Vector work runs in the
+    library's kernels (apply, dot, axpby), the (m+1) x m least-squares problem
+    with Givens rotations on the host.  Returns (iterations, relative
+    residual ||b - B x|| / ||b||, recomputed)."""
+    import math
+
+    import numpy as np
+    n = ctx.N
+    V = [torch.zeros(n, dtype=torch.float64, device=b.device) for _ in range(m + 1)]
+    Z = [torch.zeros(n, dtype=torch.float64, device=b.device) for _ in range(m)]
+    w = torch.zeros(n, dtype=torch.float64, device=b.device)
+    bnorm = math.sqrt(ctx.vec_dot(b, b))
+    its = 0
+
+    def residual():
+        ctx.apply(x, w)
+        ctx.vec_axpby(1.0, b, -1.0, w)
+        return math.sqrt(ctx.vec_dot(w, w))
+
+    beta = residual()
+    while beta > tol * bnorm and its < maxit:
+        ctx.vec_axpby(1.0 / beta, w, 0.0, V[0])
+        H = np.zeros((m + 1, m))
+        cs, sn, g = np.zeros(m), np.zeros(m), np.zeros(m + 1)
+        g[0] = beta
+        k = 0
+        for j in range(m):
+            precond(V[j], Z[j])
+            ctx.apply(Z[j], w)
+            for i in range(j + 1):  # modified Gram-Schmidt
+                H[i, j] = ctx.vec_dot(w, V[i])
+                ctx.vec_axpby(-H[i, j], V[i], 1.0, w)
+            H[j + 1, j] = math.sqrt(ctx.vec_dot(w, w))
+            if H[j + 1, j] > 0.0:
+                ctx.vec_axpby(1.0 / H[j + 1, j], w, 0.0, V[j + 1])
+            for i in range(j):  # the earlier rotations
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            d = math.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / d, H[j + 1, j] / d
+            H[j, j], H[j + 1, j] = d, 0.0
+            g[j + 1], g[j] = -sn[j] * g[j], cs[j] * g[j]
+            its += 1
+            k = j + 1
+            if abs(g[j + 1]) <= tol * bnorm or its >= maxit:
+                break
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):  # back substitution in the rotated Hessenberg matrix
+            y[i] = (g[i] - np.dot(H[i, i + 1:k], y[i + 1:k])) / H[i, i]
+        for i in range(k):
+            ctx.vec_axpby(float(y[i]), Z[i], 1.0, x)
+        beta = residual()
+    return its, beta / bnorm

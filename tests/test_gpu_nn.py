@@ -148,14 +148,21 @@ def test_pack_scale_and_unpack():
     c.close()
 
 
-def test_training_on_solver_pairs_and_the_guess_it_gives():
-    """Train on solver-generated pairs (random bodies at 33^3), then on
-    held-out problems compare the network's initial guess with zero: its
-    error and the iterations of the same solve from it."""
+@pytest.fixture(scope="module")
+def trained():
+    """The network trained on solver-generated pairs (random bodies at 33^3)."""
     train_w = [W.random_problem(s, sizes=(33,)) for s in range(6)]
     samples, escale = learned.make_samples(train_w)
     net = learned.ConvNet(seed=0, escale=escale)
     losses = learned.train(net, samples, 600, lr=2e-3)
+    return net, losses
+
+
+def test_training_on_solver_pairs_and_the_guess_it_gives(trained):
+    """Training lowers the loss; on held-out problems compare the network's
+    initial guess with zero: its error and the iterations of the same solve
+    from it."""
+    net, losses = trained
     first, last = float(np.mean(losses[:6])), float(np.mean(losses[-30:]))
     assert np.isfinite(last) and last < 0.5 * first, (first, last)
     report = []
@@ -177,3 +184,24 @@ def test_training_on_solver_pairs_and_the_guess_it_gives():
     print("learned initial guess: loss %.3e -> %.3e; held-out (seed, error ratio, iterations): %s"
           % (first, last, report))
     assert all(r[1] < 1.0 for r in report), report
+
+
+def test_network_as_preconditioner_in_flexible_gmres(trained):
+    """FGMRES whose first direction comes from the network (z = net(v) +
+    V(v - B net(v)), the V-cycle V alone afterwards) against FGMRES with the
+    V-cycle alone; both reach the solution of the plain BiCGSTAB solve (the
+    judge) on a held-out problem."""
+    net, _ = trained
+    w = W.random_problem(100, sizes=(33,))
+    smp = learned.Sample(w, tol=1e-12)
+    ctx = smp.ctx
+    ref = smp.u.cpu().numpy()
+    opts = cfp.default_opts(precond=cfp.PRECOND_MG, mg_smooth=2)
+    its = {}
+    for name, prec in (("mg", learned.mg_precond(ctx, opts)), ("net+mg", learned.net_mg_precond(ctx, net, opts))):
+        x = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+        n_it, rel = learned.fgmres(ctx, smp.rhs, x, prec, m=30, tol=1e-11, maxit=200)
+        assert rel <= 1e-11, (name, rel)
+        assert np.max(np.abs(x.cpu().numpy() - ref)) <= 1e-6 * np.max(np.abs(ref)), name
+        its[name] = n_it
+    print("FGMRES iterations to 1e-11:", its)
