@@ -1,7 +1,7 @@
 // Internal declarations of the CUDA library behind include/cfp.h.
 #pragma once
 
-#include <cuda.h>  // CUtensorMap (types only; the encoder is fetched from the driver at run time)
+#include <cuda.h>  // CUtensorMap (types only; the encoder is fetched from the CUDA driver at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 

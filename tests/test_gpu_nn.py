@@ -190,7 +190,7 @@ def test_network_as_preconditioner_in_flexible_gmres(trained):
     """FGMRES whose first direction comes from the network (z = net(v) +
     V(v - B net(v)), the V-cycle V alone afterwards) against FGMRES with the
     V-cycle alone; both reach the solution of the plain BiCGSTAB solve (the
-    judge) on a held-out problem."""
+    reference) on a held-out problem."""
     net, _ = trained
     w = W.random_problem(100, sizes=(33,))
     smp = learned.Sample(w, tol=1e-12)
