@@ -44,7 +44,9 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 // Convolution of (N, 16) BF16 into (N, 16): the GEMM rows are the warp's 16
 // voxels, the columns the 16 output channels (two n-tiles of 8), the k-steps
 // the 27 taps of 16 input channels.  Lane (g = lane / 4, q = lane % 4) holds
-// the voxel rows g and g + 8 and the channel pairs 2q and 2q + 8.
+// the voxel rows g and g + 8 and the channel pairs 2q and 2q + 8.  The
+// layer's weights are staged in shared memory once per CTA; the tap loop is
+// unrolled so the gathers of several taps are in flight together.
 // Epilogue: + bias, ReLU, or (dgrad) multiplication by [act > 0].
 template <bool RELU, bool OUT_F32>
 __global__ void __launch_bounds__(32 * kWarps)
@@ -310,12 +312,15 @@ cfp_status cfp_nn_conv3d(cfp_ctx* c, const uint16_t* in, const uint16_t* w, cons
     if (!c) return fail(CFP_EINVAL, "null context");
     if (!in || !w || (!out_bf16 == !out_f32)) return fail(CFP_EINVAL, "in, w and exactly one output are required");
     const unsigned nb = conv_blocks(c);
+    const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
+    cudaStream_t s = c->stream;
     if (out_f32) {
-        if (relu) k_nn_conv<true, true><<<nb, 32 * kWarps, 0, c->stream>>>(in, w, bias, nullptr, c->n[0], c->n[1], c->n[2], nullptr, out_f32);
-        else k_nn_conv<false, true><<<nb, 32 * kWarps, 0, c->stream>>>(in, w, bias, nullptr, c->n[0], c->n[1], c->n[2], nullptr, out_f32);
+        if (relu) k_nn_conv<true, true><<<nb, 32 * kWarps, 0, s>>>(in, w, bias, nullptr, nx, ny, nz, nullptr, out_f32);
+        else k_nn_conv<false, true><<<nb, 32 * kWarps, 0, s>>>(in, w, bias, nullptr, nx, ny, nz, nullptr, out_f32);
     } else {
-        if (relu) k_nn_conv<true, false><<<nb, 32 * kWarps, 0, c->stream>>>(in, w, bias, nullptr, c->n[0], c->n[1], c->n[2], out_bf16, nullptr);
-        else k_nn_conv<false, false><<<nb, 32 * kWarps, 0, c->stream>>>(in, w, bias, nullptr, c->n[0], c->n[1], c->n[2], out_bf16, nullptr);
+        if (relu)
+            k_nn_conv<true, false><<<nb, 32 * kWarps, 0, s>>>(in, w, bias, nullptr, nx, ny, nz, out_bf16, nullptr);
+        else k_nn_conv<false, false><<<nb, 32 * kWarps, 0, s>>>(in, w, bias, nullptr, nx, ny, nz, out_bf16, nullptr);
     }
     c->launches += 1;
     CFP_CUDA(cudaGetLastError());
