@@ -57,14 +57,24 @@ def parse():
                     help="plain launches instead of the CUDA graph (ncu cannot profile kernel nodes of graphs "
                          "with conditional nodes)")
     ap.add_argument("--no-fp64-check", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--fp64-steps", type=int, default=5,
+                    help="timed steps of the FP64 comparison solve (at most --steps; about 3 s each at 513^3)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--oracle-n", type=int, default=129)
     ap.add_argument("--oracle-iters", type=int, default=10)
+    ap.add_argument("--oracle-large", type=int, default=0,
+                    help="nodes per axis of the larger oracle sample (0: 2 * --oracle-n - 1); config 3's "
+                         "geometry needs at least 129")
     ap.add_argument("--workload", default="config3", choices=["config3", "batch"],
                     help="config3: the 513^3 two-body solve (default); batch: 64 random problems of uneven "
                          "size solved together")
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--kernels", default=None,
+                    help="time single kernels instead of the solve: a comma list of mg_sweep, rbgs, apply, "
+                         "update, nn_conv, nn_wgrad on the config-3 geometry at --n^3 (--reps launches each); "
+                         "few launches, so it is the command the ncu captures of those kernels run")
+    ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=20261203)
     return ap.parse_args()
 
@@ -148,14 +158,11 @@ def hbm_peak():
 
 
 # ----------------------------------------------------------- CPU baseline
-def oracle_sample(n_sample, iters, n_full, iters_full):
+def oracle_sample(n_sample, iters):
     """Time the CPU oracle on a bounded sample of the workload: the same
     geometry and solution on an n_sample^3 grid, set-up (classification, IBI,
-    explicit CSR assembly, right-hand side) plus `iters` BiCGSTAB iterations.
-    Extrapolated to an n_full^3 solve of `iters_full` iterations by the node
-    count ratio."""
-    import numpy as np
-
+    explicit CSR assembly, right-hand side) plus `iters` BiCGSTAB iterations
+    with its 8-sweep red-black preconditioner."""
     from oracle import pyoracle as O
     from paper_1901_08269_gb300 import workloads as W
     w = W.config3(n_sample)
@@ -169,33 +176,131 @@ def oracle_sample(n_sample, iters, n_full, iters_full):
     t1 = time.perf_counter()
     x, st, it, rel = P.bicgstab(rhs, tol=1e-30, maxit=iters, sweeps=8)
     t2 = time.perf_counter()
-    ratio = (n_full / n_sample) ** 3
-    t_iter = (t2 - t1) / max(it, 1)
-    est = ((t1 - t0) + t_iter * iters_full) * ratio
-    return {"est_s_per_solve": est, "setup_s": t1 - t0, "iter_s": t_iter, "iters": it, "cores": O.threads(),
-            "wall_s": t2 - t0}
+    return {"n": n_sample, "setup_s": t1 - t0, "iter_s": (t2 - t1) / max(it, 1), "iters": it,
+            "cores": O.threads(), "wall_s": t2 - t0}
+
+
+def oracle_extrapolate(small, large, n_full, iters_full):
+    """A 513^3 solve of iters_full iterations from two measured samples: the
+    set-up and the per-iteration time of the larger sample, scaled to n_full^3
+    nodes with the exponents measured between the two samples (time ~
+    nodes^p; p = 1 is linear)."""
+    import math as m
+    ratio = (small["n"] / large["n"]) ** 3
+    p_it = m.log(small["iter_s"] / large["iter_s"]) / m.log(ratio)
+    p_su = m.log(small["setup_s"] / large["setup_s"]) / m.log(ratio)
+    scale = (n_full / large["n"]) ** 3
+    it_full = large["iter_s"] * scale ** p_it
+    su_full = large["setup_s"] * scale ** p_su
+    return {"est_s_per_solve": su_full + iters_full * it_full, "iter_s_full": it_full, "setup_s_full": su_full,
+            "p_iter": p_it, "p_setup": p_su}
+
+
+def oracle_text(small, large, est, n_full, iters_full):
+    return ("oracle (plain C, FP64, explicit CSR, OpenMP, %d threads) on the config-3 geometry, measured: "
+            "%d^3 set-up %.2f s + %.3f s/iteration, %d^3 set-up %.2f s + %.3f s/iteration (%d BiCGSTAB "
+            "iterations each, 8-sweep red-black preconditioner); time grows as nodes^%.2f per iteration and "
+            "nodes^%.2f for the set-up between the two, so a %d^3 FP64 solve of %d iterations (the count the "
+            "same preconditioner needs on the GPU) is estimated at %.0f s (set-up %.0f s, %.2f s/iteration)"
+            % (large["cores"], small["n"], small["setup_s"], small["iter_s"], large["n"], large["setup_s"],
+               large["iter_s"], large["iters"], est["p_iter"], est["p_setup"], n_full, iters_full,
+               est["est_s_per_solve"], est["setup_s_full"], est["iter_s_full"]))
 
 
 def reference_arm(args):
+    """The oracle as it stands on the host cores.  Calibration (untimed): one
+    sample at --oracle-large nodes per axis for the growth exponents; each
+    step then times the --oracle-n sample and extrapolates it."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    vals = []
+    n_large = args.oracle_large or 2 * args.oracle_n - 1
+    large = oracle_sample(n_large, args.oracle_iters)
+    vals, walls = [], []
     for s in range(args.warmup + args.steps):
-        r = oracle_sample(args.oracle_n, args.oracle_iters, args.n, FP64_RBGS_ITERS_513)
+        small = oracle_sample(args.oracle_n, args.oracle_iters)
         if s >= args.warmup:
-            vals.append(r["est_s_per_solve"])
+            # this step's own small sample, scaled to the large one with the
+            # calibration's exponents, then to the full size
+            cal = oracle_extrapolate(small, large, args.n, FP64_RBGS_ITERS_513)
+            vals.append(cal["est_s_per_solve"])
+            walls.append(small["wall_s"])
     v = statistics.mean(vals)
-    sample = ("oracle (plain C, FP64, CSR) on config-3 geometry at %d^3: set-up + %d BiCGSTAB iterations, "
-              "extrapolated to a %d^3 solve of %d iterations by the node-count ratio" %
-              (args.oracle_n, r["iters"], args.n, FP64_RBGS_ITERS_513))
+    sample = oracle_text(small, large, cal, args.n, FP64_RBGS_ITERS_513)
+    sample += "; each timed step is the %d^3 sample (%.2f s wall on average), extrapolated" % (
+        args.oracle_n, statistics.mean(walls))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(args, 1), precision="fp64", precond="rbgs", sweeps=8),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": sample},
+            "value_kind": "extrapolated from measured samples",
+            "sample_wall_s_per_step": statistics.mean(walls),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": large["cores"], "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ kernel mode
+def nn_time(ctx, name, reps):
+    """One 16 -> 16 channel 3x3x3 layer of the learned part on the context's
+    grid (random BF16 input and weights): event-timed mean of reps launches
+    after two untimed ones; FLOP counted as 2 * 16 * 27 * 16 per node."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(0)
+    n = ctx.N
+    x = torch.randn(n * 16, generator=g, device="cuda").to(torch.bfloat16)
+    dy = torch.randn(n * 16, generator=g, device="cuda").to(torch.bfloat16)
+    w = (0.1 * torch.randn(16 * 27 * 16, generator=g, device="cuda")).to(torch.bfloat16)
+    out = torch.empty(n * 16, dtype=torch.bfloat16, device="cuda")
+    dw = torch.zeros(16 * 27 * 16, dtype=torch.float32, device="cuda")
+
+    def run():
+        if name == "nn_conv":
+            ctx.nn_conv3d(x, w, None, 1, out)
+        else:
+            ctx.nn_wgrad(x, dy, dw)
+
+    for _ in range(2):
+        run()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flop = 2.0 * 16 * 27 * 16 * n
+    return {"ms": ms, "flop": flop, "TFLOPs": flop / ms / 1e9}
+
+
+def kernel_arm(args):
+    """Single kernels of the solve, event-timed through cfp_time_kernel on
+    the config-3 geometry at n^3 (classification first): the red-black
+    half-sweep on the fine level's split arrays (the multigrid smoother's and
+    the plain inner iterations' kernel), the apply with its fused dot, the
+    x/r update, and the learned part's convolution layers."""
+    import torch
+
+    from paper_1901_08269_gb300 import cfp
+    from paper_1901_08269_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    w = W.config3(args.n)
+    ctx = cfp.Context(w.x, w.y, w.z, w.bodies)
+    ctx.classify_points()
+    prec = cfp.PREC_MIXED if args.precision == "mixed" else cfp.PREC_FP64
+    ids = {"rbgs": cfp.KERNEL_RBGS, "mg_sweep": cfp.KERNEL_MG_SWEEP, "apply": cfp.KERNEL_APPLY,
+           "update": cfp.KERNEL_UPDATE}
+    out = {"mode": "kernels", "n": args.n, "precision": args.precision, "reps": args.reps}
+    for name in args.kernels.split(","):
+        if name in ("nn_conv", "nn_wgrad"):
+            out[name] = nn_time(ctx, name, args.reps)
+            continue
+        ms, by = ctx.time_kernel(ids[name], prec, reps=args.reps)
+        out[name] = {"ms": ms, "bytes": by, "GBps": by / ms / 1e6}
+    ctx.close()
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -304,6 +409,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.kernels:
+        return kernel_arm(args)
     if args.workload == "batch":
         return batch_arm(args)
 
@@ -382,18 +489,30 @@ def main():
 
     fp64 = None
     if not args.no_fp64_check:
+        # the plain FP64 solve of the same step (classification + solve), one
+        # untimed run (it builds the FP64 graph), then the mean of fp64_steps
         u64 = torch.zeros_like(u)
-        ctx.classify_points()
+        k64 = max(1, min(args.steps, args.fp64_steps))
+
+        def step64():
+            ctx.classify_points()
+            u64.zero_()
+            return ctx.solve(f, g, gi, u64, tol=args.tol, precision=cfp.PREC_FP64, sweeps=args.sweeps,
+                             precond=pc, mg_smooth=args.mg_smooth, mg_post=args.mg_post)
+
+        step64()
+        torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        i64 = ctx.solve(f, g, gi, u64, tol=args.tol, precision=cfp.PREC_FP64, sweeps=args.sweeps, precond=pc,
-                        mg_smooth=args.mg_smooth, mg_post=args.mg_post)
+        for _ in range(k64):
+            i64 = step64()
         b.record(stream)
         torch.cuda.synchronize()
         e64 = float((u64 - ue).abs()[fluid].max())
-        fp64 = {"s_per_solve": a.elapsed_time(b) / 1000.0, "max_err": e64, "iterations": i64.iterations,
-                "err_ratio_vs_fp64": err / e64 if e64 > 0 else None, "equal_error": err <= 1.02 * e64,
-                "max_diff_vs_fp64": float((u - u64).abs().max())}
+        fp64 = {"s_per_solve": a.elapsed_time(b) / 1000.0 / k64, "steps": k64, "max_err": e64,
+                "iterations": i64.iterations, "err_ratio_vs_fp64": err / e64 if e64 > 0 else None,
+                "equal_error": err <= 1.02 * e64, "max_diff_vs_fp64": float((u - u64).abs().max()),
+                "speedup_mixed_vs_fp64": (a.elapsed_time(b) / 1000.0 / k64) / value}
         del u64
 
     # roofline of the dominant kernel: a red-black half-sweep of the
@@ -434,27 +553,32 @@ def main():
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         # one untimed call: the first allocates the context's device copies of the host buffers
         ctx.solve_host(hf, hg, hgi, hu, tol=args.tol, opts=opts)
-        hu.zero_()  # the step's initial guess, prepared in host memory like f and g
         torch.cuda.synchronize()
+        # each step: the initial guess prepared in host memory like f and g,
+        # classification, copies in, solve, copy of u out (all inside the
+        # events' span), averaged over the same steps as the headline
         a.record(stream)
-        ctx.classify_points()
-        ctx.solve_host(hf, hg, hgi, hu, tol=args.tol, opts=opts)
+        for _ in range(args.steps):
+            hu.zero_()
+            ctx.classify_points()
+            ctx.solve_host(hf, hg, hgi, hu, tol=args.tol, opts=opts)
         b.record(stream)
         torch.cuda.synchronize()
-        es = a.elapsed_time(b) / 1000.0
+        es = a.elapsed_time(b) / 1000.0 / args.steps
         h2d = (hf.numel() + hg.numel() + hu.numel() + hgi.numel()) * 8
-        e2e = {"value": es / world, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": hu.numel() * 8}
+        e2e = {"value": es / world, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": hu.numel() * 8,
+               "steps": args.steps}
         del hf, hg, hgi, hu
 
     cpu = None
     if rank == 0 and not args.no_cpu:
         iters_full = FP64_RBGS_ITERS_513
-        r = oracle_sample(args.oracle_n, args.oracle_iters, args.n, iters_full)
-        cpu = {"value": r["est_s_per_solve"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-               "sample": "oracle (plain C, FP64, CSR, OpenMP) on the same geometry at %d^3: set-up + %d "
-                         "BiCGSTAB iterations with its 8-sweep red-black preconditioner (%.1f s wall), extrapolated "
-                         "to a %d^3 FP64 solve of %d iterations (the count the same preconditioner needs on the GPU) "
-                         "by the node-count ratio" % (args.oracle_n, r["iters"], r["wall_s"], args.n, iters_full)}
+        small = oracle_sample(args.oracle_n, args.oracle_iters)
+        large = oracle_sample(args.oracle_large or 2 * args.oracle_n - 1, args.oracle_iters)
+        est = oracle_extrapolate(small, large, args.n, iters_full)
+        cpu = {"value": est["est_s_per_solve"], "unit": UNIT, "cores": large["cores"], "kind": "oracle",
+               "sample": oracle_text(small, large, est, args.n, iters_full),
+               "measured": {"n%d" % small["n"]: small, "n%d" % large["n"]: large}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -614,6 +614,22 @@ static int k_row(cfo_problem* p, int i, int j, int k, rowacc_t* row, rowacc_t* r
     return CFO_OK;
 }
 
+/* Regular row at (i,j,k), Eq. As_qs: the coefficient of u at offset
+ * (o,q,r) is Rx Ly Lz + Lx Ry Lz + Lx Ly Rz of the centre's coefficients;
+ * the 27 entries in the order r (z), q (y), o (x). */
+static void regular_row(const cfo_problem* p, int i, int j, int k, rowacc_t* row) {
+    for (int r = -1; r <= 1; ++r)
+        for (int q = -1; q <= 1; ++q)
+            for (int o = -1; o <= 1; ++o) {
+                double v = Rco(p, 0, i, o) * Lco(p, 1, j, q) * Lco(p, 2, k, r) +
+                           Lco(p, 0, i, o) * Rco(p, 1, j, q) * Lco(p, 2, k, r) +
+                           Lco(p, 0, i, o) * Lco(p, 1, j, q) * Rco(p, 2, k, r);
+                row->col[row->n] = LIN(p, i + o, j + q, k + r);
+                row->val[row->n] = v;
+                row->n++;
+            }
+}
+
 int cfo_assemble(cfo_problem* p) {
     if (!p->classified) { seterr(p, "classify first"); return CFO_EINVAL; }
     csr_free(&p->B); csr_free(&p->BI); csr_free(&p->K); csr_free(&p->KI);
@@ -634,15 +650,9 @@ int cfo_assemble(cfo_problem* p) {
         const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((int64_t)nx * ny));
         const uint8_t t = p->type[l];
         if (t == CFO_REGULAR) {
-            /* Eq. As_qs: coefficient of u at offset (o,q,r) */
-            for (int r = -1; r <= 1; ++r)
-                for (int q = -1; q <= 1; ++q)
-                    for (int o = -1; o <= 1; ++o) {
-                        double v = Rco(p, 0, i, o) * Lco(p, 1, j, q) * Lco(p, 2, k, r) +
-                                   Lco(p, 0, i, o) * Rco(p, 1, j, q) * Lco(p, 2, k, r) +
-                                   Lco(p, 0, i, o) * Lco(p, 1, j, q) * Rco(p, 2, k, r);
-                        bld_push(&bB, LIN(p, i + o, j + q, k + r), v);
-                    }
+            row->n = 0;
+            regular_row(p, i, j, k, row);
+            for (int q = 0; q < row->n; ++q) bld_push(&bB, row->col[q], row->val[q]);
         } else if (t == CFO_IRREGULAR) {
             row->n = 0; rib->n = 0;
             status = irregular_row(p, i, j, k, row, rib, &p->n_degenerate);
@@ -737,6 +747,71 @@ int cfo_rhs(cfo_problem* p, const double* f, const double* g_nodes,
         rhs[l] = q;
     }
     return CFO_OK;
+}
+
+/* B x, sum |B||x| and the right-hand side of Eq. Bu=q at a list of nodes,
+ * each row built as cfo_assemble builds it (regular_row, irregular_row)
+ * and combined as cfo_apply_B and cfo_rhs combine the stored rows, in the
+ * same order, without assembling the other rows: for grids whose explicit
+ * CSR does not fit in host memory.  Rows are independent, so the list is
+ * split over threads. */
+int cfo_rows(cfo_problem* p, int64_t nrows, const int64_t* rows, const double* x,
+             const double* f, const double* g_nodes, const double* g_ibi,
+             double* bx, double* bx_abs, double* rhs, int64_t* n_degenerate) {
+    if (!p->classified) { seterr(p, "classify first"); return CFO_EINVAL; }
+    const int nx = p->n[0], ny = p->n[1];
+    int status = CFO_OK;
+    int64_t ndeg = 0;
+    #pragma omp parallel reduction(+ : ndeg)
+    {
+        rowacc_t* row = (rowacc_t*)malloc(sizeof(rowacc_t));
+        rowacc_t* rib = (rowacc_t*)malloc(sizeof(rowacc_t));
+        #pragma omp for schedule(dynamic, 64)
+        for (int64_t q = 0; q < nrows; ++q) {
+            const int64_t l = rows[q];
+            double y = 0.0, ya = 0.0, r = 0.0;
+            int st = CFO_OK;
+            if (!row || !rib) st = CFO_ENOMEM;
+            else if (l < 0 || l >= p->N) st = CFO_EINVAL;
+            const uint8_t t = st == CFO_OK ? p->type[l] : CFO_BOUNDARY;
+            if (st == CFO_OK && is_unknown(t)) {
+                const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((int64_t)nx * ny));
+                row->n = 0; rib->n = 0;
+                if (t == CFO_REGULAR) regular_row(p, i, j, k, row);
+                else st = irregular_row(p, i, j, k, row, rib, &ndeg);
+                if (st == CFO_OK) {
+                    if (x)
+                        for (int e = 0; e < row->n; ++e) {
+                            y += row->val[e] * x[row->col[e]];
+                            ya += fabs(row->val[e]) * fabs(x[row->col[e]]);
+                        }
+                    if (rhs) {
+                        for (int rr = -1; rr <= 1; ++rr)
+                            for (int ss = -1; ss <= 1; ++ss)
+                                for (int o = -1; o <= 1; ++o) {
+                                    int64_t c = LIN(p, i + o, j + ss, k + rr);
+                                    if (p->type[c] == CFO_SOLID) continue;
+                                    r += Lco(p, 0, i, o) * Lco(p, 1, j, ss) * Lco(p, 2, k, rr) * f[c];
+                                }
+                        for (int e = 0; e < rib->n; ++e) r -= rib->val[e] * g_ibi[rib->col[e]];
+                        for (int e = 0; e < row->n; ++e)
+                            if (p->type[row->col[e]] == CFO_BOUNDARY) r -= row->val[e] * g_nodes[row->col[e]];
+                    }
+                }
+            }
+            if (st != CFO_OK) {
+                #pragma omp critical
+                { if (status == CFO_OK) status = st; }
+            }
+            if (bx) bx[q] = y;
+            if (bx_abs) bx_abs[q] = ya;
+            if (rhs) rhs[q] = r;
+        }
+        free(row); free(rib);
+    }
+    if (n_degenerate) *n_degenerate = ndeg;
+    if (status != CFO_OK && !p->err[0]) seterr(p, "row evaluation failed");
+    return status;
 }
 
 /* Approximate solve of K phi = rho (Sec. 3.3): `sweeps` red-black

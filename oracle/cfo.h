@@ -77,6 +77,14 @@ void cfo_apply_B(cfo_problem* p, const double* x, double* y);
 void cfo_apply_B_abs(cfo_problem* p, const double* x, double* y);
 int  cfo_rhs(cfo_problem* p, const double* f, const double* g_nodes,
              const double* g_ibi, double* rhs);
+/* B x, sum_c |B_lc||x_c| and the right-hand side at the nodes rows[0..nrows)
+ * (outputs indexed like rows; 0 at non-unknowns) without assembling the
+ * system; needs cfo_classify only.  x, f, g_nodes: full-grid arrays, g_ibi:
+ * n_ibi values; a NULL output skips its inputs.  n_degenerate: NULL or the
+ * degenerate operators met in those rows. */
+int cfo_rows(cfo_problem* p, int64_t nrows, const int64_t* rows, const double* x,
+             const double* f, const double* g_nodes, const double* g_ibi,
+             double* bx, double* bx_abs, double* rhs, int64_t* n_degenerate);
 /* inner iterations on K from phi = 0: red-black Gauss-Seidel sweeps
  * (cfo_precond) or ILU(0)-Richardson sweeps (cfo_precond_ilu); the solve
  * uses the kind set by cfo_set_precond (red-black by default) */

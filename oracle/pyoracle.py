@@ -51,6 +51,7 @@ def lib():
         L.cfo_apply_B.argtypes = [C.c_void_p, _D, _D]
         L.cfo_apply_B_abs.argtypes = [C.c_void_p, _D, _D]
         L.cfo_rhs.argtypes = [C.c_void_p, _D, _D, _D, _D]
+        L.cfo_rows.argtypes = [C.c_void_p, C.c_int64, _I64, _D, _D, _D, _D, _D, _D, _D, _I64]
         L.cfo_precond.argtypes = [C.c_void_p, C.c_int, _D, _D]
         L.cfo_precond_ilu.argtypes = [C.c_void_p, C.c_int, _D, _D]
         L.cfo_set_precond.argtypes = [C.c_void_p, C.c_int]
@@ -217,6 +218,33 @@ class Problem:
         out = np.zeros(self.N)
         self._check(lib().cfo_rhs(self._h, _dp(f), _dp(g), _dp(gi), _dp(out)), "rhs")
         return out
+
+    def rows(self, rows, x=None, f=None, g_nodes=None, g_ibi=None):
+        """B x, sum |B||x| and the right-hand side at the nodes ``rows``
+        (linear indices), each row built as the full assembly builds it but
+        without assembling the system.  Returns (Bx, |B||x|, rhs,
+        n_degenerate); an output whose inputs are None is None."""
+        if self.type is None:
+            self.classify()
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        n = rows.size
+        want_b = x is not None
+        want_r = f is not None
+        xs = _f64(x).reshape(-1) if want_b else None
+        fs = _f64(f).reshape(-1) if want_r else None
+        gs = _f64(g_nodes).reshape(-1) if want_r else None
+        gi = (_f64(g_ibi).reshape(-1) if self.n_ibi else np.zeros(1)) if want_r else None
+        bx = np.zeros(n) if want_b else None
+        ba = np.zeros(n) if want_b else None
+        rh = np.zeros(n) if want_r else None
+        ndeg = C.c_int64()
+        nul = C.cast(None, _D)
+        self._check(lib().cfo_rows(self._h, n, rows.ctypes.data_as(_I64), _dp(xs) if want_b else nul,
+                                   _dp(fs) if want_r else nul, _dp(gs) if want_r else nul,
+                                   _dp(gi) if want_r else nul, _dp(bx) if want_b else nul,
+                                   _dp(ba) if want_b else nul, _dp(rh) if want_r else nul, C.byref(ndeg)),
+                    "rows")
+        return bx, ba, rh, ndeg.value
 
     def precond(self, rho, sweeps=8, kind=PRECOND_RBGS):
         """sweeps inner iterations on K from phi = 0 (red-black Gauss-Seidel

@@ -393,8 +393,9 @@ cfp_status status_of(int flag) {
 
 }  // namespace
 
-// y = alpha x + beta y over all nodes (FP64)
-__global__ void k_axpby(double alpha, const double* __restrict__ x, double beta, double* __restrict__ y, int64_t N) {
+// y = alpha x + beta y over all nodes (FP64); x and y may be the same field,
+// so neither pointer is declared __restrict__
+__global__ void k_axpby(double alpha, const double* x, double beta, double* y, int64_t N) {
     GRID_STRIDE(l, N) y[l] = alpha * x[l] + beta * y[l];
 }
 

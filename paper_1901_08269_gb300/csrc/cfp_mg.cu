@@ -316,9 +316,12 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
 }
 
 // A wait that runs out (1 s) records a code in *wait_err (1: producer, stage
-// free; 2: producer, final drain; 3, 4: consumer, stage filled) and that
-// thread stops waiting: every index stays in bounds whatever the stages
-// hold, so the launch still ends, and the host reports the error.
+// free; 2: producer, final drain; 3, 4: consumer, stage filled).  A producer
+// whose wait ran out issues no further copy and then waits (bounded) for the
+// copies it has issued, so no CTA ends with a bulk copy in flight into its
+// shared memory; a consumer whose wait ran out stops waiting: every index
+// stays in bounds whatever the stages hold, so the launch still ends, and
+// the host reports the error.
 // out: e of `colour` (KIND 0), r0 (KIND 1, colour 0), phi (KIND 2, colour 1).
 template <int KIND>
 __global__ void __launch_bounds__(kTmaThreads)
@@ -347,15 +350,19 @@ __global__ void __launch_bounds__(kTmaThreads)
         if (lane != 0) return;
         unsigned g = 0;  // planes issued by this CTA; plane g uses stage g % kTmaStages
         bool ok = true;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const int tx = tile % ntx, rest = tile / ntx, tyi = rest % nty, tz = rest / nty;
             const int m0 = tx * kTmaTX, j0 = 1 + tyi * kTmaRows, k0 = 1 + tz * kTmaPlanes;
             const int k1 = min(k0 + kTmaPlanes, nz - 1);
             for (int k = k0 - 1; k <= k1; ++k, ++g) {
                 const int st = g % kTmaStages;
-                if (g >= kTmaStages && ok && !mbar_wait(&empty[st], ((g / kTmaStages) - 1) & 1)) {
+                // a stage is refilled only once every consumer warp released
+                // it; if that wait runs out, nothing more is issued (the
+                // consumers may still read the stage)
+                if (g >= kTmaStages && !mbar_wait(&empty[st], ((g / kTmaStages) - 1) & 1)) {
                     ok = false;
                     atomicExch(wait_err, 1);
+                    break;
                 }
                 unsigned char* buf = base + st * kTmaStage;
                 mbar_arrive_expect_tx(&full[st], kTmaOBytes + kTmaBBytes + (KIND == 1 ? kTmaBBytes : 0));
@@ -364,12 +371,13 @@ __global__ void __launch_bounds__(kTmaThreads)
                 if (KIND == 1) tma_load_3d(buf + kEOff, &t_own, &full[st], m0, j0, k);
             }
         }
-        // every copy has landed before the CTA may end
-        for (unsigned q = g > (unsigned)kTmaStages ? g - kTmaStages : 0; q < g && ok; ++q)
-            if (!mbar_wait(&full[q % kTmaStages], (q / kTmaStages) & 1)) {
-                ok = false;
-                atomicExch(wait_err, 2);
-            }
+        // Every copy issued has landed before the CTA may end, after a
+        // timeout too: planes g - kTmaStages .. g - 1 are the only ones whose
+        // stage was not released (an older plane's stage was waited free
+        // before it was refilled), and each of their full phases is the
+        // latest of its barrier.  Each wait is bounded again.
+        for (unsigned q = g > (unsigned)kTmaStages ? g - kTmaStages : 0; q < g; ++q)
+            if (!mbar_wait(&full[q % kTmaStages], (q / kTmaStages) & 1)) atomicExch(wait_err, 2);
         return;
     }
     // consumers: thread (lx, group) owns pair m0 + lx of the rows r0 .. r0 + 3

@@ -259,40 +259,77 @@ def quartic_workload(x, y, z, bodies=(), seed=0, fluid_inside=False) -> Workload
                     list(bodies), u, f, fluid_inside=fluid_inside)
 
 
+def _cells_inside(grid: np.ndarray, lo: float, hi: float, margin: int) -> bool:
+    """True if [lo, hi] lies between grid nodes margin and n-1-margin."""
+    return lo >= grid[margin] and hi <= grid[grid.size - 1 - margin]
+
+
+def _local_h(grid: np.ndarray, lo: float, hi: float) -> float:
+    """Largest spacing of the grid cells that meet [lo, hi]."""
+    a = max(int(np.searchsorted(grid, lo)) - 1, 0)
+    b = min(int(np.searchsorted(grid, hi)) + 1, grid.size - 1)
+    return float(np.max(np.diff(grid[a:b + 1])))
+
+
+BODY_CLEARANCE_CELLS = 3
+
+
 def random_problem(seed: int, sizes=(33, 49, 65, 97, 129)) -> Workload:
     """One problem of the batched workload: n drawn from ``sizes`` (same on
     each axis), tanh factors U[1,2] per axis, 1-3 spheres/ellipsoids with
-    radii in [0.1, 0.3] and random rotations, kept >= 6 cells from the box and
-    from each other (rejection sampling), f = sum of 8 random Fourier modes
-    with wavenumbers 1..6 and N(0,1) amplitudes, g = 0."""
+    radii in [0.1, 0.3] and random rotations, f = sum of 8 random Fourier
+    modes with wavenumbers 1..6 and N(0,1) amplitudes, g = 0.
+
+    Clearance is counted in cells of the stretched grid itself: the bounding
+    box of every body (its centre +- its largest semi-axis) lies between the
+    nodes 3 and n-4 of each axis (the batched workload's ">= 3 cells from the
+    box"), and the surfaces of two bodies are at least 3 of the largest local
+    cells apart (the cells of each axis over the interval the two bodies
+    span).  A moment-matched stencil of Secs. 2.2-2.3 reaches five nodes past
+    its irregular point, so near the box or another body some of them end
+    early (the degenerate operators the library counts).  A candidate body that breaks a rule is
+    redrawn (centre, radii, rotation); if the bodies still cannot be placed,
+    the stretching factors are redrawn; a seed for which nothing fits raises
+    ValueError instead of returning fewer bodies."""
     rng = np.random.default_rng(seed)
     n = int(rng.choice(sizes))
-    betas = rng.uniform(1.0, 2.0, 3)
-    x = tanh_grid(-1.0, 1.0, n, betas[0])
-    y = tanh_grid(-1.0, 1.0, n, betas[1])
-    z = tanh_grid(-1.0, 1.0, n, betas[2])
-    hmax = max(np.max(np.diff(x)), np.max(np.diff(y)), np.max(np.diff(z)))
     nb = int(rng.integers(1, 4))
-    bodies = []
-    for _ in range(200):
-        if len(bodies) == nb:
+    m = BODY_CLEARANCE_CELLS
+    for _attempt in range(50):
+        betas = rng.uniform(1.0, 2.0, 3)
+        x = tanh_grid(-1.0, 1.0, n, betas[0])
+        y = tanh_grid(-1.0, 1.0, n, betas[1])
+        z = tanh_grid(-1.0, 1.0, n, betas[2])
+        axes = (x, y, z)
+        placed = []  # (body, centre, bounding radius)
+        for _ in range(400):
+            if len(placed) == nb:
+                break
+            r = rng.uniform(0.1, 0.3, 3)
+            kind = "sphere" if rng.random() < 0.5 else "ellipsoid"
+            if kind == "sphere":
+                r[:] = r[0]
+            c = rng.uniform(-1.0, 1.0, 3)
+            R = rot_euler(*rng.uniform(0, 2 * math.pi, 3))
+            rad = float(np.max(r))
+            if not all(_cells_inside(axes[d], c[d] - rad, c[d] + rad, m) for d in range(3)):
+                continue
+            ok = True
+            for _b, c2, rad2 in placed:
+                h = max(_local_h(axes[d], min(c[d] - rad, c2[d] - rad2), max(c[d] + rad, c2[d] + rad2))
+                        for d in range(3))
+                if np.linalg.norm(c - c2) - rad - rad2 < m * h:
+                    ok = False
+                    break
+            if not ok:
+                continue
+            b = sphere(c, r[0]) if kind == "sphere" else ellipsoid(c, r, R)
+            placed.append((b, c, rad))
+        if len(placed) == nb:
             break
-        r = rng.uniform(0.1, 0.3, 3)
-        kind = "sphere" if rng.random() < 0.5 else "ellipsoid"
-        if kind == "sphere":
-            r[:] = r[0]
-        c = rng.uniform(-1.0, 1.0, 3)
-        R = rot_euler(*rng.uniform(0, 2 * math.pi, 3))
-        rad = float(np.max(r))
-        if np.any(np.abs(c) + rad > 1.0 - 6.0 * hmax):
-            continue
-        if any(np.linalg.norm(c - np.asarray(b["c"])) < rad + b["_rad"] + 6.0 * hmax for b in bodies):
-            continue
-        b = sphere(c, r[0]) if kind == "sphere" else ellipsoid(c, r, R)
-        b["_rad"] = rad
-        bodies.append(b)
-    for b in bodies:
-        b.pop("_rad", None)
+    else:
+        raise ValueError("random_problem(seed=%d): could not place %d bodies on the %d^3 grid" % (seed, nb, n))
+    bodies = [b for b, _c, _r in placed]
     k = rng.integers(1, 7, (8, 3)).astype(np.float64)
     amp = rng.standard_normal(8)
     ph = rng.uniform(0, 2 * math.pi, 8)

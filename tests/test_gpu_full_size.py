@@ -9,10 +9,15 @@ not assemble the system (its CSR would need ~44 GB), so:
     27-term definition of the regular row (Eq. A27: Rx Ly Lz + Lx Ry Lz +
     Lx Ly Rz with the oracle's 1D coefficients of Eq. app_xxx), summed here
     in numpy;
-  - the irregular rows, the right-hand side and the preconditioned solve are
-    checked through what holds at any size: the mixed-precision solve with
-    the multigrid V(4,3) preconditioner (the bench's) reaches a true relative
-    residual of 1e-15 and the FP64 solve's max-norm error within 2 %."""
+  - every irregular row of B x (the modified stencils of Secs. 2.2-2.3, the
+    degenerate operators included) and of the right-hand side, plus a seeded
+    sample of regular and non-unknown rows, is compared element by element
+    with the oracle's rows, which it builds one by one without assembling
+    the system (cfo_rows);
+  - the preconditioned solve is checked through what holds at any size: the
+    mixed-precision solve with the multigrid V(4,3) preconditioner (the
+    bench's) reaches a true relative residual of 1e-15 and the FP64 solve's
+    max-norm error within 2 %."""
 import numpy as np
 import pytest
 
@@ -41,11 +46,18 @@ def full():
     ctx.close()
 
 
-def test_full_size_classification_and_ibi_points_bit_exact(full):
-    w, ctx, ty, xyz = full
+@pytest.fixture(scope="module")
+def oracle(full):
+    w = full[0]
     P = O.Problem(w.x, w.y, w.z, w.bodies)
     otype = P.classify()
     _, _, oxyz = P.ibi()
+    return P, otype, oxyz
+
+
+def test_full_size_classification_and_ibi_points_bit_exact(full, oracle):
+    w, ctx, ty, xyz = full
+    P, otype, oxyz = oracle
     assert ctx.n_irregular == P.n_irr and ctx.n_ibi == P.n_ibi
     np.testing.assert_array_equal(ty.cpu().numpy(), otype)
     np.testing.assert_array_equal(xyz.cpu().numpy(), oxyz)
@@ -92,6 +104,57 @@ def test_full_size_apply_on_sampled_regular_rows(full):
     got = y[torch.as_tensor(lin, device="cuda")].cpu().numpy()
     err = np.abs(got - want) / scale
     assert np.max(err) <= 1e-13, np.max(err)
+
+
+def _rows_under_test(otype, seed):
+    """Every irregular row plus a seeded sample of 20000 other nodes (regular,
+    solid and box rows)."""
+    rng = np.random.default_rng(seed)
+    irr = np.flatnonzero(otype == O.IRREGULAR)
+    return np.concatenate([irr, rng.integers(0, otype.size, 20000)]), irr.size
+
+
+def test_full_size_irregular_rows_of_the_apply(full, oracle):
+    w, ctx, ty, xyz = full
+    P, otype, oxyz = oracle
+    rows, n_irr = _rows_under_test(otype, 17)
+    assert n_irr == ctx.n_irregular and n_irr > 300000
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5130)
+    x = torch.randn(w.N, generator=gen, dtype=torch.float64, device="cuda")
+    x[ty == O.SOLID] = 0.0  # box values stay: the rows next to the box read them
+    y = torch.empty_like(x)
+    ctx.apply(x, y)
+    bx, ba, _, ndeg = P.rows(rows, x=x.cpu().numpy())
+    assert ndeg > 0  # the degenerate operators of this geometry are among the rows
+    got = y[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+    err = np.abs(got - bx)
+    # the bar of the small parity cases: an irregular row is the regular row
+    # plus merged corrections, rounding bounded by 1e-12 |B||x|
+    assert np.all(err <= 1e-12 * ba + 1e-300), np.max(err / (ba + 1e-300))
+    assert np.all(got[otype[rows] == O.SOLID] == 0.0)
+
+
+def test_full_size_rhs_rows(full, oracle):
+    w, ctx, ty, xyz = full
+    P, otype, oxyz = oracle
+    rows, _ = _rows_under_test(otype, 18)
+    f, g = w.fields(torch, "cuda")
+    gi = w.g_at(xyz, torch).contiguous()
+    rhs = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+    ctx.assemble_rhs(f, g, gi, rhs)
+    X, Y, Z = w.mesh(torch, "cuda")
+    u = w.u(X, Y, Z, torch).reshape(-1)
+    u[ty == O.SOLID] = 0.0
+    del X, Y, Z
+    # the same g at the IBI points on both sides (the coordinates are
+    # bit-equal; the values are evaluated once, on the device)
+    _, ba, ro, _ = P.rows(rows, x=u.cpu().numpy(), f=f.cpu().numpy(), g_nodes=g.cpu().numpy(),
+                          g_ibi=gi.cpu().numpy())
+    got = rhs[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+    scale = ba + np.abs(ro) + 1.0  # the bar of the small parity cases
+    err = np.abs(got - ro)
+    assert np.all(err <= 1e-12 * scale), np.max(err / scale)
 
 
 def test_full_size_mixed_multigrid_solve_reaches_fp64_error(full):

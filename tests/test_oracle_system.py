@@ -309,3 +309,27 @@ def test_paper_error_tables_show_fourth_order():
     for tab, v in by.items():
         for (n1, e1), (n2, e2) in zip(v[:-1], v[1:]):
             assert 3.95 < _order(e1, e2, n1, n2) < 4.05, tab
+
+
+@pytest.mark.parametrize("body", ["sphere", "torus", "two"])
+def test_rows_without_assembly_equal_the_assembled_rows(body):
+    # cfo_rows builds any chosen rows as the full assembly does and combines
+    # them in the same order: B x, |B||x| and the right-hand side equal those
+    # of the assembled CSR bit for bit (regular, irregular, degenerate and
+    # non-unknown rows alike), so it can stand in for the assembly on grids
+    # whose CSR does not fit in memory.
+    w = W.Workload("rows", *_grids(27), BODIES[body], W._c3_u, W._c3_f)
+    P, t, f, g, gi = _setup(w)
+    P.assemble()
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(w.N)
+    x[t == O.SOLID] = 0.0
+    irr = np.flatnonzero(t == O.IRREGULAR)
+    rows = np.concatenate([irr, rng.integers(0, w.N, 500)])
+    bx, ba, rh, ndeg = P.rows(rows, x, f, g, gi)
+    np.testing.assert_array_equal(bx, P.apply_B(x)[rows])
+    np.testing.assert_array_equal(ba, P.apply_B(x, absval=True)[rows])
+    np.testing.assert_array_equal(rh, P.rhs(f, g, gi)[rows])
+    assert irr.size > 0
+    bx2, _, rh2, nd2 = P.rows(irr)
+    assert rh2 is None and bx2 is None and nd2 == P.degenerate()
