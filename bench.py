@@ -242,24 +242,29 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------ kernel mode
-def nn_time(ctx, name, reps):
-    """One 16 -> 16 channel 3x3x3 layer of the learned part on the context's
-    grid (random BF16 input and weights): event-timed mean of reps launches
-    after two untimed ones; FLOP counted as 2 * 16 * 27 * 16 per node."""
+def nn_time(ctx, name, reps, cin=16, cout=16):
+    """One cin -> cout 3x3x3 layer of the learned part on the context's grid
+    (random BF16 activations and weights): event-timed mean of reps calls
+    after two untimed ones (each call packs the weights, launches the
+    tensor-core kernel and checks its wait word); FLOP = 2 * 27 * cin * cout
+    per node."""
     import torch
+
+    from paper_1901_08269_gb300 import cfp
     g = torch.Generator(device="cuda").manual_seed(0)
-    n = ctx.N
-    x = torch.randn(n * 16, generator=g, device="cuda").to(torch.bfloat16)
-    dy = torch.randn(n * 16, generator=g, device="cuda").to(torch.bfloat16)
-    w = (0.1 * torch.randn(16 * 27 * 16, generator=g, device="cuda")).to(torch.bfloat16)
-    out = torch.empty(n * 16, dtype=torch.bfloat16, device="cuda")
-    dw = torch.zeros(16 * 27 * 16, dtype=torch.float32, device="cuda")
+    dims = (ctx.x.size, ctx.y.size, ctx.z.size)
+    npad = (dims[0] + 2) * (dims[1] + 2) * (dims[2] + 2)
+    x = torch.randn(npad * cin, generator=g, device="cuda").to(torch.bfloat16)
+    dy = torch.randn(npad * cout, generator=g, device="cuda").to(torch.bfloat16)
+    w = (0.1 * torch.randn(cout * 27 * cin, generator=g, device="cuda")).to(torch.bfloat16)
+    out = torch.empty(npad * cout, dtype=torch.bfloat16, device="cuda")
+    dw = torch.zeros(cout * 27 * cin, dtype=torch.float32, device="cuda")
 
     def run():
         if name == "nn_conv":
-            ctx.nn_conv3d(x, w, None, 1, out)
+            ctx.nn_conv3d(dims, cin, cout, x, w, out, flags=cfp.NN_RELU)
         else:
-            ctx.nn_wgrad(x, dy, dw)
+            ctx.nn_wgrad(dims, cin, cout, x, dy, dw)
 
     for _ in range(2):
         run()
@@ -271,8 +276,8 @@ def nn_time(ctx, name, reps):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
-    flop = 2.0 * 16 * 27 * 16 * n
-    return {"ms": ms, "flop": flop, "TFLOPs": flop / ms / 1e9}
+    flop = 2.0 * 27 * cin * cout * dims[0] * dims[1] * dims[2]
+    return {"ms": ms, "flop": flop, "TFLOPs": flop / ms / 1e9, "cin": cin, "cout": cout}
 
 
 def kernel_arm(args):

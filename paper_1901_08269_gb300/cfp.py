@@ -52,9 +52,12 @@ _D = C.POINTER(C.c_double)
 EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_destroy", "cfp_classify_points",
            "cfp_ibi_points", "cfp_assemble_rhs", "cfp_apply", "cfp_precondition", "cfp_solve", "cfp_solve_host",
            "cfp_time_kernel", "cfp_launch_count", "cfp_assemble_rhs_noalloc", "cfp_precondition_ex",
-           "cfp_solve_batch", "cfp_autotune", "cfp_diag_bounded_wait", "cfp_nn_pack", "cfp_nn_conv3d",
-           "cfp_nn_conv3d_dgrad", "cfp_nn_conv3d_wgrad", "cfp_nn_mse", "cfp_nn_adam", "cfp_nn_unpack",
-           "cfp_vec_dot", "cfp_vec_axpby"]
+           "cfp_solve_batch", "cfp_autotune", "cfp_diag_bounded_wait", "cfp_vec_dot", "cfp_vec_axpby",
+           "cfp_nn_conv3d", "cfp_nn_conv3d_wgrad", "cfp_nn_transfer", "cfp_unet_create", "cfp_unet_destroy",
+           "cfp_unet_param_count", "cfp_unet_get_params", "cfp_unet_set_params", "cfp_unet_forward_raw",
+           "cfp_unet_train_step", "cfp_unet_apply", "cfp_unet_check", "cfp_solve_fgmres"]
+NN_RELU, NN_MASK, NN_OUT_F32, NN_ACCUM, NN_DGRAD = 1, 2, 4, 8, 16
+NN_INJECT, NN_PROLONG_ADD, NN_PROLONG_T, NN_SKIP_GRAD = 0, 1, 2, 3
 KERNEL_APPLY, KERNEL_RBGS, KERNEL_UPDATE, KERNEL_MG_SWEEP = 0, 1, 2, 3
 
 
@@ -91,17 +94,27 @@ def lib(build_if_missing=True):
         L.cfp_launch_count.argtypes = [_P]
         L.cfp_launch_count.restype = C.c_int64
         L.cfp_diag_bounded_wait.argtypes = [_P]
-        L.cfp_nn_pack.argtypes = [_P, _P, _P, C.c_double, C.c_double, _P, _P, _P, _D]
-        L.cfp_nn_conv3d.argtypes = [_P, _P, _P, _P, C.c_int, _P, _P]
-        L.cfp_nn_conv3d_dgrad.argtypes = [_P, _P, _P, _P, _P]
-        L.cfp_nn_conv3d_wgrad.argtypes = [_P, _P, _P, _P, _P]
-        L.cfp_nn_mse.argtypes = [_P, _P, _P, _P, C.c_double, _P, _D]
-        L.cfp_nn_adam.argtypes = [_P, C.c_int64, _P, _P, _P, _P, C.c_int, C.c_double, _P]
-        L.cfp_nn_unpack.argtypes = [_P, _P, C.c_double, _P]
         L.cfp_vec_dot.argtypes = [_P, _P, _P, _D]
         L.cfp_vec_axpby.argtypes = [_P, C.c_double, _P, C.c_double, _P]
+        _I = C.c_int
+        L.cfp_nn_conv3d.argtypes = [_P, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I, _P]
+        L.cfp_nn_conv3d_wgrad.argtypes = [_P, _I, _I, _I, _I, _I, _P, _P, _P, _P]
+        L.cfp_nn_transfer.argtypes = [_P, _I, _I, _I, _I, _I, _P, _P, _P, _P]
+        L.cfp_unet_create.argtypes = [_P, C.c_uint64, C.POINTER(_P)]
+        L.cfp_unet_destroy.argtypes = [_P]
+        L.cfp_unet_destroy.restype = None
+        L.cfp_unet_param_count.argtypes = []
+        L.cfp_unet_param_count.restype = C.c_int64
+        L.cfp_unet_get_params.argtypes = [_P, _P, _P]
+        L.cfp_unet_set_params.argtypes = [_P, _P]
+        L.cfp_unet_forward_raw.argtypes = [_P, _I, _I, _I, _P, _P, _P, _I, _P, _D]
+        L.cfp_unet_train_step.argtypes = [_P, _P, _P, _P, C.c_double, _D]
+        L.cfp_unet_apply.argtypes = [_P, _P, _P, _P]
+        L.cfp_unet_check.argtypes = [_P]
+        L.cfp_solve_fgmres.argtypes = [_P, _P, _P, _P, _P, _P, C.c_double, C.POINTER(Opts), _I, _I,
+                                       C.POINTER(Info)]
         for name in EXPORTS[2:]:
-            if name not in ("cfp_ctx_destroy", "cfp_launch_count"):
+            if name not in ("cfp_ctx_destroy", "cfp_launch_count", "cfp_unet_destroy", "cfp_unet_param_count"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -185,73 +198,64 @@ class Context:
         self._h = h
         self.n_irregular = self.n_ibi = None
 
-    # ---- the learned part (include/cfp_nn.h): activations are N x 16 bfloat16,
-    # weights 16 x 27 x 16 bfloat16, all CUDA tensors; argument marshalling only
-    def _nn(self, t, name, dtype, numel):
+    # ---- the learned part's single kernels (include/cfp_nn.h): padded,
+    # channels-last bfloat16 activations on an nx x ny x nz grid; argument
+    # marshalling only
+    @staticmethod
+    def _bf(t, name, numel, dtype=None):
+        import torch
+        dtype = dtype or torch.bfloat16
         if t is None or not t.is_cuda or t.dtype != dtype or t.numel() != numel:
             raise ValueError("%s must be a CUDA %s tensor with %d elements" % (name, dtype, numel))
         return _ptr(t)
 
-    def nn_pack(self, r, e, scale, escale, x, target=None, mask=None):
-        """Returns the scale used (scale <= 0: 1 / max |r| at the unknowns)."""
+    def nn_conv3d(self, dims, cin, cout, inp, w, out, bias=None, act=None, flags=0):
+        """out = epilogue(conv(inp, w) + bias) on the grid dims = (nx, ny, nz)."""
         import torch
-        used = C.c_double()
-        _check(lib().cfp_nn_pack(self._h, self._field(r, "r"), None if e is None else self._field(e, "e"),
-                                 float(scale), float(escale), self._nn(x, "x", torch.bfloat16, 16 * self.N),
-                                 None if target is None else self._nn(target, "target", torch.float32, self.N),
-                                 None if mask is None else self._nn(mask, "mask", torch.float32, self.N),
-                                 C.byref(used)), "cfp_nn_pack")
-        return used.value
-
-    def nn_conv3d(self, inp, w, bias, relu, out):
-        import torch
-        bf, f32 = (out, None) if out.dtype == torch.bfloat16 else (None, out)
-        _check(lib().cfp_nn_conv3d(self._h, self._nn(inp, "in", torch.bfloat16, 16 * self.N),
-                                   self._nn(w, "w", torch.bfloat16, 16 * 27 * 16),
-                                   None if bias is None else self._nn(bias, "bias", torch.float32, 16), int(relu),
-                                   None if bf is None else self._nn(bf, "out", torch.bfloat16, 16 * self.N),
-                                   None if f32 is None else self._nn(f32, "out", torch.float32, 16 * self.N)),
+        nx, ny, nz = dims
+        npad = (nx + 2) * (ny + 2) * (nz + 2)
+        f32 = bool(flags & NN_OUT_F32)
+        _check(lib().cfp_nn_conv3d(self._h, nx, ny, nz, cin, cout, self._bf(inp, "in", npad * cin),
+                                   self._bf(w, "w", cout * 27 * cin),
+                                   None if bias is None else self._bf(bias, "bias", cout, torch.float32),
+                                   None if act is None else self._bf(act, "act", npad * cout), int(flags),
+                                   self._bf(out, "out", npad * cout, torch.float32 if f32 else torch.bfloat16)),
                "cfp_nn_conv3d")
         return out
 
-    def nn_dgrad(self, dout, w, act, din):
+    def nn_wgrad(self, dims, cin, cout, inp, gout, dw, db=None):
         import torch
-        _check(lib().cfp_nn_conv3d_dgrad(self._h, self._nn(dout, "dout", torch.bfloat16, 16 * self.N),
-                                         self._nn(w, "w", torch.bfloat16, 16 * 27 * 16),
-                                         None if act is None else self._nn(act, "act", torch.bfloat16, 16 * self.N),
-                                         self._nn(din, "din", torch.bfloat16, 16 * self.N)), "cfp_nn_conv3d_dgrad")
-        return din
-
-    def nn_wgrad(self, inp, dout, dw, db=None):
-        import torch
-        _check(lib().cfp_nn_conv3d_wgrad(self._h, self._nn(inp, "in", torch.bfloat16, 16 * self.N),
-                                         self._nn(dout, "dout", torch.bfloat16, 16 * self.N),
-                                         self._nn(dw, "dw", torch.float32, 16 * 27 * 16),
-                                         None if db is None else self._nn(db, "db", torch.float32, 16)),
+        nx, ny, nz = dims
+        npad = (nx + 2) * (ny + 2) * (nz + 2)
+        _check(lib().cfp_nn_conv3d_wgrad(self._h, nx, ny, nz, cin, cout, self._bf(inp, "in", npad * cin),
+                                         self._bf(gout, "gout", npad * cout),
+                                         self._bf(dw, "dw", cout * 27 * cin, torch.float32),
+                                         None if db is None else self._bf(db, "db", cout, torch.float32)),
                "cfp_nn_conv3d_wgrad")
 
-    def nn_mse(self, y, target, mask, inv_count, dout):
-        import torch
-        loss = C.c_double()
-        _check(lib().cfp_nn_mse(self._h, self._nn(y, "y", torch.float32, 16 * self.N),
-                                self._nn(target, "target", torch.float32, self.N),
-                                self._nn(mask, "mask", torch.float32, self.N), float(inv_count),
-                                self._nn(dout, "dout", torch.bfloat16, 16 * self.N), C.byref(loss)), "cfp_nn_mse")
-        return loss.value
+    def nn_transfer(self, kind, dims, c, a, out, b=None, act=None):
+        for t in (a, out, b, act):
+            if t is not None and (not t.is_cuda or not t.is_contiguous()):
+                raise ValueError("transfer operands must be contiguous CUDA tensors")
+        nx, ny, nz = dims
+        _check(lib().cfp_nn_transfer(self._h, int(kind), nx, ny, nz, c, _ptr(a), _ptr(b), _ptr(act), _ptr(out)),
+               "cfp_nn_transfer")
+        return out
 
-    def nn_adam(self, w, grad, m, v, step, lr, w_bf16=None):
-        n = w.numel()
-        for t in (grad, m, v):
-            if t.numel() != n or not t.is_cuda:
-                raise ValueError("Adam arrays must be CUDA tensors of equal size")
-        _check(lib().cfp_nn_adam(self._h, n, _ptr(w), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr),
-                                 _ptr(w_bf16)), "cfp_nn_adam")
-
-    def nn_unpack(self, y, inv_scale, u):
-        import torch
-        _check(lib().cfp_nn_unpack(self._h, self._nn(y, "y", torch.float32, 16 * self.N), float(inv_scale),
-                                   self._field(u, "u")), "cfp_nn_unpack")
-        return u
+    def solve_fgmres(self, f, g_nodes, g_ibi, u, tol=1e-10, net=None, m=20, net_guess=False, opts=None,
+                     check=True, **kw):
+        """cfp_solve_fgmres: flexible GMRES(m), with the network `net`
+        (UNet or None) in its preconditioner."""
+        o = opts if opts is not None else default_opts(**kw)
+        info = Info()
+        st = lib().cfp_solve_fgmres(self._h, None if net is None else net._h, self._field(f, "f"),
+                                    self._field(g_nodes, "g_nodes"),
+                                    None if g_ibi is None or g_ibi.numel() == 0 else _ptr(g_ibi),
+                                    self._field(u, "u"), float(tol), C.byref(o), int(m), int(bool(net_guess)),
+                                    C.byref(info))
+        if check:
+            _check(st, "cfp_solve_fgmres")
+        return info
 
     def vec_dot(self, a, b):
         out = C.c_double()
@@ -380,3 +384,63 @@ class Context:
         if check:
             _check(st, "cfp_solve_host")
         return info
+
+
+class UNet:
+    """The learned part's network (cfp_unet) on the device and stream of a
+    context; its calls take FP64 fields of classified contexts."""
+
+    def __init__(self, ctx, seed=0):
+        h = _P()
+        _check(lib().cfp_unet_create(ctx._h, int(seed), C.byref(h)), "cfp_unet_create")
+        self._h = h
+        self.ctx = ctx
+        self.n_params = lib().cfp_unet_param_count()
+
+    def params(self, grads=False):
+        import numpy as np
+        p = np.zeros(self.n_params, dtype=np.float32)
+        g = np.zeros(self.n_params, dtype=np.float32) if grads else None
+        _check(lib().cfp_unet_get_params(self._h, p.ctypes.data_as(_P),
+                                         None if g is None else g.ctypes.data_as(_P)), "cfp_unet_get_params")
+        return (p, g) if grads else p
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != self.n_params:
+            raise ValueError("expected %d parameters" % self.n_params)
+        _check(lib().cfp_unet_set_params(self._h, p.ctypes.data_as(_P)), "cfp_unet_set_params")
+
+    def forward_raw(self, dims, x, y=None, target=None, mask=None, count=0):
+        """Forward (and, with target, mask, count, the loss and the backward
+        pass into the gradient accumulators) on a packed input x."""
+        nx, ny, nz = dims
+        loss = C.c_double()
+        _check(lib().cfp_unet_forward_raw(self._h, nx, ny, nz, _ptr(x), _ptr(target), _ptr(mask), int(count),
+                                          _ptr(y), C.byref(loss)), "cfp_unet_forward_raw")
+        return loss.value
+
+    def train_step(self, ctx, r, e, lr, want_loss=False):
+        loss = C.c_double()
+        _check(lib().cfp_unet_train_step(self._h, ctx._h, ctx._field(r, "r"), ctx._field(e, "e"), float(lr),
+                                         C.byref(loss) if want_loss else None), "cfp_unet_train_step")
+        return loss.value if want_loss else None
+
+    def apply(self, ctx, r, z):
+        _check(lib().cfp_unet_apply(self._h, ctx._h, ctx._field(r, "r"), ctx._field(z, "z")), "cfp_unet_apply")
+        return z
+
+    def check(self):
+        _check(lib().cfp_unet_check(self._h), "cfp_unet_check")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cfp_unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/cfp.h"
+#include "../../include/cfp_nn.h"
 
 namespace cfp {
 
@@ -316,6 +317,11 @@ int mg_key(const cfp_ctx* c);
 cfp_status check_waits(cfp_ctx* c);
 // one CTA whose bounded mbarrier wait runs out (code 5), then check_waits
 cfp_status diag_bounded_wait(cfp_ctx* c);
+// learned part (cfp_unet.cu): the stream a network enqueues on (NULL: its
+// context's), returning the previous one; its context's launch counter
+cudaStream_t unet_use_stream(cfp_unet* u, cudaStream_t s);
+int64_t unet_launches(const cfp_unet* u);
+cfp_ctx* unet_owner(const cfp_unet* u);
 // FP64 vector helpers over all N nodes: dot (synchronises), y = alpha x + beta y
 cfp_status vec_dot(cfp_ctx* c, const double* a, const double* b, double* out);
 cfp_status vec_axpby(cfp_ctx* c, double alpha, const double* x, double beta, double* y);
