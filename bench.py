@@ -72,7 +72,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--kernels", default=None,
                     help="time single kernels instead of the solve: a comma list of mg_sweep, rbgs, apply, "
-                         "update, nn_conv, nn_wgrad on the config-3 geometry at --n^3 (--reps launches each); "
+                         "update, nn_conv[C], nn_wgrad[C] (C -> C channels, default 16) on the config-3 geometry "
+                         "at --n^3 (--reps launches each); "
                          "few launches, so it is the command the ncu captures of those kernels run")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=20261203)
@@ -299,8 +300,11 @@ def kernel_arm(args):
            "update": cfp.KERNEL_UPDATE}
     out = {"mode": "kernels", "n": args.n, "precision": args.precision, "reps": args.reps}
     for name in args.kernels.split(","):
-        if name in ("nn_conv", "nn_wgrad"):
-            out[name] = nn_time(ctx, name, args.reps)
+        if name.startswith("nn_conv") or name.startswith("nn_wgrad"):
+            # nn_conv / nn_wgrad: 16 -> 16 channels; nn_conv64 / nn_wgrad128: c -> c
+            base = "nn_conv" if name.startswith("nn_conv") else "nn_wgrad"
+            c = int(name[len(base):] or 16)
+            out[name] = nn_time(ctx, base, args.reps, c, c)
             continue
         ms, by = ctx.time_kernel(ids[name], prec, reps=args.reps)
         out[name] = {"ms": ms, "bytes": by, "GBps": by / ms / 1e6}
