@@ -346,6 +346,23 @@ cfp_status cfp_time_kernel(cfp_ctx* ctx, int kernel, int precision, int reps,
                            double* ms_per_launch, double* bytes_per_launch);
 
 /*
+ * Tile autotuner of the compact-stencil apply (B x: the regular rows of Eq.
+ * A27 matrix-free, then the corrections of the irregular rows of Eq. Bdec),
+ * per precision (CFP_PREC_FP64, or CFP_PREC_MIXED for the FP32 apply of the
+ * mixed solve's inner iterations): rows per thread (2 or 4; a CTA owns 128
+ * columns) x planes a CTA marches in z (16, 32 or 64).  rows = planes = 0:
+ * each of the six shapes is timed (CUDA events, 5 launches after two untimed,
+ * on the context's work vectors) and the fastest is kept by the context for
+ * its later solves; otherwise that shape is set and timed.  The rows of B x
+ * do not depend on the shape (same arithmetic per row); the dot products
+ * fused into the apply are summed per CTA, so their rounding does.  Without a
+ * call the context uses 4 x 64 in FP64 and 2 x 64 in FP32.
+ *   ms  NULL or the chosen shape's mean time per launch.
+ * Requires classification.  Synchronises.  Errors: CFP_ESTATE, CFP_EINVAL.
+ */
+cfp_status cfp_tune_apply(cfp_ctx* ctx, int precision, int rows, int planes, double* ms);
+
+/*
  * FP64 vector helpers over all N nodes of two fields, for outer iterations
  * built on this interface (the learned part's flexible Krylov method):
  * *out_host = sum a[l] b[l] (synchronises); y = alpha x + beta y (x and y

@@ -55,7 +55,7 @@ EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_dest
            "cfp_solve_batch", "cfp_autotune", "cfp_diag_bounded_wait", "cfp_vec_dot", "cfp_vec_axpby",
            "cfp_nn_conv3d", "cfp_nn_conv3d_wgrad", "cfp_nn_transfer", "cfp_unet_create", "cfp_unet_destroy",
            "cfp_unet_param_count", "cfp_unet_get_params", "cfp_unet_set_params", "cfp_unet_forward_raw",
-           "cfp_unet_train_step", "cfp_unet_apply", "cfp_unet_check", "cfp_solve_fgmres"]
+           "cfp_unet_train_step", "cfp_unet_apply", "cfp_unet_check", "cfp_solve_fgmres", "cfp_tune_apply"]
 NN_RELU, NN_MASK, NN_OUT_F32, NN_ACCUM, NN_DGRAD = 1, 2, 4, 8, 16
 NN_INJECT, NN_PROLONG_ADD, NN_PROLONG_T, NN_SKIP_GRAD = 0, 1, 2, 3
 KERNEL_APPLY, KERNEL_RBGS, KERNEL_UPDATE, KERNEL_MG_SWEEP = 0, 1, 2, 3
@@ -94,6 +94,7 @@ def lib(build_if_missing=True):
         L.cfp_launch_count.argtypes = [_P]
         L.cfp_launch_count.restype = C.c_int64
         L.cfp_diag_bounded_wait.argtypes = [_P]
+        L.cfp_tune_apply.argtypes = [_P, C.c_int, C.c_int, C.c_int, _D]
         L.cfp_vec_dot.argtypes = [_P, _P, _P, _D]
         L.cfp_vec_axpby.argtypes = [_P, C.c_double, _P, C.c_double, _P]
         _I = C.c_int
@@ -256,6 +257,14 @@ class Context:
         if check:
             _check(st, "cfp_solve_fgmres")
         return info
+
+    def tune_apply(self, precision=PREC_MIXED, rows=0, planes=0):
+        """cfp_tune_apply: the apply's tile shape (rows = planes = 0:
+        autotuned); returns the chosen shape's ms per launch."""
+        ms = C.c_double()
+        _check(lib().cfp_tune_apply(self._h, int(precision), int(rows), int(planes), C.byref(ms)),
+               "cfp_tune_apply")
+        return ms.value
 
     def vec_dot(self, a, b):
         out = C.c_double()

@@ -337,6 +337,12 @@ cfp_status cfp_time_kernel(cfp_ctx* c, int kernel, int precision, int reps, doub
     return time_kernel(c, kernel, precision, reps, ms, bytes);
 }
 
+cfp_status cfp_tune_apply(cfp_ctx* c, int precision, int rows, int planes, double* ms) {
+    CFP_TRY(need_classified(c));
+    if (precision != CFP_PREC_FP64 && precision != CFP_PREC_MIXED) return fail(CFP_EINVAL, "bad precision");
+    return tune_apply(c, precision, rows, planes, 5, ms);
+}
+
 cfp_status cfp_vec_dot(cfp_ctx* c, const double* a, const double* b, double* out) {
     if (!c) return fail(CFP_EINVAL, "null context");
     if (!out) return fail(CFP_EINVAL, "NULL output");

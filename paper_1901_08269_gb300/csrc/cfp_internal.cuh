@@ -229,6 +229,12 @@ struct cfp_ctx {
     // kernels enqueued since the context was created
     int64_t launches = 0;
 
+    // the apply's tile shape per precision (0 FP64, 1 FP32): rows per thread
+    // (2 or 4) and planes per z chunk (16, 32 or 64); 0: the defaults (set by
+    // the autotuner)
+    int apply_ty[2] = {0, 0};
+    int apply_kc[2] = {0, 0};
+
     // preconditioner of the current solve and its multigrid hierarchy
     int precond_kind = CFP_PRECOND_RBGS;
     int mg_smooth = 2;
@@ -307,6 +313,7 @@ void launch_metrics(cfp_ctx* c);  // Eq. app_xxx and Eq. 2ndorder_coef per axis
 // Krylov (cfp_krylov.cu)
 cfp_status ensure_work(cfp_ctx* c, bool need32);
 cfp_status time_kernel(cfp_ctx* c, int kernel, int prec, int reps, double* ms, double* bytes);
+cfp_status tune_apply(cfp_ctx* c, int prec, int rows, int planes, int reps, double* best_ms);
 // phi = P(rho) in FP32 (the mixed solve's inner preconditioner) for FP64
 // fields: rho rounded to FP32, phi widened back; phi zeroed first
 cfp_status precondition32(cfp_ctx* c, int sweeps, const double* rho, double* phi);

@@ -475,6 +475,40 @@ cfp_status time_kernel_t(cfp_ctx* c, int prec, int kernel, int reps, double* ms,
 }
 }  // namespace
 
+// Tile autotuner of the apply: rows per thread x planes per z chunk, each
+// candidate timed over `reps` launches (after two untimed) with the fused
+// (r_hat0, v) dot, the fastest kept in the context.  rows, planes > 0: that
+// shape is set and timed only.
+cfp_status tune_apply(cfp_ctx* c, int prec, int rows, int planes, int reps, double* best_ms) {
+    const int q = prec == CFP_PREC_MIXED ? 1 : 0;
+    std::vector<std::pair<int, int>> cand;
+    if (rows > 0 || planes > 0) {
+        if ((rows != 2 && rows != 4) || (planes != 16 && planes != 32 && planes != 64))
+            return fail(CFP_EINVAL, "apply tile: rows 2 or 4, planes 16, 32 or 64");
+        cand.push_back({rows, planes});
+    } else {
+        for (int r : {2, 4})
+            for (int k : {16, 32, 64}) cand.push_back({r, k});
+    }
+    double best = INFINITY;
+    int br = 0, bk = 0;
+    for (auto [r, k] : cand) {
+        c->apply_ty[q] = r;
+        c->apply_kc[q] = k;
+        double ms = 0.0;
+        CFP_TRY(time_kernel(c, CFP_KERNEL_APPLY, prec, reps, &ms, nullptr));
+        if (ms < best) {
+            best = ms;
+            br = r;
+            bk = k;
+        }
+    }
+    c->apply_ty[q] = br;
+    c->apply_kc[q] = bk;
+    if (best_ms) *best_ms = best;
+    return CFP_OK;
+}
+
 cfp_status time_kernel(cfp_ctx* c, int kernel, int prec, int reps, double* ms, double* bytes) {
     if (kernel < CFP_KERNEL_APPLY || kernel > CFP_KERNEL_MG_SWEEP || reps < 1 || !ms)
         return fail(CFP_EINVAL, "bad kernel id, reps or output pointer");

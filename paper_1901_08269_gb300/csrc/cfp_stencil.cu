@@ -84,41 +84,42 @@ __device__ __forceinline__ void block_reduce2(double& a, double& b) {
     }
 }
 
-// Regular part of B x at the unknowns.  One thread owns the columns (i, j)
-// of kApplyRows<T> consecutive rows j and marches kApplyKC planes in z.  Per
-// plane it loads the values x(i-1..i+1, j) of the rows j0-1 .. j0+TY (the x
-// and y neighbours come from L1/L2; the loads of the next plane are issued
+// Regular part of B x at the unknowns.  One thread owns the column i of TY
+// consecutive rows j and marches the planes k0 .. k1 - 1 of its z chunk (KC
+// planes); TY x KC is the tile shape the autotuner picks per grid.  The z
+// coefficients of the chunk are staged in shared memory once.
+// Per plane it loads the values x(i-1..i+1, j) of the rows j0-1 .. j0+TY (the
+// x and y neighbours come from L1/L2; the loads of the next plane are issued
 // before the current one is used), forms the x-pass XR = Rx x, XL = Lx x of
 // those rows (each shared by up to three output rows), the y-pass
-// P = Ly XR + Ry XL, Q = Ly XL of its rows, and keeps P, Q of three planes
-// in registers for the z-pass
+// P = Ly XR + Ry XL, Q = Ly XL of its rows, and keeps P, Q of three planes in
+// registers for the z-pass
 //   out(k) = Lz (P(k-1), P(k), P(k+1)) + Rz (Q(k-1), Q(k), Q(k+1)).
 // No shared memory and no barriers.  Solid rows are zero; the rows of
-// irregular points get their side-list corrections from k_apply_corr.
+// irregular points get their side-list corrections from k_apply_corr, launched
+// right after.  (Gathering the corrections inside this kernel, at each plane or
+// from a per-warp list after the march, measured 1.57x slower at 513^3: the
+// dependent side-list loads stall the streaming march, and the CTAs near the
+// bodies become the tail.)
 // DOT = 0: y only; 1: partial (d0, y); 2: partials (d0, y) and (y, y).
-template <class T>
-struct ApplyRows {
-    static constexpr int value = 2;
-};
-// FP64 is arithmetic-bound: four rows per thread share each x-pass among
-// more output rows (7.5 instead of 10 FP64 operations per node for it)
-template <>
-struct ApplyRows<double> {
-    static constexpr int value = 4;
-};
-constexpr int kQfRows = 2;  // rows per thread of k_qf
-
-template <class T, int DOT>
-__global__ void __launch_bounds__(kAX, sizeof(T) == 4 ? 8 : 1)
-    k_apply(Grid<T> G, Side<T> S, const uint8_t* __restrict__ type, const T* __restrict__ x,
-            T* __restrict__ y, const T* __restrict__ d0, double* __restrict__ partial) {
-    constexpr int TY = ApplyRows<T>::value;
+template <class T, int DOT, int TY, int KC>
+__global__ void __launch_bounds__(kAX, TY == 2 ? (sizeof(T) == 4 ? 8 : 2) : (sizeof(T) == 4 ? 4 : 2))
+    k_apply(Grid<T> G, const uint8_t* __restrict__ type, const T* __restrict__ x, T* __restrict__ y,
+            const T* __restrict__ d0, double* __restrict__ partial) {
     constexpr int R = TY + 2;  // rows loaded per plane
     const int nx = G.nx, ny = G.ny, nz = G.nz;
     const int i = 1 + blockIdx.x * kAX + threadIdx.x;
     const int j0 = 1 + blockIdx.y * TY;
-    const int k0 = 1 + blockIdx.z * kApplyKC;
-    const int k1 = min(k0 + kApplyKC, nz - 1);
+    const int k0 = 1 + blockIdx.z * KC;
+    const int k1 = min(k0 + KC, nz - 1);
+    // z coefficients of the chunk's output planes k0 .. k1 - 1
+    __shared__ T zc[5][KC];
+    for (int q = threadIdx.x; q < 5 * KC; q += kAX) {
+        const int m = q / KC, kc = min(k0 + q % KC, nz - 2);
+        const T* src = m == 0 ? G.ax[2].a : m == 1 ? G.ax[2].c : m == 2 ? G.ax[2].ar : m == 3 ? G.ax[2].br : G.ax[2].cr;
+        zc[m][q % KC] = src[kc];
+    }
+    __syncthreads();
     const bool iin = i <= nx - 2;
     const int ic = iin ? i : 1;  // clamped: every load stays inside the grid
     // node offsets fit in 32 bits: contexts hold fewer than 2^31 nodes
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(kAX, sizeof(T) == 4 ? 8 : 1)
 #pragma unroll
     for (int t = 0; t < TY; ++t) Pm[t] = P0[t] = Pp[t] = Qm[t] = Q0[t] = Qp[t] = T(0);
     DotAcc<T> dacc0, dacc1;
+#pragma unroll 3
     for (int kk = k0 - 1; kk <= k1; ++kk) {
         T c[3 * R];
 #pragma unroll
@@ -211,9 +213,9 @@ __global__ void __launch_bounds__(kAX, sizeof(T) == 4 ? 8 : 1)
             Qp[t] = ay[t] * XL[t] + XL[t + 1] + cy[t] * XL[t + 2];
         }
         if (kk >= k0 + 1 && iin) {
-            const int k = kk - 1;
-            const T az = G.ax[2].a[k], cz = G.ax[2].c[k];
-            const T arz = G.ax[2].ar[k], brz = G.ax[2].br[k], crz = G.ax[2].cr[k];
+            const int k = kk - 1, kl = k - k0;
+            const T az = zc[0][kl], cz = zc[1][kl];
+            const T arz = zc[2][kl], brz = zc[3][kl], crz = zc[4][kl];
 #pragma unroll
             for (int t = 0; t < TY; ++t) {
                 if (!jin[t]) continue;
@@ -236,6 +238,8 @@ __global__ void __launch_bounds__(kAX, sizeof(T) == 4 ? 8 : 1)
         }
     }
 }
+constexpr int kQfRows = 2;  // rows per thread of k_qf
+
 // B gb for a field gb that is zero away from the box (the boundary lift of
 // the right-hand side): its regular rows can be nonzero only on the shell of
 // interior nodes next to the box, so only those rows are evaluated, with the
@@ -468,15 +472,16 @@ unsigned flat_grid(int64_t n) {
 
 namespace {
 
-dim3 rows_grid(const cfp_ctx* c, int rows) {
+dim3 rows_grid(const cfp_ctx* c, int rows, int kc = kApplyKC) {
     return dim3((unsigned)((c->n[0] - 2 + kAX - 1) / kAX), (unsigned)((c->n[1] - 2 + rows - 1) / rows),
-                (unsigned)((c->n[2] - 2 + kApplyKC - 1) / kApplyKC));
+                (unsigned)((c->n[2] - 2 + kc - 1) / kc));
 }
 
-template <class T>
-dim3 apply_grid(const cfp_ctx* c) {
-    return rows_grid(c, ApplyRows<T>::value);
-}
+// the apply's tile shape of precision q (0 FP64, 1 FP32): rows per thread
+// and planes per z chunk, as set by the autotuner; otherwise 2 x 64 in FP32
+// and 4 x 64 in FP64, the fastest of the six at 385^3 and 513^3 (measured)
+int apply_rows(const cfp_ctx* c, int q) { return c->apply_ty[q] ? c->apply_ty[q] : (q ? 2 : 4); }
+int apply_planes(const cfp_ctx* c, int q) { return c->apply_kc[q] ? c->apply_kc[q] : 64; }
 
 }  // namespace
 
@@ -496,33 +501,55 @@ int corr_blocks(const cfp_ctx* c) {
     return (int)std::min<int64_t>((c->n_irr + 7) / 8, 152 * 16);
 }
 
+// the most CTAs any apply tile shape launches, with the correction kernel's
+// (dot-product partials per launch)
 int apply_blocks(cfp_ctx* c) {
-    const dim3 g = apply_grid<float>(c), h = apply_grid<double>(c);
-    return (int)std::max(g.x * g.y * g.z, h.x * h.y * h.z) + corr_blocks(c);
+    int64_t m = 0;
+    for (int ty : {2, 4})
+        for (int kc : {16, 32, 64}) {
+            const dim3 g = rows_grid(c, ty, kc);
+            m = std::max<int64_t>(m, (int64_t)g.x * g.y * g.z);
+        }
+    return (int)m + corr_blocks(c);
+}
+
+template <class T, int DOT, int TY, int KC>
+void apply_launch(cfp_ctx* c, const T* x, T* y, const T* d0, double* partial, cudaStream_t s, int* nb) {
+    const dim3 grid = rows_grid(c, TY, KC);
+    k_apply<T, DOT, TY, KC><<<grid, kAX, 0, s>>>(grid_view<T>(c), c->type, x, y, d0, partial);
+    const int nmain = (int)(grid.x * grid.y * grid.z);
+    const int ncorr = corr_blocks(c);
+    if (ncorr)
+        k_apply_corr<T, DOT><<<ncorr, 256, 0, s>>>(side_view<T>(c), c->irr_lin, c->n_irr, x, y, d0,
+                                                   partial ? partial + 2 * (int64_t)nmain : nullptr);
+    c->launches += ncorr ? 1 : 0;
+    if (nb) *nb = nmain + ncorr;
+}
+
+template <class T, int TY, int KC>
+void apply_dot(cfp_ctx* c, const T* x, T* y, const T* d0, int dotmode, double* partial, cudaStream_t s, int* nb) {
+    if (dotmode == 0) apply_launch<T, 0, TY, KC>(c, x, y, d0, partial, s, nb);
+    else if (dotmode == 1) apply_launch<T, 1, TY, KC>(c, x, y, d0, partial, s, nb);
+    else apply_launch<T, 2, TY, KC>(c, x, y, d0, partial, s, nb);
+}
+
+template <class T, int TY>
+void apply_depth(cfp_ctx* c, int kc, const T* x, T* y, const T* d0, int dotmode, double* partial, cudaStream_t s,
+                 int* nb) {
+    if (kc == 16) apply_dot<T, TY, 16>(c, x, y, d0, dotmode, partial, s, nb);
+    else if (kc == 64) apply_dot<T, TY, 64>(c, x, y, d0, dotmode, partial, s, nb);
+    else apply_dot<T, TY, 32>(c, x, y, d0, dotmode, partial, s, nb);
 }
 
 template <class T>
 void launch_apply(cfp_ctx* c, const T* x, T* y, const T* d0, int dotmode, double* partial, cudaStream_t s,
                   int* nblocks_out) {
-    const dim3 grid = apply_grid<T>(c);
-    const dim3 block(kAX);
-    const Grid<T> G = grid_view<T>(c);
-    const Side<T> S = side_view<T>(c);
-    if (dotmode == 0) k_apply<T, 0><<<grid, block, 0, s>>>(G, S, c->type, x, y, d0, partial);
-    else if (dotmode == 1) k_apply<T, 1><<<grid, block, 0, s>>>(G, S, c->type, x, y, d0, partial);
-    else k_apply<T, 2><<<grid, block, 0, s>>>(G, S, c->type, x, y, d0, partial);
-    const int nmain = (int)(grid.x * grid.y * grid.z);
-    const int ncorr = corr_blocks(c);
-    double* pc = partial ? partial + 2 * (int64_t)nmain : nullptr;
-    if (ncorr) {
-        if (dotmode == 0) k_apply_corr<T, 0><<<ncorr, 256, 0, s>>>(S, c->irr_lin, c->n_irr, x, y, d0, pc);
-        else if (dotmode == 1) k_apply_corr<T, 1><<<ncorr, 256, 0, s>>>(S, c->irr_lin, c->n_irr, x, y, d0, pc);
-        else k_apply_corr<T, 2><<<ncorr, 256, 0, s>>>(S, c->irr_lin, c->n_irr, x, y, d0, pc);
-    }
-    c->launches += ncorr ? 2 : 1;
-    if (nblocks_out) *nblocks_out = nmain + ncorr;
+    const int q = sizeof(T) == 4 ? 1 : 0;
+    const int ty = apply_rows(c, q), kc = apply_planes(c, q);
+    if (ty == 4) apply_depth<T, 4>(c, kc, x, y, d0, dotmode, partial, s, nblocks_out);
+    else apply_depth<T, 2>(c, kc, x, y, d0, dotmode, partial, s, nblocks_out);
+    c->launches += 1;
 }
-
 
 // `sweeps` red-black sweeps from phi = 0 (sweeps = 0: masked copy).  The
 // sweeps run on the fine level's red/black split arrays of the multigrid
