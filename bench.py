@@ -66,9 +66,14 @@ def parse():
     ap.add_argument("--oracle-large", type=int, default=0,
                     help="nodes per axis of the larger oracle sample (0: 2 * --oracle-n - 1); config 3's "
                          "geometry needs at least 129")
-    ap.add_argument("--workload", default="config3", choices=["config3", "batch"],
+    ap.add_argument("--workload", default="config3", choices=["config3", "batch", "learned"],
                     help="config3: the 513^3 two-body solve (default); batch: 64 random problems of uneven "
-                         "size solved together")
+                         "size solved together; learned: the U-Net trained on solver-generated pairs, then "
+                         "the paper's method, GMRES and the flexible GMRES with the network compared at "
+                         "--learned-n^3 on held-out geometries")
+    ap.add_argument("--learned-n", type=int, default=257)
+    ap.add_argument("--learned-problems", type=int, default=300,
+                    help="random geometries (65^3) whose solver-generated pairs train the network")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--kernels", default=None,
                     help="time single kernels instead of the solve: a comma list of mg_sweep, rbgs, apply, "
@@ -313,6 +318,73 @@ def kernel_arm(args):
     return 0
 
 
+# ----------------------------------------------------------- learned arm
+def learned_arm(args):
+    """The learned part as a workload: train the U-Net (tcgen05 kernels) on
+    the pairs of --learned-problems random geometries at 65^3 (one Adam step
+    per pair), then solve held-out random geometries with 1-3 bodies at
+    --learned-n^3 to a relative residual of 1e-10 three ways: the paper's
+    method (BiCGSTAB, eight red-black sweeps on K), GMRES(20) with the same
+    sweeps, and the flexible GMRES(20) with the network in its
+    preconditioner and initial guess.  Every solution is checked against a
+    tight multigrid-preconditioned solve (max difference relative to its
+    maximum); the line reports iterations and seconds per solve of each."""
+    import torch
+
+    from paper_1901_08269_gb300 import cfp, learned
+    from paper_1901_08269_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    host = cfp.Context(W.uniform_grid(0, 1, 9), W.uniform_grid(0, 1, 9), W.uniform_grid(0, 1, 9), [])
+    net = cfp.UNet(host, seed=5)
+    pairs, train_s, tail = learned.train(net, seeds=list(range(2000, 2000 + args.learned_problems)), sizes=(65,))
+    rows = []
+    for seed in (9001, 9002, 9003):
+        w = W.random_problem(seed, sizes=(args.learned_n,))
+        ctx = cfp.Context(w.x, w.y, w.z, w.bodies)
+        ctx.classify_points()
+        xyz = ctx.ibi_points()
+        f, g = w.fields(torch, "cuda")
+        gi = w.g_at(xyz, torch).contiguous() if ctx.n_ibi else None
+        ref = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+        # random g = 0 problems reach a relative residual of about 1e-13 at best in FP64
+        ctx.solve(f, g, gi, ref, tol=1e-12, precond=cfp.PRECOND_MG)
+        row = {"seed": seed, "bodies": len(w.bodies), "n": args.learned_n}
+        for name in ("bicgstab_rbgs8", "gmres_rbgs8", "fgmres_net_rbgs8"):
+            for rep in range(2):  # the first run builds graphs and buffers
+                u = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if name == "bicgstab_rbgs8":
+                    info = ctx.solve(f, g, gi, u, tol=1e-10, precond=cfp.PRECOND_RBGS, sweeps=8)
+                else:
+                    info = ctx.solve_fgmres(f, g, gi, u, tol=1e-10, net=net if "net" in name else None, m=20,
+                                            net_guess="net" in name, precond=cfp.PRECOND_RBGS, sweeps=8)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+            row[name] = {"iterations": info.iterations, "s": dt, "rel_residual": info.rel_residual,
+                         "max_diff_vs_ref": float((u - ref).abs().max() / ref.abs().max())}
+            if "net" in name:
+                row[name]["steps_with_network_direction"] = info.refinements
+        rows.append(row)
+        ctx.close()
+    net.close()
+    host.close()
+    mean = lambda k, q: statistics.mean(r[k][q] for r in rows)
+    line = {"metric": "s/solve at %d^3 to equal error: paper's method vs flexible GMRES with the learned network"
+                      % args.learned_n, "value": mean("fgmres_net_rbgs8", "s"), "unit": "s/solve", "n_gpus": 1,
+            "steps": len(rows), "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 network, f64 solve", "data": "synthetic",
+            "config": {"workload": "config5-learned-%d^3" % args.learned_n, "train_problems": args.learned_problems,
+                       "train_pairs": pairs, "train_s": train_s, "train_loss_tail": statistics.mean(tail),
+                       "tol": 1e-10},
+            "paper_method_s": mean("bicgstab_rbgs8", "s"), "gmres_s": mean("gmres_rbgs8", "s"),
+            "iterations": {k: [r[k]["iterations"] for r in rows]
+                           for k in ("bicgstab_rbgs8", "gmres_rbgs8", "fgmres_net_rbgs8")},
+            "problems": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------- batched arm
 def batch_arm(args):
     """64 random problems (n in {33,49,65,97,129}, 1-3 spheres/ellipsoids,
@@ -422,6 +494,8 @@ def main():
         return kernel_arm(args)
     if args.workload == "batch":
         return batch_arm(args)
+    if args.workload == "learned":
+        return learned_arm(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

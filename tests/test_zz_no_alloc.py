@@ -36,6 +36,26 @@ def _check_close(a, b, ref_scale):
     assert bool((err <= 1e-12 * ref_scale).all()), float((err / ref_scale).max())
 
 
+def _row_bounds(w):
+    """Per node, the sums of the absolute weights of its regular row: of the
+    27-point operator (Rx Ly Lz + Lx Ry Lz + Lx Ly Rz, Eq. A27) and of the
+    source operator Q = Lx Ly Lz (Eq. q), from the 1D coefficients of Eq.
+    app_xxx.  Rounding of either assembly is bounded by 1e-12 times these
+    sums times the data's magnitude (the test geometries keep the bodies away
+    from the box, so the rows that see the box values are regular)."""
+    from oracle import pyoracle as O
+    sums = []
+    for xs in (w.x, w.y, w.z):
+        a, c, ar, br, cr = O.compact_coefs(xs)
+        sums.append((np.abs(a) + 1.0 + np.abs(c), np.abs(ar) + np.abs(br) + np.abs(cr)))
+    (Lx, Rx), (Ly, Ry), (Lz, Rz) = sums
+    L3 = Lz[:, None, None] * Ly[None, :, None] * Lx[None, None, :]
+    B3 = (Lz[:, None, None] * Ly[None, :, None] * Rx[None, None, :] +
+          Lz[:, None, None] * Ry[None, :, None] * Lx[None, None, :] +
+          Rz[:, None, None] * Ly[None, :, None] * Lx[None, None, :])
+    return (torch.as_tensor(B3.reshape(-1), device="cuda"), torch.as_tensor(L3.reshape(-1), device="cuda"))
+
+
 @pytest.mark.parametrize("make", [lambda: W.config2(33),
                                   lambda: W.Workload("ragged", W.tanh_grid(-1, 1, 37, 1.1),
                                                      W.tanh_grid(-1, 1, 49, 0.7), W.uniform_grid(-1, 1, 31),
@@ -57,7 +77,8 @@ def test_noalloc_rhs_matches_allocating_entry_point_twice(make):
         got = torch.full((w.N,), float("nan"), dtype=torch.float64, device="cuda")
         ctx.assemble_rhs_noalloc(f, g, gi, got)
         torch.cuda.synchronize()
-        scale = ref.abs() + f.abs().max() + g.abs().max() * 1e4 + 1.0
+        Bsum, Lsum = _row_bounds(w)
+        scale = ref.abs() + Bsum * g.abs().max() + Lsum * f.abs().max() + 1.0
         _check_close(got, ref, scale)
         outs.append(got)
     assert not torch.equal(outs[0], outs[1])
