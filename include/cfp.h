@@ -203,6 +203,16 @@ cfp_status cfp_assemble_rhs(cfp_ctx* ctx, const double* f_dev,
 cfp_status cfp_apply(cfp_ctx* ctx, const double* x_dev, double* y_dev);
 
 /*
+ * The same y = B x in FP32: the operator the mixed-precision solve's inner
+ * iterations use (the 1D metrics and the irregular rows' weights rounded
+ * from their FP64 values, FP32 arithmetic), in the tile shape the context
+ * holds for CFP_PREC_MIXED (cfp_tune_apply).  x_dev, y_dev: N floats on the
+ * device, must not overlap.  Synchronises (a timed-out pipeline wait of the
+ * ring kernel is reported).  Errors: CFP_ESTATE, CFP_EINVAL, CFP_ECUDA.
+ */
+cfp_status cfp_apply_f32(cfp_ctx* ctx, const float* x_dev, float* y_dev);
+
+/*
  * phi = P(rho): `sweeps` red-black Gauss-Seidel sweeps on K phi = rho from
  * phi = 0 (K: the 7-point second-order operator of Eq. A7 with the
  * Shortley-Weller rows of Eq. A7_mod and zero Dirichlet data; Sec. 3.3),
@@ -345,22 +355,41 @@ enum { CFP_KERNEL_APPLY = 0,    /* B x with the fused (r_hat0, v) dot, as in
 cfp_status cfp_time_kernel(cfp_ctx* ctx, int kernel, int precision, int reps,
                            double* ms_per_launch, double* bytes_per_launch);
 
+/* The apply's kernels (cfp_tune_apply). */
+enum { CFP_APPLY_STREAM = 1,  /* each thread streams its column of `rows`
+                                 rows through the z planes of its chunk with
+                                 plain loads, one plane ahead (FP64, FP32)  */
+       CFP_APPLY_RING = 2     /* FP32: a producer warp copies the planes of a
+                                 512-column x 2-row tile with bulk (TMA)
+                                 copies into a ring of shared-memory stages
+                                 ahead of 256 consumer threads; persistent
+                                 grid.  Needs 16-byte aligned x and dot
+                                 operand (otherwise the streaming kernel
+                                 runs)                                       */
+};
+
 /*
- * Tile autotuner of the compact-stencil apply (B x: the regular rows of Eq.
- * A27 matrix-free, then the corrections of the irregular rows of Eq. Bdec),
- * per precision (CFP_PREC_FP64, or CFP_PREC_MIXED for the FP32 apply of the
- * mixed solve's inner iterations): rows per thread (2 or 4; a CTA owns 128
- * columns) x planes a CTA marches in z (16, 32 or 64).  rows = planes = 0:
- * each of the six shapes is timed (CUDA events, 5 launches after two untimed,
- * on the context's work vectors) and the fastest is kept by the context for
- * its later solves; otherwise that shape is set and timed.  The rows of B x
- * do not depend on the shape (same arithmetic per row); the dot products
- * fused into the apply are summed per CTA, so their rounding does.  Without a
- * call the context uses 4 x 64 in FP64 and 2 x 64 in FP32.
- *   ms  NULL or the chosen shape's mean time per launch.
- * Requires classification.  Synchronises.  Errors: CFP_ESTATE, CFP_EINVAL.
+ * Autotuner of the compact-stencil apply (B x: the regular rows of Eq. A27
+ * matrix-free, then the corrections of the irregular rows of Eq. Bdec), per
+ * precision (CFP_PREC_FP64, or CFP_PREC_MIXED for the FP32 apply of the
+ * mixed solve's inner iterations): the kernel (CFP_APPLY_STREAM with 2 or 4
+ * rows per thread and 16, 32 or 64 planes a CTA marches in z;
+ * CFP_APPLY_RING, FP32 only, 2 rows per tile and 32 or 64 planes).
+ * kernel = rows = planes = 0: every candidate (6 in FP64, 8 in FP32) is
+ * timed (CUDA events, 5 launches after two untimed, on the context's work
+ * vectors) and the fastest is kept by the context for its later solves;
+ * otherwise that choice is set and timed.  The rows of B x do not depend on the choice (the same fused
+ * multiply-add chain per row in every kernel); the dot products fused into
+ * the apply are summed per CTA, so their rounding does.  Without a call the
+ * context uses CFP_APPLY_STREAM with 4 rows x 64 planes in FP64; in FP32
+ * CFP_APPLY_RING with 64 planes where its 512-column tiles are at least 85 %
+ * filled by the n_x - 2 interior columns, else CFP_APPLY_STREAM with 2 x 64.
+ *   ms  NULL or the chosen candidate's mean time per launch.
+ * Requires classification.  Synchronises.  Errors: CFP_ESTATE, CFP_EINVAL
+ * (a choice outside those values, or CFP_APPLY_RING with CFP_PREC_FP64 or
+ * where the ring cannot be set up), CFP_ECUDA.
  */
-cfp_status cfp_tune_apply(cfp_ctx* ctx, int precision, int rows, int planes, double* ms);
+cfp_status cfp_tune_apply(cfp_ctx* ctx, int precision, int kernel, int rows, int planes, double* ms);
 
 /*
  * FP64 vector helpers over all N nodes of two fields, for outer iterations

@@ -50,7 +50,7 @@ _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 
 EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_destroy", "cfp_classify_points",
-           "cfp_ibi_points", "cfp_assemble_rhs", "cfp_apply", "cfp_precondition", "cfp_solve", "cfp_solve_host",
+           "cfp_ibi_points", "cfp_assemble_rhs", "cfp_apply", "cfp_apply_f32", "cfp_precondition", "cfp_solve", "cfp_solve_host",
            "cfp_time_kernel", "cfp_launch_count", "cfp_assemble_rhs_noalloc", "cfp_precondition_ex",
            "cfp_solve_batch", "cfp_autotune", "cfp_diag_bounded_wait", "cfp_vec_dot", "cfp_vec_axpby",
            "cfp_nn_conv3d", "cfp_nn_conv3d_wgrad", "cfp_nn_transfer", "cfp_unet_create", "cfp_unet_destroy",
@@ -59,6 +59,7 @@ EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_dest
 NN_RELU, NN_MASK, NN_OUT_F32, NN_ACCUM, NN_DGRAD = 1, 2, 4, 8, 16
 NN_INJECT, NN_PROLONG_ADD, NN_PROLONG_T, NN_SKIP_GRAD = 0, 1, 2, 3
 KERNEL_APPLY, KERNEL_RBGS, KERNEL_UPDATE, KERNEL_MG_SWEEP = 0, 1, 2, 3
+APPLY_STREAM, APPLY_RING = 1, 2
 
 
 def library_path():
@@ -82,6 +83,7 @@ def lib(build_if_missing=True):
         L.cfp_ibi_points.argtypes = [_P, _P, C.c_int]
         L.cfp_assemble_rhs.argtypes = [_P, _P, _P, _P, _P]
         L.cfp_apply.argtypes = [_P, _P, _P]
+        L.cfp_apply_f32.argtypes = [_P, _P, _P]
         L.cfp_precondition.argtypes = [_P, C.c_int, _P, _P]
         L.cfp_solve.argtypes = [_P, _P, _P, _P, _P, C.c_double, C.POINTER(Opts), C.POINTER(Info)]
         L.cfp_solve_host.argtypes = [_P, _P, _P, _P, _P, C.c_double, C.POINTER(Opts), C.POINTER(Info)]
@@ -94,7 +96,7 @@ def lib(build_if_missing=True):
         L.cfp_launch_count.argtypes = [_P]
         L.cfp_launch_count.restype = C.c_int64
         L.cfp_diag_bounded_wait.argtypes = [_P]
-        L.cfp_tune_apply.argtypes = [_P, C.c_int, C.c_int, C.c_int, _D]
+        L.cfp_tune_apply.argtypes = [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]
         L.cfp_vec_dot.argtypes = [_P, _P, _P, _D]
         L.cfp_vec_axpby.argtypes = [_P, C.c_double, _P, C.c_double, _P]
         _I = C.c_int
@@ -258,11 +260,14 @@ class Context:
             _check(st, "cfp_solve_fgmres")
         return info
 
-    def tune_apply(self, precision=PREC_MIXED, rows=0, planes=0):
-        """cfp_tune_apply: the apply's tile shape (rows = planes = 0:
-        autotuned); returns the chosen shape's ms per launch."""
+    def tune_apply(self, precision=PREC_MIXED, rows=0, planes=0, kernel=None):
+        """cfp_tune_apply: the apply's kernel and tile shape (all 0:
+        autotuned; kernel defaults to APPLY_STREAM when a shape is given);
+        returns the chosen one's ms per launch."""
+        if kernel is None:
+            kernel = 0 if not (rows or planes) else APPLY_STREAM
         ms = C.c_double()
-        _check(lib().cfp_tune_apply(self._h, int(precision), int(rows), int(planes), C.byref(ms)),
+        _check(lib().cfp_tune_apply(self._h, int(precision), int(kernel), int(rows), int(planes), C.byref(ms)),
                "cfp_tune_apply")
         return ms.value
 
@@ -293,10 +298,11 @@ class Context:
         except Exception:
             pass
 
-    def _field(self, t, name):
+    def _field(self, t, name, dtype=None):
         import torch
-        if t is None or not t.is_cuda or t.dtype != torch.float64 or t.numel() != self.N:
-            raise ValueError("%s must be a CUDA float64 tensor with %d elements" % (name, self.N))
+        dtype = torch.float64 if dtype is None else dtype
+        if t is None or not t.is_cuda or t.dtype != dtype or t.numel() != self.N:
+            raise ValueError("%s must be a CUDA %s tensor with %d elements" % (name, dtype, self.N))
         return _ptr(t)
 
     def classify_points(self, type_out=None):
@@ -337,6 +343,13 @@ class Context:
 
     def apply(self, x, y):
         _check(lib().cfp_apply(self._h, self._field(x, "x"), self._field(y, "y")), "cfp_apply")
+        return y
+
+    def apply_f32(self, x, y):
+        """cfp_apply_f32: y = B x in FP32 (float32 tensors)."""
+        import torch
+        _check(lib().cfp_apply_f32(self._h, self._field(x, "x", torch.float32), self._field(y, "y", torch.float32)),
+               "cfp_apply_f32")
         return y
 
     def precondition(self, rho, phi, sweeps=8):

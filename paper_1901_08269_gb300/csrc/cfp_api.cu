@@ -214,9 +214,9 @@ cfp_status cfp_assemble_rhs(cfp_ctx* c, const double* f, const double* g, const 
     if (c->n_ibi > 0) CFP_TRY(need_field(gi, "g_ibi_dev"));
     CFP_TRY(ensure_work(c, false));
     const int64_t N = c->N;
-    double* gb = c->v64 + V_TMP * N;
-    double* bg = c->v64 + V_TMP2 * N;
-    double* qf = c->v64 + V_T * N;
+    double* gb = c->v64 + V_TMP * vstride(c);
+    double* bg = c->v64 + V_TMP2 * vstride(c);
+    double* qf = c->v64 + V_T * vstride(c);
     if (rhs == gb || rhs == bg || rhs == qf) return fail(CFP_EINVAL, "rhs aliases the context's work space");
     launch_boundary_lift(c, g, gb, c->stream);
     launch_apply_lift(c, gb, bg, c->stream);
@@ -237,6 +237,18 @@ cfp_status cfp_apply(cfp_ctx* c, const double* x, double* y) {
     return CFP_OK;
 }
 
+cfp_status cfp_apply_f32(cfp_ctx* c, const float* x, float* y) {
+    CFP_TRY(need_classified(c));
+    CFP_TRY(need_field(x, "x_dev"));
+    CFP_TRY(need_field(y, "y_dev"));
+    if (x == y) return fail(CFP_EINVAL, "x and y must not overlap");
+    setup_apply_ring(c);
+    CFP_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * c->N, c->stream));
+    launch_apply<float>(c, x, y, nullptr, 0, nullptr, c->stream, nullptr);
+    CFP_CUDA(cudaGetLastError());
+    return check_waits(c);
+}
+
 cfp_status cfp_precondition(cfp_ctx* c, int sweeps, const double* rho, double* phi) {
     CFP_TRY(need_classified(c));
     CFP_TRY(need_field(rho, "rho_dev"));
@@ -244,7 +256,7 @@ cfp_status cfp_precondition(cfp_ctx* c, int sweeps, const double* rho, double* p
     if (sweeps < 0) return fail(CFP_EINVAL, "sweeps must be >= 0");
     if (rho == phi) return fail(CFP_EINVAL, "rho and phi must not overlap");
     CFP_TRY(ensure_work(c, false));
-    if (phi == c->v64 + (int64_t)V_TMP2 * c->N) return fail(CFP_EINVAL, "phi aliases the context's work space");
+    if (phi == c->v64 + (int64_t)V_TMP2 * vstride(c)) return fail(CFP_EINVAL, "phi aliases the context's work space");
     if (sweeps > 0) CFP_TRY(ensure_mg(c, 0));
     CFP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * c->N, c->stream));
     c->precond_kind = CFP_PRECOND_RBGS;
@@ -267,7 +279,7 @@ cfp_status cfp_precondition_ex(cfp_ctx* c, const cfp_opts* o, const double* rho,
     if (rho == phi) return fail(CFP_EINVAL, "rho and phi must not overlap");
     const int prec = opts.precision == CFP_PREC_MIXED ? 1 : 0;
     CFP_TRY(ensure_work(c, prec == 1));
-    if (phi == c->v64 + (int64_t)V_TMP2 * c->N) return fail(CFP_EINVAL, "phi aliases the context's work space");
+    if (phi == c->v64 + (int64_t)V_TMP2 * vstride(c)) return fail(CFP_EINVAL, "phi aliases the context's work space");
     c->precond_kind = opts.precond;
     c->mg_smooth = std::max(1, opts.mg_smooth);
     c->mg_post = opts.mg_post > 0 ? opts.mg_post : c->mg_smooth;
@@ -337,10 +349,10 @@ cfp_status cfp_time_kernel(cfp_ctx* c, int kernel, int precision, int reps, doub
     return time_kernel(c, kernel, precision, reps, ms, bytes);
 }
 
-cfp_status cfp_tune_apply(cfp_ctx* c, int precision, int rows, int planes, double* ms) {
+cfp_status cfp_tune_apply(cfp_ctx* c, int precision, int kernel, int rows, int planes, double* ms) {
     CFP_TRY(need_classified(c));
     if (precision != CFP_PREC_FP64 && precision != CFP_PREC_MIXED) return fail(CFP_EINVAL, "bad precision");
-    return tune_apply(c, precision, rows, planes, 5, ms);
+    return tune_apply(c, precision, kernel, rows, planes, 5, ms);
 }
 
 cfp_status cfp_vec_dot(cfp_ctx* c, const double* a, const double* b, double* out) {

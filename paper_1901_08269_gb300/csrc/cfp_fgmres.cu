@@ -481,8 +481,8 @@ extern "C" cfp_status cfp_solve_fgmres(cfp_ctx* c, cfp_unet* net, const double* 
         if (net) unet_use_stream(net, net_prev);
     };
 
-    double* rhs = c->v64 + V_RHS * N;
-    double* X = c->v64 + V_X * N;
+    double* rhs = c->v64 + V_RHS * vstride(c);
+    double* X = c->v64 + V_X * vstride(c);
     const auto t1 = clk::now();
     cfp_status s = cfp_assemble_rhs(c, f, gn, gi, rhs);
     if (s) {

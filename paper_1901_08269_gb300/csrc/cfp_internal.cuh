@@ -229,9 +229,11 @@ struct cfp_ctx {
     // kernels enqueued since the context was created
     int64_t launches = 0;
 
-    // the apply's tile shape per precision (0 FP64, 1 FP32): rows per thread
-    // (2 or 4) and planes per z chunk (16, 32 or 64); 0: the defaults (set by
-    // the autotuner)
+    // the apply's kernel and tile shape per precision (0 FP64, 1 FP32):
+    // CFP_APPLY_STREAM (rows per thread 2 or 4) or CFP_APPLY_RING (FP32, 8
+    // rows per tile), planes per z chunk (16, 32 or 64); 0: the defaults (set
+    // by the autotuner)
+    int apply_kind[2] = {0, 0};
     int apply_ty[2] = {0, 0};
     int apply_kc[2] = {0, 0};
 
@@ -241,6 +243,7 @@ struct cfp_ctx {
     int mg_post = 2;
     int mg_tma = 1;            // 1: TMA-fed FP32 half-sweeps where a level supports them
     int* dwait = nullptr;      // device word: nonzero once a bounded pipeline wait timed out
+    int ring_grid = 0;         // CTAs of the apply ring's persistent grid (0: not set up)
     std::vector<cfp::MgLevel> mg;
     // ILU(0) of K (CFP_PRECOND_ILU): [pivots | work field], FP64 and FP32
     double* ilu64 = nullptr;
@@ -257,6 +260,9 @@ struct cfp_ctx {
 namespace cfp {
 
 constexpr int kNV64 = 12;  // x r rh p ph v s sh t rhs tmp tmp2
+// distance between two work fields in v64 / v32: N rounded up to 64 entries,
+// so that every field starts 256-byte aligned (bulk copies want 16)
+inline int64_t vstride(const cfp_ctx* c) { return (c->N + 63) / 64 * 64; }
 constexpr int kNV32 = 9;   // x r rh p ph v s sh t
 enum { V_X = 0, V_R, V_RH, V_P, V_PH, V_V, V_S, V_SH, V_T, V_RHS, V_TMP, V_TMP2 };
 
@@ -313,7 +319,9 @@ void launch_metrics(cfp_ctx* c);  // Eq. app_xxx and Eq. 2ndorder_coef per axis
 // Krylov (cfp_krylov.cu)
 cfp_status ensure_work(cfp_ctx* c, bool need32);
 cfp_status time_kernel(cfp_ctx* c, int kernel, int prec, int reps, double* ms, double* bytes);
-cfp_status tune_apply(cfp_ctx* c, int prec, int rows, int planes, int reps, double* best_ms);
+cfp_status tune_apply(cfp_ctx* c, int prec, int kind, int rows, int planes, int reps, double* best_ms);
+// sets up the FP32 apply ring (shared-memory limit, persistent grid); false if unusable
+bool setup_apply_ring(cfp_ctx* c);
 // phi = P(rho) in FP32 (the mixed solve's inner preconditioner) for FP64
 // fields: rho rounded to FP32, phi widened back; phi zeroed first
 cfp_status precondition32(cfp_ctx* c, int sweeps, const double* rho, double* phi);

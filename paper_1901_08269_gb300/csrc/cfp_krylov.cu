@@ -231,13 +231,13 @@ struct Vecs {
 
 Vecs<double> vecs64(cfp_ctx* c) {
     double* b = c->v64;
-    const int64_t N = c->N;
+    const int64_t N = vstride(c);
     return Vecs<double>{b + V_X * N, b + V_R * N, b + V_RH * N, b + V_P * N, b + V_PH * N,
                         b + V_V * N, b + V_S * N, b + V_SH * N, b + V_T * N};
 }
 Vecs<float> vecs32(cfp_ctx* c) {
     float* b = c->v32;
-    const int64_t N = c->N;
+    const int64_t N = vstride(c);
     return Vecs<float>{b + 0 * N, b + 1 * N, b + 2 * N, b + 3 * N, b + 4 * N, b + 5 * N, b + 6 * N, b + 7 * N, b + 8 * N};
 }
 template <class T>
@@ -366,7 +366,7 @@ double* scalar_slot(cfp_ctx* c, int q) { return reinterpret_cast<double*>(c->dto
 
 // ||b - B x||^2 with out = b - B x (FP64)
 cfp_status true_residual(cfp_ctx* c, const double* b, const double* x, double* out, double* r2) {
-    double* tmp = c->v64 + V_TMP2 * c->N;
+    double* tmp = c->v64 + V_TMP2 * vstride(c);
     launch_apply<double>(c, x, tmp, nullptr, 0, nullptr, c->stream, nullptr);
     k_resid<<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(b, tmp, out, c->partial, c->N);
     k_fin_store<<<1, 256, 0, c->stream>>>(c->partial, kUpdBlocks, scalar_slot(c, 6));
@@ -425,12 +425,13 @@ cfp_status vec_axpby(cfp_ctx* c, double alpha, const double* x, double beta, dou
 cfp_status ensure_work(cfp_ctx* c, bool need32) {
     const int64_t N = c->N;
     if (!c->v64) {
-        CFP_CUDA(cudaMalloc(&c->v64, sizeof(double) * N * kNV64));
-        CFP_CUDA(cudaMemsetAsync(c->v64, 0, sizeof(double) * N * kNV64, c->stream));
+        CFP_CUDA(cudaMalloc(&c->v64, sizeof(double) * vstride(c) * kNV64));
+        CFP_CUDA(cudaMemsetAsync(c->v64, 0, sizeof(double) * vstride(c) * kNV64, c->stream));
     }
+    if (need32) setup_apply_ring(c);
     if (need32 && !c->v32) {
-        CFP_CUDA(cudaMalloc(&c->v32, sizeof(float) * N * (kNV32 + 1)));  // + the FP32 right-hand side
-        CFP_CUDA(cudaMemsetAsync(c->v32, 0, sizeof(float) * N * (kNV32 + 1), c->stream));
+        CFP_CUDA(cudaMalloc(&c->v32, sizeof(float) * vstride(c) * (kNV32 + 1)));  // + the FP32 right-hand side
+        CFP_CUDA(cudaMemsetAsync(c->v32, 0, sizeof(float) * vstride(c) * (kNV32 + 1), c->stream));
     }
     return ensure_partial(c);
 }
@@ -475,36 +476,49 @@ cfp_status time_kernel_t(cfp_ctx* c, int prec, int kernel, int reps, double* ms,
 }
 }  // namespace
 
-// Tile autotuner of the apply: rows per thread x planes per z chunk, each
-// candidate timed over `reps` launches (after two untimed) with the fused
-// (r_hat0, v) dot, the fastest kept in the context.  rows, planes > 0: that
-// shape is set and timed only.
-cfp_status tune_apply(cfp_ctx* c, int prec, int rows, int planes, int reps, double* best_ms) {
+// Autotuner of the apply: kernel (streaming with 2 or 4 rows per thread, or
+// the FP32 ring with 2 rows per tile) x planes per z chunk, each candidate
+// timed over `reps` launches (after two untimed) with the fused (r_hat0, v)
+// dot, the fastest kept in the context.  kind, rows, planes > 0: that choice
+// is set and timed only.
+cfp_status tune_apply(cfp_ctx* c, int prec, int kind, int rows, int planes, int reps, double* best_ms) {
     const int q = prec == CFP_PREC_MIXED ? 1 : 0;
-    std::vector<std::pair<int, int>> cand;
-    if (rows > 0 || planes > 0) {
-        if ((rows != 2 && rows != 4) || (planes != 16 && planes != 32 && planes != 64))
-            return fail(CFP_EINVAL, "apply tile: rows 2 or 4, planes 16, 32 or 64");
-        cand.push_back({rows, planes});
+    struct Choice {
+        int kind, ty, kc;
+    };
+    const bool ring = q == 1 && setup_apply_ring(c);
+    std::vector<Choice> cand;
+    if (kind > 0 || rows > 0 || planes > 0) {
+        const bool shape = kind == CFP_APPLY_STREAM ? (rows == 2 || rows == 4) && (planes == 16 || planes == 32 || planes == 64)
+                                                    : kind == CFP_APPLY_RING && rows == 2 && (planes == 32 || planes == 64);
+        if (!shape)
+            return fail(CFP_EINVAL, "apply: kernel 1 with rows 2 or 4 and planes 16, 32 or 64, or kernel 2 with "
+                                    "rows 2 and planes 32 or 64");
+        if (kind == CFP_APPLY_RING && !ring)
+            return fail(CFP_EINVAL, "apply ring: FP32 only, and its launch could not be set up");
+        cand.push_back({kind, rows, planes});
     } else {
         for (int r : {2, 4})
-            for (int k : {16, 32, 64}) cand.push_back({r, k});
+            for (int k : {16, 32, 64}) cand.push_back({CFP_APPLY_STREAM, r, k});
+        if (ring)
+            for (int k : {32, 64}) cand.push_back({CFP_APPLY_RING, 2, k});
     }
     double best = INFINITY;
-    int br = 0, bk = 0;
-    for (auto [r, k] : cand) {
-        c->apply_ty[q] = r;
-        c->apply_kc[q] = k;
+    Choice bs{CFP_APPLY_STREAM, 0, 0};
+    for (const Choice& ch : cand) {
+        c->apply_kind[q] = ch.kind;
+        c->apply_ty[q] = ch.ty;
+        c->apply_kc[q] = ch.kc;
         double ms = 0.0;
         CFP_TRY(time_kernel(c, CFP_KERNEL_APPLY, prec, reps, &ms, nullptr));
         if (ms < best) {
             best = ms;
-            br = r;
-            bk = k;
+            bs = ch;
         }
     }
-    c->apply_ty[q] = br;
-    c->apply_kc[q] = bk;
+    c->apply_kind[q] = bs.kind;
+    c->apply_ty[q] = bs.ty;
+    c->apply_kc[q] = bs.kc;
     if (best_ms) *best_ms = best;
     return CFP_OK;
 }
@@ -528,14 +542,14 @@ cfp_status check_waits(cfp_ctx* c) {
     if (w == 0) return CFP_OK;
     CFP_CUDA(cudaMemsetAsync(c->dwait, 0, sizeof(int), c->stream));
     CFP_CUDA(cudaStreamSynchronize(c->stream));
-    return fail(CFP_ECUDA, "a shared-memory pipeline wait of the multigrid smoother timed out (code " +
+    return fail(CFP_ECUDA, "a shared-memory pipeline wait (multigrid smoother or apply ring) timed out (code " +
                                std::to_string(w) + "); the results of that call are not valid");
 }
 
 cfp_status precondition32(cfp_ctx* c, int sweeps, const double* rho, double* phi) {
     const int64_t N = c->N;
-    float* rho32 = c->v32 + (int64_t)V_R * N;
-    float* phi32 = c->v32 + (int64_t)V_PH * N;
+    float* rho32 = c->v32 + (int64_t)V_R * vstride(c);
+    float* phi32 = c->v32 + (int64_t)V_PH * vstride(c);
     k_to32<<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(rho, rho32, 1.0, N);
     k_zero<float><<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(phi32, N);
     launch_precond<float>(c, sweeps, rho32, phi32, c->stream);
@@ -577,9 +591,9 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
     if (c->precond_kind == CFP_PRECOND_ILU) CFP_TRY(ensure_ilu(c, mixed ? 1 : 0));
     CFP_TRY(ensure_work(c, mixed));
     const int64_t N = c->N;
-    double* rhs = c->v64 + V_RHS * N;
-    double* tmp = c->v64 + V_TMP * N;
-    double* X = c->v64 + V_X * N;
+    double* rhs = c->v64 + V_RHS * vstride(c);
+    double* tmp = c->v64 + V_TMP * vstride(c);
+    double* X = c->v64 + V_X * vstride(c);
     const auto t1 = clk::now();
     cfp_status st = cfp_assemble_rhs(c, f, g, gi, rhs);
     if (st) return st;
@@ -617,7 +631,7 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
     } else {
         // Iterative refinement: FP64 residual (with the FP64 irregular rows),
         // FP32 correction solve, FP64 update.
-        float* b32 = c->v32 + kNV32 * N;
+        float* b32 = c->v32 + kNV32 * vstride(c);
         float* e32 = c->v32;  // the x vector of the FP32 run
         double r2 = b2;
         const double* res = rhs;  // the current residual

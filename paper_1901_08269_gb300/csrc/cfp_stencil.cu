@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "cfp_internal.cuh"
+#include "cfp_tc.cuh"
 
 namespace cfp {
 
@@ -83,6 +84,14 @@ __device__ __forceinline__ void block_reduce2(double& a, double& b) {
         }
     }
 }
+
+// Fused multiply-add in either precision: the apply's sums are written as
+// explicit chains so that every tile shape (and the packed FP32 kernel)
+// rounds each row the same way.
+__device__ __forceinline__ float fmat(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mult(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mult(double a, double b) { return __dmul_rn(a, b); }
 
 // Regular part of B x at the unknowns.  One thread owns the column i of TY
 // consecutive rows j and marches the planes k0 .. k1 - 1 of its z chunk (KC
@@ -199,8 +208,8 @@ __global__ void __launch_bounds__(kAX, TY == 2 ? (sizeof(T) == 4 ? 8 : 2) : (siz
         T XR[R], XL[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            XR[r] = arx * c[3 * r] + brx * c[3 * r + 1] + crx * c[3 * r + 2];
-            XL[r] = ax * c[3 * r] + c[3 * r + 1] + cx * c[3 * r + 2];
+            XR[r] = fmat(crx, c[3 * r + 2], fmat(brx, c[3 * r + 1], mult(arx, c[3 * r])));
+            XL[r] = fmat(cx, c[3 * r + 2], fmat(ax, c[3 * r], c[3 * r + 1]));
         }
 #pragma unroll
         for (int t = 0; t < TY; ++t) {
@@ -208,9 +217,10 @@ __global__ void __launch_bounds__(kAX, TY == 2 ? (sizeof(T) == 4 ? 8 : 2) : (siz
             P0[t] = Pp[t];
             Qm[t] = Q0[t];
             Q0[t] = Qp[t];
-            Pp[t] = ay[t] * XR[t] + XR[t + 1] + cy[t] * XR[t + 2] + ary[t] * XL[t] + bry[t] * XL[t + 1] +
-                    cry[t] * XL[t + 2];
-            Qp[t] = ay[t] * XL[t] + XL[t + 1] + cy[t] * XL[t + 2];
+            Pp[t] = fmat(cry[t], XL[t + 2],
+                         fmat(bry[t], XL[t + 1],
+                              fmat(ary[t], XL[t], fmat(cy[t], XR[t + 2], fmat(ay[t], XR[t], XR[t + 1])))));
+            Qp[t] = fmat(cy[t], XL[t + 2], fmat(ay[t], XL[t], XL[t + 1]));
         }
         if (kk >= k0 + 1 && iin) {
             const int k = kk - 1, kl = k - k0;
@@ -219,7 +229,7 @@ __global__ void __launch_bounds__(kAX, TY == 2 ? (sizeof(T) == 4 ? 8 : 2) : (siz
 #pragma unroll
             for (int t = 0; t < TY; ++t) {
                 if (!jin[t]) continue;
-                T v = az * Pm[t] + P0[t] + cz * Pp[t] + (arz * Qm[t] + brz * Q0[t] + crz * Qp[t]);
+                T v = fmat(cz, Pp[t], fmat(az, Pm[t], P0[t])) + fmat(crz, Qp[t], fmat(brz, Q0[t], mult(arz, Qm[t])));
                 const unsigned l = (unsigned)k * sz + (unsigned)(j0 + t) * sy + (unsigned)i;
                 if (t_cur[t] == CFP_SOLID) v = 0;  // irregular rows: k_apply_corr adds their corrections
                 y[l] = v;
@@ -238,6 +248,318 @@ __global__ void __launch_bounds__(kAX, TY == 2 ? (sizeof(T) == 4 ? 8 : 2) : (siz
         }
     }
 }
+// The FP32 apply fed by a ring of bulk copies (the TMA engine) through shared
+// memory.  The streaming kernel above keeps one plane of loads in flight per
+// thread, too few bytes per SM to cover the HBM latency.  Here a producer
+// warp copies each plane of a tile several planes ahead of the consumers
+// into one of kRingStages stages: the x rows j0-1 .. j0+2 with their halo
+// columns, and for the output planes the dot operand and the type bytes of
+// the rows j0, j0+1.  A tile is 512 columns x 2 rows x KC planes.  When it
+// spans the whole row width (n_x <= 514), its rows are contiguous in the
+// natural layout and each array's rows of a plane are one bulk copy; wider
+// grids copy row by row.  Rows start at any 4-byte offset (n_x is odd in the
+// benchmark grids), so each copy starts at the 16-byte boundary at or below
+// its first element and the consumers add that offset.  A copy never passes
+// the array's last 16-byte boundary; the elements after it (at the end of
+// the array only) are stored into the stage by the producer lane itself.
+// Tiles go to a persistent grid, rows fastest within a z chunk; 256 consumer
+// threads own columns i0 + lx and i0 + 256 + lx of both rows and march the
+// planes with the same sum-factorised arithmetic and fused multiply-add
+// chains as k_apply<float>, so both give the same bits.  Solid rows are zero;
+// irregular rows get their corrections from k_apply_corr.
+// A wait that runs out (1 s) records a code in *wait_err (31: producer, stage
+// free; 32: producer, final drain; 33: consumer, stage filled).  A producer
+// whose wait ran out issues no further copy and waits (bounded) for the
+// copies it issued; a consumer whose wait ran out stops waiting (every index
+// stays in bounds whatever a stage holds), so the launch still ends.
+constexpr int kRingTX = 512;                // columns per tile
+constexpr int kRingRows = 2;                // rows per tile
+constexpr int kRingCons = 256;              // consumer threads: two columns each
+constexpr int kRingThreads = kRingCons + 32;
+constexpr int kRingStages = 6;
+constexpr int kRingSpanNx = kRingTX + 2;    // widest grid copied as whole-plane spans
+constexpr int kRingXRow = 520;              // floats per x row (row-by-row copies): 514 + alignment
+constexpr int kRingDRow = 516;              // floats per dot-operand row: 512 + alignment
+constexpr int kRingTRow = 528;              // bytes per type row: 512 + alignment
+constexpr int kRingXBytes = 8320;           // >= 4 x-rows either way (span: 4 n_x + 6 floats)
+constexpr int kRingDBytes = 4160;           // >= 2 dot rows either way (span: 2 n_x + 6 floats)
+constexpr int kRingTBytes = 1088;           // >= 2 type rows either way (span: 2 n_x + 30 bytes)
+constexpr int kRingDOff = kRingXBytes, kRingTOff = kRingDOff + kRingDBytes;
+constexpr int kRingStage = kRingTOff + kRingTBytes;
+constexpr int kRingSmem = kRingStages * kRingStage + 2 * kRingStages * 8;  // + barriers
+static_assert(kRingXBytes >= (kRingRows + 2) * kRingXRow * 4 && kRingXBytes >= (4 * kRingSpanNx + 8) * 4 &&
+                  kRingDBytes >= kRingRows * kRingDRow * 4 && kRingDBytes >= (2 * kRingSpanNx + 8) * 4 &&
+                  kRingTBytes >= kRingRows * kRingTRow && kRingTBytes >= 2 * kRingSpanNx + 32,
+              "stage regions hold either copy pattern");
+static_assert(kRingStage % 128 == 0 && kRingDOff % 16 == 0 && kRingTOff % 16 == 0 && kRingXRow % 4 == 0 &&
+                  kRingDRow % 4 == 0 && kRingTRow % 16 == 0,
+              "bulk copies want 16-byte destinations");
+
+// Elements e .. e + want - 1 of an array of n elements of esize bytes into
+// the stage at dst, which receives the array from e0 = the 16-byte boundary
+// at or below e onward.  The bulk copy stops at the array's last 16-byte
+// boundary (and at the end of what is wanted, rounded up); the producer lane
+// stores the remaining elements itself.  Returns the bytes the bulk copy
+// delivers (0: none to issue) and its source in *src_out.
+__device__ __forceinline__ unsigned ring_copy(unsigned char* dst, const unsigned char* base, int64_t e, int want,
+                                              int esize, int64_t n, const unsigned char** src_out) {
+    const int per16 = 16 / esize;
+    const int64_t e0 = e & ~(int64_t)(per16 - 1);
+    const int64_t end = e + want;                   // one past the last wanted element
+    const int64_t nal = n & ~(int64_t)(per16 - 1);  // the array's last 16-byte boundary, in elements
+    int64_t stop = (end + per16 - 1) & ~(int64_t)(per16 - 1);
+    if (stop > nal) stop = nal;
+    bool tail = false;
+    for (int64_t q = max(stop, e0); q < min(end, n); ++q) {  // the tail after the last boundary
+        for (int b = 0; b < esize; ++b) dst[(q - e0) * esize + b] = base[q * esize + b];
+        tail = true;
+    }
+    // order these generic stores before later bulk (async-proxy) writes into
+    // the stage; only the rare copies with a tail pay for the fence
+    if (tail) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    *src_out = base + e0 * esize;
+    return stop > e0 ? (unsigned)((stop - e0) * esize) : 0u;
+}
+
+// Packed FP32 pairs: the halves are the two columns a ring consumer thread
+// owns, and one fma.rn.f32x2 instruction does the (IEEE, round-to-nearest)
+// arithmetic of both, with the results of two scalar fmaf calls.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2b(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+// DotAcc<float> on both halves at once: a running sum and its lost
+// low-order part per column
+struct DotAcc2 {
+    float2 s = {0.f, 0.f}, c = {0.f, 0.f};
+    __device__ __forceinline__ void add(float2 x, float2 y) {
+        const float2 v = fma2(x, y, make_float2(-c.x, -c.y));
+        const float2 t = add2(s, v);
+        c = sub2(sub2(t, s), v);
+        s = t;
+    }
+    __device__ __forceinline__ double total() const {
+        return ((double)s.x - (double)c.x) + ((double)s.y - (double)c.y);
+    }
+};
+
+template <int DOT, int KC, bool SPAN>
+__global__ void __launch_bounds__(kRingThreads, 2)
+    k_apply_ring(Grid<float> G, const uint8_t* __restrict__ type, const float* __restrict__ x, float* __restrict__ y,
+                 const float* __restrict__ d0, double* __restrict__ partial, int ntx, int nty, int ntz,
+                 int* __restrict__ wait_err) {
+    using namespace tc;
+    // indexed from the __shared__ array itself, so that every stage access
+    // is a shared-memory load with a 32-bit address
+    extern __shared__ __align__(16) unsigned char ring_smem[];
+    const float* sf = reinterpret_cast<const float*>(ring_smem);
+    uint64_t* full = reinterpret_cast<uint64_t*>(ring_smem + kRingStages * kRingStage);  // filled: 32 producer lanes
+    uint64_t* empty = full + kRingStages;  // released by the consumer warps
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kRingStages; ++q) {
+            mbar_init(&full[q], 32);
+            mbar_init(&empty[q], kRingCons / 32);
+        }
+        mbar_fence_init();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const unsigned sy = (unsigned)nx, sz = (unsigned)nx * (unsigned)ny;
+    const int64_t N = (int64_t)sz * nz;
+    const int ntiles = ntx * nty * ntz;
+    DotAcc2 dacc0, dacc1;
+    if (warp == kRingCons / 32) {
+        // producer warp.  SPAN (n_x <= 514, one tile column): lane 0 copies
+        // x, lane 1 the dot operand, lane 2 the type bytes, each as one span
+        // of whole rows.  Otherwise lanes 0-3 copy the x rows, 4-5 the dot
+        // rows, 6-7 the type rows.  Every lane arrives on the stage's barrier
+        // once per plane with the bytes its copy will deliver.
+        constexpr int nxl = SPAN ? 1 : kRingRows + 2, per = SPAN ? 1 : kRingRows;
+        const bool xl = lane < nxl, dl = !xl && lane < nxl + per, tl = !xl && !dl && lane < nxl + 2 * per;
+        const int r = xl ? lane : dl ? lane - nxl : lane - nxl - per;  // row of a row copy
+        const unsigned char* arr = xl ? (const unsigned char*)x : dl ? (const unsigned char*)d0 : type;
+        const int esize = tl ? 1 : 4;
+        const int dst_off = xl ? r * kRingXRow * 4 : dl ? kRingDOff + r * kRingDRow * 4 : kRingTOff + r * kRingTRow;
+        unsigned g = 0;  // planes issued; plane g uses stage g % kRingStages
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int tyi = tile % nty, rest = tile / nty, tx = rest % ntx, tz = rest / ntx;
+            const int i0 = 1 + tx * kRingTX, j0 = 1 + tyi * kRingRows, k0 = 1 + tz * KC;
+            const int k1 = min(k0 + KC, nz - 1);
+            int64_t rowe;  // the copy's first element within a plane
+            int w;         // elements wanted
+            if (SPAN) {
+                rowe = (int64_t)(xl ? j0 - 1 : j0) * sy;
+                w = xl ? min(4, ny - (j0 - 1)) * nx : 2 * nx;  // the rows that exist
+            } else {
+                rowe = xl ? (int64_t)min(j0 - 1 + r, ny - 1) * sy + (i0 - 1) : (int64_t)min(j0 + r, ny - 2) * sy + i0;
+                w = xl ? kRingTX + 2 : kRingTX;
+            }
+            for (int k = k0 - 1; k <= k1; ++k, ++g) {
+                const int st = g % kRingStages;
+                if (g >= kRingStages) {  // refill only a stage every consumer warp released
+                    bool okw = true;
+                    if (lane == 0) okw = mbar_wait(&empty[st], ((g / kRingStages) - 1) & 1);
+                    if (!__shfl_sync(0xffffffffu, okw, 0)) {
+                        ok = false;
+                        if (lane == 0) atomicExch(wait_err, 31);
+                        break;
+                    }
+                }
+                const bool outp = k >= k0 && k < k1;  // an output plane
+                const bool act = xl || (outp && (tl || (dl && DOT)));
+                unsigned bytes = 0;
+                const unsigned char* src = nullptr;
+                unsigned char* dst = ring_smem + st * kRingStage + dst_off;
+                if (act) bytes = ring_copy(dst, arr, (int64_t)k * sz + rowe, w, esize, N, &src);
+                mbar_arrive_expect_tx(&full[st], bytes);
+                if (bytes) bulk_load(dst, src, bytes, &full[st]);
+            }
+        }
+        // every copy issued has landed before the CTA may end (after a
+        // timeout too): only the last kRingStages planes can be in flight
+        if (lane == 0)
+            for (unsigned q = g > (unsigned)kRingStages ? g - kRingStages : 0; q < g; ++q)
+                if (!mbar_wait(&full[q % kRingStages], (q / kRingStages) & 1)) atomicExch(wait_err, 32);
+        __syncwarp();
+    } else {
+        // consumer: columns i0 + lx (low half) and i0 + 256 + lx (high half)
+        // of the rows j0, j0 + 1
+        const int lx = threadIdx.x;
+        unsigned g = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int tyi = tile % nty, rest = tile / nty, tx = rest % ntx, tz = rest / ntx;
+            const int i0 = 1 + tx * kRingTX, j0 = 1 + tyi * kRingRows, k0 = 1 + tz * KC;
+            const int k1 = min(k0 + KC, nz - 1);
+            const int c = i0 + lx;  // the low half's column; the high half's is c + 256
+            const bool in0 = c <= nx - 2, in1 = c + kRingCons <= nx - 2;
+            const int c0i = in0 ? c : nx - 2, c1i = in1 ? c + kRingCons : nx - 2;
+            const float2 AX = f2(G.ax[0].a[c0i], G.ax[0].a[c1i]), CX = f2(G.ax[0].c[c0i], G.ax[0].c[c1i]);
+            const float2 ARX = f2(G.ax[0].ar[c0i], G.ax[0].ar[c1i]), BRX = f2(G.ax[0].br[c0i], G.ax[0].br[c1i]);
+            const float2 CRX = f2(G.ax[0].cr[c0i], G.ax[0].cr[c1i]);
+            float2 AY[2], CY[2], ARY[2], BRY[2], CRY[2];
+            bool jin[2];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                jin[t] = j0 + t <= ny - 2;
+                const int jc = min(j0 + t, ny - 2);
+                AY[t] = f2b(G.ax[1].a[jc]);
+                CY[t] = f2b(G.ax[1].c[jc]);
+                ARY[t] = f2b(G.ax[1].ar[jc]);
+                BRY[t] = f2b(G.ax[1].br[jc]);
+                CRY[t] = f2b(G.ax[1].cr[jc]);
+            }
+            // stage positions: element (row q, column col) of a plane at
+            // xb[q] + ((kp + xa[q]) & 3) + col, kp = the plane's first element
+            // (SPAN: one offset for all rows); likewise for the output rows
+            int xb[4], db[2], tb[2];
+            unsigned xa[4], da[2], ta[2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                xb[q] = SPAN ? q * nx : q * kRingXRow - (i0 - 1);
+                xa[q] = SPAN ? ((unsigned)(j0 - 1) * sy) & 3u
+                             : ((unsigned)min(j0 - 1 + q, ny - 1) * sy + (unsigned)(i0 - 1)) & 3u;
+            }
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const unsigned jr = SPAN ? (unsigned)j0 : (unsigned)min(j0 + t, ny - 2);
+                db[t] = SPAN ? t * nx : t * kRingDRow - i0;
+                tb[t] = SPAN ? t * nx : t * kRingTRow - i0;
+                da[t] = (jr * sy + (SPAN ? 0u : (unsigned)i0)) & 3u;
+                ta[t] = (jr * sy + (SPAN ? 0u : (unsigned)i0)) & 15u;
+            }
+            float2 Pm[2], P0[2], Pp[2], Qm[2], Q0[2], Qp[2];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) Pm[t] = P0[t] = Pp[t] = Qm[t] = Q0[t] = Qp[t] = f2b(0.f);
+            // z coefficients of the plane the next step outputs, loaded a step ahead
+            float zn[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int kk = k0 - 1; kk <= k1; ++kk) {
+                const float2 AZ = f2b(zn[0]), CZ = f2b(zn[1]), ARZ = f2b(zn[2]), BRZ = f2b(zn[3]), CRZ = f2b(zn[4]);
+                if (kk < k1) {
+                    const int kn = max(kk, 1);
+                    zn[0] = G.ax[2].a[kn];
+                    zn[1] = G.ax[2].c[kn];
+                    zn[2] = G.ax[2].ar[kn];
+                    zn[3] = G.ax[2].br[kn];
+                    zn[4] = G.ax[2].cr[kn];
+                }
+                const unsigned gp = g + (unsigned)(kk - (k0 - 1));
+                const unsigned st = gp % kRingStages;
+                if (ok && !mbar_wait(&full[st], (gp / kRingStages) & 1)) {
+                    ok = false;
+                    atomicExch(wait_err, 33);
+                }
+                const unsigned kp = (unsigned)kk * sz;
+                const float* xs = sf + st * (kRingStage / 4) + c;
+                float2 XR[4], XL[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float* row = xs + xb[q] + (int)((kp + xa[SPAN ? 0 : q]) & 3u);
+                    const float2 xm = f2(row[-1], row[kRingCons - 1]), x0 = f2(row[0], row[kRingCons]),
+                                 xp = f2(row[1], row[kRingCons + 1]);
+                    XR[q] = fma2(CRX, xp, fma2(BRX, x0, mul2(ARX, xm)));
+                    XL[q] = fma2(CX, xp, fma2(AX, xm, x0));
+                }
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    Pm[t] = P0[t];
+                    P0[t] = Pp[t];
+                    Qm[t] = Q0[t];
+                    Q0[t] = Qp[t];
+                    Pp[t] = fma2(CRY[t], XL[t + 2],
+                                 fma2(BRY[t], XL[t + 1],
+                                      fma2(ARY[t], XL[t], fma2(CY[t], XR[t + 2], fma2(AY[t], XR[t], XR[t + 1])))));
+                    Qp[t] = fma2(CY[t], XL[t + 2], fma2(AY[t], XL[t], XL[t + 1]));
+                }
+                if (kk >= k0) {
+                    const unsigned sq = (gp - 1) % kRingStages;  // plane kk - 1: output (from kk = k0 + 1 on), then released
+                    if (kk >= k0 + 1 && in0) {
+                        const unsigned kq = (unsigned)(kk - 1) * sz;
+                        const unsigned char* ts = ring_smem + sq * kRingStage + kRingTOff + c;
+                        const float* ds = sf + sq * (kRingStage / 4) + kRingDOff / 4 + c;
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {
+                            if (!jin[t]) continue;
+                            float2 v = add2(fma2(CZ, Pp[t], fma2(AZ, Pm[t], P0[t])),
+                                            fma2(CRZ, Qp[t], fma2(BRZ, Q0[t], mul2(ARZ, Qm[t]))));
+                            const unsigned char* tr = ts + tb[t] + (int)((kq + ta[SPAN ? 0 : t]) & 15u);
+                            if (tr[0] == CFP_SOLID) v.x = 0.f;  // irregular rows: k_apply_corr
+                            if (!in1 || tr[kRingCons] == CFP_SOLID) v.y = 0.f;
+                            float* yr = y + (kq + (unsigned)(j0 + t) * sy + (unsigned)c);
+                            yr[0] = v.x;
+                            if (in1) yr[kRingCons] = v.y;
+                            if (DOT >= 1) {
+                                const float* dr = ds + db[t] + (int)((kq + da[SPAN ? 0 : t]) & 3u);
+                                dacc0.add(f2(dr[0], in1 ? dr[kRingCons] : 0.f), v);
+                            }
+                            if (DOT == 2) dacc1.add(v, v);
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[sq]);
+                }
+            }
+            __syncwarp();
+            g += (unsigned)(k1 - k0 + 2);
+            if (lane == 0) mbar_arrive(&empty[(g - 1) % kRingStages]);  // the tile's last plane
+        }
+    }
+    if (DOT) {
+        double acc0 = dacc0.total(), acc1 = dacc1.total();
+        block_reduce2(acc0, acc1);
+        if (threadIdx.x == 0) {
+            partial[2 * blockIdx.x] = acc0;
+            partial[2 * blockIdx.x + 1] = acc1;
+        }
+    }
+}
+
 constexpr int kQfRows = 2;  // rows per thread of k_qf
 
 // B gb for a field gb that is zero away from the box (the boundary lift of
@@ -477,11 +799,30 @@ dim3 rows_grid(const cfp_ctx* c, int rows, int kc = kApplyKC) {
                 (unsigned)((c->n[2] - 2 + kc - 1) / kc));
 }
 
-// the apply's tile shape of precision q (0 FP64, 1 FP32): rows per thread
-// and planes per z chunk, as set by the autotuner; otherwise 2 x 64 in FP32
-// and 4 x 64 in FP64, the fastest of the six at 385^3 and 513^3 (measured)
+// the apply's kernel and tile shape of precision q (0 FP64, 1 FP32), as set
+// by the autotuner; otherwise in FP64 the streaming kernel with 4 x 64, in
+// FP32 the ring (2 x 64) where its 512-column tiles are at least 85 % filled
+// (n_x = 513: 511 of 512 columns) and else the streaming kernel with 2 x 64
+// (at 385^3, 383 of 512 columns, it measured 0.285 ms against 0.256 ms)
+int apply_kind(const cfp_ctx* c, int q) {
+    if (c->apply_kind[q]) return c->apply_kind[q];
+    if (q == 1 && c->ring_grid > 0) {
+        const int cols = c->n[0] - 2, tiles = (cols + kRingTX - 1) / kRingTX;
+        if (cols * 100 >= 85 * tiles * kRingTX) return CFP_APPLY_RING;
+    }
+    return CFP_APPLY_STREAM;
+}
 int apply_rows(const cfp_ctx* c, int q) { return c->apply_ty[q] ? c->apply_ty[q] : (q ? 2 : 4); }
 int apply_planes(const cfp_ctx* c, int q) { return c->apply_kc[q] ? c->apply_kc[q] : 64; }
+
+// the ring's tiles: 512 columns x 2 rows x kc planes
+void ring_tiles(const cfp_ctx* c, int kc, int* ntx, int* nty, int* ntz) {
+    *ntx = (c->n[0] - 2 + kRingTX - 1) / kRingTX;
+    *nty = (c->n[1] - 2 + kRingRows - 1) / kRingRows;
+    *ntz = (c->n[2] - 2 + kc - 1) / kc;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
 
@@ -502,7 +843,8 @@ int corr_blocks(const cfp_ctx* c) {
 }
 
 // the most CTAs any apply tile shape launches, with the correction kernel's
-// (dot-product partials per launch)
+// (dot-product partials per launch); the ring's persistent grid never has
+// more CTAs than the streaming kernel with 2 rows x 16 planes
 int apply_blocks(cfp_ctx* c) {
     int64_t m = 0;
     for (int ty : {2, 4})
@@ -515,9 +857,28 @@ int apply_blocks(cfp_ctx* c) {
 
 template <class T, int DOT, int TY, int KC>
 void apply_launch(cfp_ctx* c, const T* x, T* y, const T* d0, double* partial, cudaStream_t s, int* nb) {
-    const dim3 grid = rows_grid(c, TY, KC);
-    k_apply<T, DOT, TY, KC><<<grid, kAX, 0, s>>>(grid_view<T>(c), c->type, x, y, d0, partial);
-    const int nmain = (int)(grid.x * grid.y * grid.z);
+    int nmain = 0;
+    bool ring = false;
+    if constexpr (sizeof(T) == 4)
+        ring = apply_kind(c, 1) == CFP_APPLY_RING && c->ring_grid > 0 && aligned16(x) && (!DOT || aligned16(d0));
+    if (ring) {
+        if constexpr (sizeof(T) == 4) {
+            constexpr int RKC = KC < 32 ? 32 : KC;  // the ring marches 32 or 64 planes
+            int ntx, nty, ntz;
+            ring_tiles(c, RKC, &ntx, &nty, &ntz);
+            nmain = std::min(ntx * nty * ntz, c->ring_grid);
+            if (c->n[0] <= kRingSpanNx)
+                k_apply_ring<DOT, RKC, true><<<nmain, kRingThreads, kRingSmem, s>>>(
+                    grid_view<float>(c), c->type, x, y, d0, partial, ntx, nty, ntz, c->dwait);
+            else
+                k_apply_ring<DOT, RKC, false><<<nmain, kRingThreads, kRingSmem, s>>>(
+                    grid_view<float>(c), c->type, x, y, d0, partial, ntx, nty, ntz, c->dwait);
+        }
+    } else {
+        const dim3 grid = rows_grid(c, TY, KC);
+        k_apply<T, DOT, TY, KC><<<grid, kAX, 0, s>>>(grid_view<T>(c), c->type, x, y, d0, partial);
+        nmain = (int)(grid.x * grid.y * grid.z);
+    }
     const int ncorr = corr_blocks(c);
     if (ncorr)
         k_apply_corr<T, DOT><<<ncorr, 256, 0, s>>>(side_view<T>(c), c->irr_lin, c->n_irr, x, y, d0,
@@ -539,6 +900,38 @@ void apply_depth(cfp_ctx* c, int kc, const T* x, T* y, const T* d0, int dotmode,
     if (kc == 16) apply_dot<T, TY, 16>(c, x, y, d0, dotmode, partial, s, nb);
     else if (kc == 64) apply_dot<T, TY, 64>(c, x, y, d0, dotmode, partial, s, nb);
     else apply_dot<T, TY, 32>(c, x, y, d0, dotmode, partial, s, nb);
+}
+
+namespace {
+template <int DOT, int KC, bool SPAN>
+bool ring_attr(int* per) {
+    if (cudaFuncSetAttribute(k_apply_ring<DOT, KC, SPAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmem) !=
+        cudaSuccess)
+        return false;
+    int p = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k_apply_ring<DOT, KC, SPAN>, kRingThreads, kRingSmem) !=
+        cudaSuccess)
+        return false;
+    *per = std::min(*per, p);
+    return true;
+}
+template <int DOT>
+bool ring_attr_kc(int* per) {
+    return ring_attr<DOT, 32, true>(per) && ring_attr<DOT, 64, true>(per) && ring_attr<DOT, 32, false>(per) &&
+           ring_attr<DOT, 64, false>(per);
+}
+}  // namespace
+
+// The ring's launch attributes and persistent grid (CTAs resident on every
+// SM at once), once per context before any capture.
+bool setup_apply_ring(cfp_ctx* c) {
+    if (c->ring_grid) return c->ring_grid > 0;
+    int per = 1 << 20, nsm = 0;
+    const bool ok = ring_attr_kc<0>(&per) && ring_attr_kc<1>(&per) && ring_attr_kc<2>(&per) &&
+                    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess;
+    cudaGetLastError();
+    c->ring_grid = ok && per >= 1 ? per * nsm : -1;
+    return c->ring_grid > 0;
 }
 
 template <class T>

@@ -124,6 +124,68 @@ def test_apply_parity(name, zero_off):
     assert np.all(y.cpu().numpy()[nonunk] == 0.0)
 
 
+# FP32 apply kernels and tile shapes (kernel, rows, planes per z chunk): the
+# streaming kernel in both row counts and the bulk-copy ring in every depth
+SHAPES_F32 = [(cfp.APPLY_STREAM, 2, 64), (cfp.APPLY_STREAM, 4, 16), (cfp.APPLY_RING, 2, 32),
+              (cfp.APPLY_RING, 2, 64)]
+
+
+# grids around the ring's span limit (rows of up to 514 nodes are copied as
+# whole-plane spans, wider ones row by row)
+WIDE = {
+    "span-514": lambda: W.Workload("span-514", W.uniform_grid(-1, 1, 514), W.tanh_grid(-1, 1, 15, 0.5),
+                                   W.uniform_grid(-1, 1, 12), [W.sphere((0.1, 0.02, -0.03), 0.4)], W._c2_u, W._c2_f),
+    "rows-530": lambda: W.Workload("rows-530", W.tanh_grid(-1, 1, 530, 0.6), W.tanh_grid(-1, 1, 14, 0.5),
+                                   W.uniform_grid(-1, 1, 11), [W.sphere((-0.05, 0.0, 0.04), 0.35)], W._c2_u, W._c2_f),
+}
+
+
+def _apply_f32_case(p):
+    x = p.rand_field(2, zero_off=False).astype(np.float32)
+    x64 = x.astype(np.float64)
+    yo = p.P.apply_B(x64)
+    scale = p.P.apply_B(x64, absval=True)
+    xd = torch.as_tensor(x, device="cuda")
+    outs = []
+    for kernel, rows, planes in SHAPES_F32:
+        p.ctx.tune_apply(cfp.PREC_MIXED, rows, planes, kernel=kernel)
+        y = torch.full((p.w.N,), float("nan"), dtype=torch.float32, device="cuda")
+        p.ctx.apply_f32(xd, y)
+        outs.append(y)
+    p.ctx.tune_apply(cfp.PREC_MIXED, 2, 64, kernel=cfp.APPLY_STREAM)
+    y = outs[0].double().cpu().numpy()
+    err = np.abs(y - yo)
+    reg = p.otype == O.REGULAR
+    irr = p.otype == O.IRREGULAR
+    assert np.all(err[reg] <= 64 * 2.0 ** -24 * scale[reg] + 1e-30), np.max(err[reg] / (scale[reg] + 1e-30))
+    assert np.all(err[irr] <= 2.0 ** 29 * 1e-12 * scale[irr] + 1e-30), np.max(err[irr] / (scale[irr] + 1e-30))
+    nonunk = np.ones(p.w.N, bool)
+    nonunk[p.unk] = False
+    assert np.all(y[nonunk] == 0.0)
+    for shape, o in zip(SHAPES_F32[1:], outs[1:]):
+        assert torch.equal(o, outs[0]), shape
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_f32_parity_and_tile_shapes(name):
+    """The FP32 apply of the mixed solve's inner iterations against the FP64
+    oracle on the same FP32 input.  Regular rows: the rounding of the 1D
+    metrics to FP32 and of the FP32 sum-factorised arithmetic are a few units
+    of 2^-24 relative to |B||x|, bounded here by 64 * 2^-24.  Irregular rows
+    carry the split form's larger intermediate terms (the FP64 test's 1e-12
+    bar), scaled here from 2^-53 to 2^-24.  Every kernel and tile shape gives
+    the same bits: each row is the same chain of fused multiply-adds."""
+    _apply_f32_case(pair(name))
+
+
+@pytest.mark.parametrize("name", list(WIDE))
+def test_apply_f32_ring_copy_patterns(name):
+    """The same on grids at and beyond the width the ring copies as
+    whole-plane spans (514 nodes per row): its row-by-row copies and ragged
+    second column tile."""
+    _apply_f32_case(Pair(WIDE[name]()))
+
+
 @pytest.mark.parametrize("name", ["c2-33", "ragged-torus", "random-3"])
 @pytest.mark.parametrize("sweeps", [0, 1, 8])
 def test_preconditioner_parity(name, sweeps):
