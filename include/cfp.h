@@ -85,7 +85,10 @@ typedef struct {
     int max_restarts;  /* restarts after a breakdown or a failed true-residual
                           check (default 3)                                  */
     double inner_tol;  /* CFP_PREC_MIXED: relative residual reduction of each
-                          FP32 inner solve (default 1e-5)                    */
+                          FP32 inner solve (default 1e-5); a step that can
+                          end the solve aims at 0.3 tol / (its starting
+                          relative residual) instead, where that lies
+                          between inner_tol / 8 and inner_tol                */
     int max_refine;    /* CFP_PREC_MIXED: cap on refinement steps (default 40) */
     int use_graph;     /* 1 (default): the iteration runs as one CUDA graph
                           with a device-side while loop; 0: plain launches   */

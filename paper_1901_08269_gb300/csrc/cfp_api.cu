@@ -133,6 +133,9 @@ cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny, cons
     if (c->dwait) chk(cudaMemsetAsync(c->dwait, 0, sizeof(int), c->stream), "cudaMemsetAsync");
     chk(cudaMalloc(&c->kst, sizeof(KState) * 2), "cudaMalloc");
     chk(cudaMallocHost(&c->hkst, sizeof(KState) * 2), "cudaMallocHost");
+    chk(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
+    chk(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "cudaEventCreateWithFlags");
+    chk(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "cudaEventCreateWithFlags");
     if (st == CFP_OK) {
         for (int d = 0; d < 3; ++d)
             chk(cudaMemcpyAsync(c->dX[d], src[d], sizeof(double) * n[d], cudaMemcpyHostToDevice, c->stream),
@@ -181,6 +184,9 @@ void cfp_ctx_destroy(cfp_ctx* c) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->hkst) cudaFreeHost(c->hkst);
+    if (c->aux) cudaStreamSynchronize(c->aux), cudaStreamDestroy(c->aux);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 

@@ -170,6 +170,10 @@ struct cfp_ctx {
     int64_t N = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
+    // a second stream and two events: the apply forks its irregular rows
+    // onto `aux` to run beside the regular rows, and joins back
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<double> X[3];
     std::vector<cfp_body> bodies;
     int fluid_inside = 0;

@@ -650,8 +650,14 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
             c->launches += 2;
             int flag = 0, used = 0;
             double rr = 0.0;
-            const double it2 = opts.inner_tol * opts.inner_tol;
-            CFP_TRY(run_bicgstab<float>(c, 1, b32, it2, opts.maxit - total, opts.sweeps, opts.use_graph != 0, true,
+            // The inner solve's target reduction: inner_tol, tightened (down to
+            // inner_tol / 8) to the reduction 0.3 tol / rel that would end the
+            // solve in this step (a 3x margin) where inner_tol alone would
+            // leave the residual just above tol and cost a whole further
+            // refinement step.  Never looser than inner_tol.
+            const double need = 0.3 * tol / rel;
+            const double it = need < opts.inner_tol && need >= opts.inner_tol / 8 ? need : opts.inner_tol;
+            CFP_TRY(run_bicgstab<float>(c, 1, b32, it * it, opts.maxit - total, opts.sweeps, opts.use_graph != 0, true,
                                         &flag, &used, &rr));
             total += used;
             ++refinements;

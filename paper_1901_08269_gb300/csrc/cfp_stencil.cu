@@ -105,8 +105,8 @@ __device__ __forceinline__ double mult(double a, double b) { return __dmul_rn(a,
 // registers for the z-pass
 //   out(k) = Lz (P(k-1), P(k), P(k+1)) + Rz (Q(k-1), Q(k), Q(k+1)).
 // No shared memory and no barriers.  Solid rows are zero; the rows of
-// irregular points get their side-list corrections from k_apply_corr, launched
-// right after.  (Gathering the corrections inside this kernel, at each plane or
+// irregular points are left to k_apply_irr, which runs beside this kernel on
+// a second stream.  (Gathering the corrections inside this kernel, at each plane or
 // from a per-warp list after the march, measured 1.57x slower at 513^3: the
 // dependent side-list loads stall the streaming march, and the CTAs near the
 // bodies become the tail.)
@@ -231,8 +231,9 @@ __global__ void __launch_bounds__(kAX, TY == 2 ? (sizeof(T) == 4 ? 8 : 2) : (siz
                 if (!jin[t]) continue;
                 T v = fmat(cz, Pp[t], fmat(az, Pm[t], P0[t])) + fmat(crz, Qp[t], fmat(brz, Q0[t], mult(arz, Qm[t])));
                 const unsigned l = (unsigned)k * sz + (unsigned)(j0 + t) * sy + (unsigned)i;
-                if (t_cur[t] == CFP_SOLID) v = 0;  // irregular rows: k_apply_corr adds their corrections
-                y[l] = v;
+                // solid rows are zero; irregular rows belong to k_apply_irr
+                if (t_cur[t] != CFP_REGULAR) v = 0;
+                if (t_cur[t] != CFP_IRREGULAR) y[l] = v;
                 if (DOT >= 1) dacc0.add(d_cur[t], v);
                 if (DOT == 2) dacc1.add(v, v);
             }
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(kAX, TY == 2 ? (sizeof(T) == 4 ? 8 : 2) : (siz
 // threads own columns i0 + lx and i0 + 256 + lx of both rows and march the
 // planes with the same sum-factorised arithmetic and fused multiply-add
 // chains as k_apply<float>, so both give the same bits.  Solid rows are zero;
-// irregular rows get their corrections from k_apply_corr.
+// irregular rows are left to k_apply_irr.
 // A wait that runs out (1 s) records a code in *wait_err (31: producer, stage
 // free; 32: producer, final drain; 33: consumer, stage filled).  A producer
 // whose wait ran out issues no further copy and waits (bounded) for the
@@ -529,11 +530,13 @@ __global__ void __launch_bounds__(kRingThreads, 2)
                             float2 v = add2(fma2(CZ, Pp[t], fma2(AZ, Pm[t], P0[t])),
                                             fma2(CRZ, Qp[t], fma2(BRZ, Q0[t], mul2(ARZ, Qm[t]))));
                             const unsigned char* tr = ts + tb[t] + (int)((kq + ta[SPAN ? 0 : t]) & 15u);
-                            if (tr[0] == CFP_SOLID) v.x = 0.f;  // irregular rows: k_apply_corr
-                            if (!in1 || tr[kRingCons] == CFP_SOLID) v.y = 0.f;
+                            // solid rows are zero; irregular rows belong to k_apply_irr
+                            const uint8_t t0 = tr[0], t1 = in1 ? tr[kRingCons] : (uint8_t)CFP_SOLID;
+                            if (t0 != CFP_REGULAR) v.x = 0.f;
+                            if (t1 != CFP_REGULAR) v.y = 0.f;
                             float* yr = y + (kq + (unsigned)(j0 + t) * sy + (unsigned)c);
-                            yr[0] = v.x;
-                            if (in1) yr[kRingCons] = v.y;
+                            if (t0 != CFP_IRREGULAR) yr[0] = v.x;
+                            if (in1 && t1 != CFP_IRREGULAR) yr[kRingCons] = v.y;
                             if (DOT >= 1) {
                                 const float* dr = ds + db[t] + (int)((kq + da[SPAN ? 0 : t]) & 3u);
                                 dacc0.add(f2(dr[0], in1 ? dr[kRingCons] : 0.f), v);
@@ -615,12 +618,64 @@ __global__ void k_lift_shell(Grid<double> G, const uint8_t* __restrict__ type, c
     }
 }
 
+// The rows of the irregular points, whole (Eq. Bdec): the regular 27-point
+// part with the arithmetic of the factorised kernels -- the same fused
+// multiply-add chains on the same 27 values, so that part has the same bits
+// as there -- plus the side-list corrections of the row's modified lines
+// (Eqs. A27_mod, cor, cor_case2).  One thread per irregular point.  The
+// regular rows' kernels leave these rows alone, so this kernel runs beside
+// them on a second stream; its dot terms go to its own partials.
+template <class T, int DOT>
+__global__ void __launch_bounds__(128)
+    k_apply_irr(Grid<T> G, Side<T> S, const int32_t* __restrict__ irr_lin, int64_t n_irr, const T* __restrict__ x,
+                T* __restrict__ y, const T* __restrict__ d0, double* __restrict__ partial) {
+    const int nx = G.nx, ny = G.ny;
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_irr;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = irr_lin[s];
+        const int k = (int)(l / sz), rem = (int)(l - k * sz), j = rem / nx, i = rem - j * nx;
+        const T ax = G.ax[0].a[i], cx = G.ax[0].c[i], arx = G.ax[0].ar[i], brx = G.ax[0].br[i], crx = G.ax[0].cr[i];
+        const T ay = G.ax[1].a[j], cy = G.ax[1].c[j], ary = G.ax[1].ar[j], bry = G.ax[1].br[j], cry = G.ax[1].cr[j];
+        const T az = G.ax[2].a[k], cz = G.ax[2].c[k], arz = G.ax[2].ar[k], brz = G.ax[2].br[k], crz = G.ax[2].cr[k];
+        T P[3], Q[3];
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz) {
+            T XR[3], XL[3];
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy) {
+                const T* q = x + l + (dz - 1) * sz + (dy - 1) * sy;
+                XR[dy] = fmat(crx, q[1], fmat(brx, q[0], mult(arx, q[-1])));
+                XL[dy] = fmat(cx, q[1], fmat(ax, q[-1], q[0]));
+            }
+            P[dz] = fmat(cry, XL[2], fmat(bry, XL[1], fmat(ary, XL[0], fmat(cy, XR[2], fmat(ay, XR[0], XR[1])))));
+            Q[dz] = fmat(cy, XL[2], fmat(ay, XL[0], XL[1]));
+        }
+        T v = fmat(cz, P[2], fmat(az, P[0], P[1])) + fmat(crz, Q[2], fmat(brz, Q[1], mult(arz, Q[0])));
+        T cor = T(0);
+        for (int e = S.corr_ptr[s]; e < S.corr_ptr[s + 1]; ++e) cor = fmat(S.corr_val[e], x[l + S.corr_off[e]], cor);
+        v = v + cor;
+        y[l] = v;
+        if (DOT >= 1) acc0 += (double)d0[l] * (double)v;
+        if (DOT == 2) acc1 += (double)v * (double)v;
+    }
+    if (DOT) {
+        block_reduce2(acc0, acc1);
+        if (threadIdx.x == 0) {
+            partial[2 * blockIdx.x] = acc0;
+            partial[2 * blockIdx.x + 1] = acc1;
+        }
+    }
+}
+
 // Side-list corrections of the irregular rows (the modified stencils of
-// Secs. 2.2-2.3, the C part of Eq. Bdec), one warp per irregular point: the
-// lanes gather the merged entries in parallel, lane 0 adds the sum to y and
-// updates the dot partials: (d0, y) gains d0 c, (y, y) gains 2 v c + c^2
-// where v is the row's regular part.  Partials are written after those of
-// k_apply, one pair per CTA.
+// Secs. 2.2-2.3, the C part of Eq. Bdec) added to a y that holds their
+// regular part, one warp per irregular point: the lanes gather the merged
+// entries in parallel, lane 0 adds the sum to y and updates the dot partials:
+// (d0, y) gains d0 c, (y, y) gains 2 v c + c^2 where v is the row's regular
+// part.  Used for the boundary lift (after k_lift_shell), one pair of
+// partials per CTA.
 template <class T, int DOT>
 __global__ void __launch_bounds__(256)
     k_apply_corr(Side<T> S, const int32_t* __restrict__ irr_lin, int64_t n_irr, const T* __restrict__ x,
@@ -842,6 +897,13 @@ int corr_blocks(const cfp_ctx* c) {
     return (int)std::min<int64_t>((c->n_irr + 7) / 8, 152 * 16);
 }
 
+// CTAs of k_apply_irr (128 threads, one irregular point each per pass; at
+// most 152 x 8, never more than corr_blocks)
+int irr_blocks(const cfp_ctx* c) {
+    if (c->n_irr <= 0) return 0;
+    return (int)std::min<int64_t>((c->n_irr + 127) / 128, 152 * 8);
+}
+
 // the most CTAs any apply tile shape launches, with the correction kernel's
 // (dot-product partials per launch); the ring's persistent grid never has
 // more CTAs than the streaming kernel with 2 rows x 16 planes
@@ -855,18 +917,34 @@ int apply_blocks(cfp_ctx* c) {
     return (int)m + corr_blocks(c);
 }
 
+// B x: the regular rows' kernel on s and, forked onto the context's second
+// stream and joined back before anything later on s, the irregular rows'
+// kernel; dot partials: the main kernel's CTAs, then k_apply_irr's.
 template <class T, int DOT, int TY, int KC>
 void apply_launch(cfp_ctx* c, const T* x, T* y, const T* d0, double* partial, cudaStream_t s, int* nb) {
     int nmain = 0;
     bool ring = false;
+    constexpr int RKC = KC < 32 ? 32 : KC;  // the ring marches 32 or 64 planes
+    int ntx = 0, nty = 0, ntz = 0;
+    dim3 grid;
     if constexpr (sizeof(T) == 4)
         ring = apply_kind(c, 1) == CFP_APPLY_RING && c->ring_grid > 0 && aligned16(x) && (!DOT || aligned16(d0));
     if (ring) {
+        ring_tiles(c, RKC, &ntx, &nty, &ntz);
+        nmain = std::min(ntx * nty * ntz, c->ring_grid);
+    } else {
+        grid = rows_grid(c, TY, KC);
+        nmain = (int)(grid.x * grid.y * grid.z);
+    }
+    const int nirr = irr_blocks(c);
+    if (nirr) {
+        cudaEventRecord(c->ev_fork, s);
+        cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+        k_apply_irr<T, DOT><<<nirr, 128, 0, c->aux>>>(grid_view<T>(c), side_view<T>(c), c->irr_lin, c->n_irr, x, y,
+                                                      d0, partial ? partial + 2 * (int64_t)nmain : nullptr);
+    }
+    if (ring) {
         if constexpr (sizeof(T) == 4) {
-            constexpr int RKC = KC < 32 ? 32 : KC;  // the ring marches 32 or 64 planes
-            int ntx, nty, ntz;
-            ring_tiles(c, RKC, &ntx, &nty, &ntz);
-            nmain = std::min(ntx * nty * ntz, c->ring_grid);
             if (c->n[0] <= kRingSpanNx)
                 k_apply_ring<DOT, RKC, true><<<nmain, kRingThreads, kRingSmem, s>>>(
                     grid_view<float>(c), c->type, x, y, d0, partial, ntx, nty, ntz, c->dwait);
@@ -875,16 +953,14 @@ void apply_launch(cfp_ctx* c, const T* x, T* y, const T* d0, double* partial, cu
                     grid_view<float>(c), c->type, x, y, d0, partial, ntx, nty, ntz, c->dwait);
         }
     } else {
-        const dim3 grid = rows_grid(c, TY, KC);
         k_apply<T, DOT, TY, KC><<<grid, kAX, 0, s>>>(grid_view<T>(c), c->type, x, y, d0, partial);
-        nmain = (int)(grid.x * grid.y * grid.z);
     }
-    const int ncorr = corr_blocks(c);
-    if (ncorr)
-        k_apply_corr<T, DOT><<<ncorr, 256, 0, s>>>(side_view<T>(c), c->irr_lin, c->n_irr, x, y, d0,
-                                                   partial ? partial + 2 * (int64_t)nmain : nullptr);
-    c->launches += ncorr ? 1 : 0;
-    if (nb) *nb = nmain + ncorr;
+    if (nirr) {
+        cudaEventRecord(c->ev_join, c->aux);
+        cudaStreamWaitEvent(s, c->ev_join, 0);
+    }
+    c->launches += nirr ? 1 : 0;
+    if (nb) *nb = nmain + nirr;
 }
 
 template <class T, int TY, int KC>
