@@ -388,9 +388,13 @@ def learned_arm(args):
 # ----------------------------------------------------------- batched arm
 def batch_arm(args):
     """64 random problems (n in {33,49,65,97,129}, 1-3 spheres/ellipsoids,
-    tanh factors in [1,2], 8-mode source, g = 0) solved together with
-    cfp_solve_batch, mixed precision, multigrid; one step = classification
-    of every problem + the batched solve."""
+    tanh factors in [1,2], 8-mode source, g = 0) solved together as one graph
+    launch (cfp_batch: every problem's refinement and BiCGSTAB loops driven
+    on the device), mixed precision, multigrid, the solver settings and the
+    apply's tile autotuned per grid size; one step = classification of every
+    problem + the batch (captured again, as the classification replaced the
+    side data) + its launch.  The host-thread batch (cfp_solve_batch) is
+    timed beside it."""
     import torch
 
     from paper_1901_08269_gb300 import cfp
@@ -410,56 +414,91 @@ def batch_arm(args):
     prec = cfp.PREC_MIXED if args.precision == "mixed" else cfp.PREC_FP64
     opts = cfp.default_opts(precision=prec, precond=cfp.PRECOND_MG, mg_smooth=args.mg_smooth, mg_post=args.mg_post,
                             inner_tol=args.inner_tol)
-    # autotune once per grid size (first problem of each size), then share
-    tuned = {}
+    # autotune once per grid size (first problem of each size): the solver
+    # settings and the FP32 apply's kernel and tile; the others of that size
+    # take both
+    tuned, shapes = {}, {}
     for w, ctx, f, g, gi, u in probs:
         n = w.x.size
         if n not in tuned:
             tuned[n] = ctx.autotune(f, g, gi, u, tol=args.batch_tol, opts=cfp.default_opts(
                 precision=prec, precond=cfp.PRECOND_MG, inner_tol=args.inner_tol))[0]
-    by_n = {n: (o.mg_smooth, o.inner_tol) for n, o in tuned.items()}
-    # the batch call takes one opts: use the setting tuned for the largest size
-    nmax = max(tuned)
-    opts = tuned[nmax]
+            if prec == cfp.PREC_MIXED:
+                ctx.tune_apply(cfp.PREC_MIXED)
+                shapes[n] = ctx.apply_shape(cfp.PREC_MIXED)
+        elif n in shapes:
+            k, r, q = shapes[n]
+            ctx.tune_apply(cfp.PREC_MIXED, r, q, kernel=k)
+    by_n = {n: (o.mg_smooth, o.inner_tol) + tuple(shapes.get(n, ())) for n, o in tuned.items()}
+    popts = [tuned[p[0].x.size] for p in probs]
+    # the host-thread batch takes one opts: the setting tuned for the largest size
+    opts = tuned[max(tuned)]
 
     from concurrent.futures import ThreadPoolExecutor
     pool = ThreadPoolExecutor(16)  # contexts classify independently (the C calls release the GIL)
+    graph = prec == cfp.PREC_MIXED
+    batch = cfp.Batch([p[1] for p in probs], [p[2] for p in probs], [p[3] for p in probs], [p[4] for p in probs],
+                      [p[5] for p in probs], tol=args.batch_tol, opts=popts) if graph else None
 
-    def step():
+    def classify():
         list(pool.map(lambda p: p[1].classify_points(), probs))
         for w, ctx, f, g, gi, u in probs:
             u.zero_()
         torch.cuda.synchronize()
+
+    def step_graph():
+        classify()
+        return batch.run()
+
+    def step_threads():
+        classify()
         return cfp.solve_batch([p[1] for p in probs], [p[2] for p in probs], [p[3] for p in probs],
                                [p[4] for p in probs], [p[5] for p in probs], tol=args.batch_tol, opts=opts)
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        infos = step()
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / args.steps
+    def timed(step, k):
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            out = step()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / k, out
+
+    dt, infos = timed(step_graph if graph else step_threads, args.steps)
+    dt_threads = timed(step_threads, max(1, min(args.steps, 3)))[0] if graph else dt
+    reuse = None
+    if graph:
+        # the same geometries again: no classification, the graph reused
+        def step_reuse():
+            for p in probs:
+                p[5].zero_()
+            torch.cuda.synchronize()
+            return batch.run()
+        reuse = timed(step_reuse, max(1, min(args.steps, 3)))[0]
     # the same problems one after another (no overlap), for comparison
     t1 = time.perf_counter()
     for w, ctx, f, g, gi, u in probs:
         ctx.classify_points()
         u.zero_()
-        ctx.solve(f, g, gi, u, tol=args.batch_tol, opts=opts)
+        ctx.solve(f, g, gi, u, tol=args.batch_tol, opts=tuned[w.x.size])
     torch.cuda.synchronize()
     seq = time.perf_counter() - t1
     nodes = sum(p[0].N for p in probs)
+    launches = sum(i.launches for i in infos) if graph else None
     line = {"metric": "s per batch of %d random immersed-body problems (config 4)" % args.batch, "value": dt,
             "unit": "s/batch", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
             "ms_per_step": 1000 * dt, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == cfp.PREC_MIXED else "f64", "data": "synthetic",
             "config": {"workload": "config4-batch%d-seed%d" % (args.batch, args.seed), "total_nodes": nodes,
                        "sizes": sorted(set(p[0].x.size for p in probs)), "tuned": {str(k): v for k, v in by_n.items()},
-                       "tol": args.batch_tol},
-            "sequential_s": seq, "iterations": [i.iterations for i in infos[:8]], "gpu_launches": None}
+                       "tol": args.batch_tol, "impl": "one graph launch per batch" if graph else "host threads"},
+            "host_threads_s": dt_threads, "graph_reused_s": reuse, "sequential_s": seq, "iterations": [i.iterations for i in infos[:8]],
+            "gpu_launches": launches}
     print(json.dumps(line), flush=True)
     pool.shutdown()
+    if batch is not None:
+        batch.close()
     for p in probs:
         p[1].close()
     return 0

@@ -287,6 +287,45 @@ cfp_status cfp_solve_batch(cfp_ctx* const* ctxs, int nprob,
                            cfp_info* infos);
 
 /*
+ * A batch of independent mixed-precision solves as ONE graph launch.  Each
+ * problem's whole solve -- right-hand side, the refinement loop of
+ * CFP_PREC_MIXED with its scaling, inner-tolerance, stall and stopping
+ * decisions taken by one-block kernels on device-resident scalars, the
+ * preconditioned BiCGSTAB loop inside each refinement step, the solution --
+ * is captured with its two loops as nested while nodes of a CUDA graph, and
+ * the problems are the parallel branches of one graph.  cfp_batch_run
+ * launches it once: no host round trip between refinement steps or problems,
+ * and the GPU interleaves the problems' kernels.  Each problem's result is
+ * bitwise the one cfp_solve gives with the same settings (the same kernels
+ * in the same order on the same values).
+ *   cfp_batch_create: ctxs, f_dev, g_nodes_dev, g_ibi_dev (NULL allowed:
+ *     every problem without IBI points), u_dev: nprob entries as cfp_solve
+ *     (u_dev: initial guess in, solution out, of the next run); opts: NULL
+ *     (defaults) or nprob settings, each with precision = CFP_PREC_MIXED;
+ *     tol as cfp_solve.  Classifies the contexts that are not, prepares
+ *     their work space and preconditioners, captures and instantiates the
+ *     graph.  The batch holds the pointers: the buffers must live until
+ *     cfp_batch_destroy; their contents may change between runs.
+ *   cfp_batch_run: launches the graph and waits for it; infos (NULL
+ *     allowed): nprob results, ms_solve = the whole batch's wall time.  A
+ *     context reclassified (or whose multigrid / ILU data or apply kernel
+ *     was replaced) since the capture makes the run capture the graph
+ *     again first.  Returns the first failing problem's status (CFP_ENOCONV,
+ *     CFP_ENAN, CFP_EBREAKDOWN) with its index in the message; infos holds
+ *     every problem's.
+ * A context must not be used by another call while its batch runs.
+ * Errors: CFP_EINVAL (NULL or repeated entries, nprob < 1, a problem with
+ * IBI points and no g_ibi_dev, another precision), CFP_ECUDA, CFP_ENOMEM,
+ * CFP_EGEOM from the classification.
+ */
+typedef struct cfp_batch cfp_batch;
+cfp_status cfp_batch_create(cfp_ctx* const* ctxs, int nprob, const double* const* f_dev,
+                            const double* const* g_nodes_dev, const double* const* g_ibi_dev,
+                            double* const* u_dev, double tol, const cfp_opts* opts, cfp_batch** out);
+cfp_status cfp_batch_run(cfp_batch* batch, cfp_info* infos);
+void cfp_batch_destroy(cfp_batch* batch);
+
+/*
  * Autotuner of the solver settings for one problem: times the solve (best
  * of two runs each) with the multigrid preconditioner and mg_smooth in
  * {1, 2, 3} and, for CFP_PREC_MIXED, inner_tol in {1e-2, 1e-3, 1e-4}, and
@@ -393,6 +432,14 @@ enum { CFP_APPLY_STREAM = 1,  /* each thread streams its column of `rows`
  * where the ring cannot be set up), CFP_ECUDA.
  */
 cfp_status cfp_tune_apply(cfp_ctx* ctx, int precision, int kernel, int rows, int planes, double* ms);
+
+/*
+ * The apply's kernel and tile shape the context uses for `precision` (set
+ * by cfp_tune_apply or the default), as cfp_tune_apply takes them: for
+ * instance to give contexts of one grid size the shape tuned on one of them.
+ * Outputs may be NULL.  Errors: CFP_EINVAL.
+ */
+cfp_status cfp_apply_shape(const cfp_ctx* ctx, int precision, int* kernel, int* rows, int* planes);
 
 /*
  * FP64 vector helpers over all N nodes of two fields, for outer iterations

@@ -52,7 +52,7 @@ _D = C.POINTER(C.c_double)
 EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_destroy", "cfp_classify_points",
            "cfp_ibi_points", "cfp_assemble_rhs", "cfp_apply", "cfp_apply_f32", "cfp_precondition", "cfp_solve", "cfp_solve_host",
            "cfp_time_kernel", "cfp_launch_count", "cfp_assemble_rhs_noalloc", "cfp_precondition_ex",
-           "cfp_solve_batch", "cfp_autotune", "cfp_diag_bounded_wait", "cfp_vec_dot", "cfp_vec_axpby",
+           "cfp_solve_batch", "cfp_apply_shape", "cfp_batch_create", "cfp_batch_run", "cfp_batch_destroy", "cfp_autotune", "cfp_diag_bounded_wait", "cfp_vec_dot", "cfp_vec_axpby",
            "cfp_nn_conv3d", "cfp_nn_conv3d_wgrad", "cfp_nn_transfer", "cfp_unet_create", "cfp_unet_destroy",
            "cfp_unet_param_count", "cfp_unet_get_params", "cfp_unet_set_params", "cfp_unet_forward_raw",
            "cfp_unet_train_step", "cfp_unet_apply", "cfp_unet_check", "cfp_solve_fgmres", "cfp_tune_apply"]
@@ -92,11 +92,17 @@ def lib(build_if_missing=True):
         L.cfp_precondition_ex.argtypes = [_P, C.POINTER(Opts), _P, _P]
         L.cfp_solve_batch.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                       C.POINTER(_P), C.c_double, C.POINTER(Opts), C.c_int, C.POINTER(Info)]
+        L.cfp_batch_create.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
+                                       C.POINTER(_P), C.c_double, C.POINTER(Opts), C.POINTER(_P)]
+        L.cfp_batch_run.argtypes = [_P, C.POINTER(Info)]
+        L.cfp_batch_destroy.argtypes = [_P]
+        L.cfp_batch_destroy.restype = None
         L.cfp_autotune.argtypes = [_P, _P, _P, _P, _P, C.c_double, C.POINTER(Opts), _D]
         L.cfp_launch_count.argtypes = [_P]
         L.cfp_launch_count.restype = C.c_int64
         L.cfp_diag_bounded_wait.argtypes = [_P]
         L.cfp_tune_apply.argtypes = [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]
+        L.cfp_apply_shape.argtypes = [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.cfp_vec_dot.argtypes = [_P, _P, _P, _D]
         L.cfp_vec_axpby.argtypes = [_P, C.c_double, _P, C.c_double, _P]
         _I = C.c_int
@@ -176,6 +182,44 @@ def solve_batch(ctxs, fs, gs, gis, us, tol=1e-12, opts=None, nthreads=0, check=T
     if check:
         _check(st, "cfp_solve_batch")
     return [infos[m] for m in range(n)]
+
+
+class Batch:
+    """cfp_batch: the problems' mixed-precision solves as one graph launch.
+    opts: None, one Opts for all problems or a list of one per problem.  The
+    tensors must stay alive while the batch does."""
+
+    def __init__(self, ctxs, fs, gs, gis, us, tol=1e-12, opts=None, **kw):
+        n = len(ctxs)
+        if opts is None:
+            opts = default_opts(**kw)
+        if isinstance(opts, Opts):
+            opts = [opts] * n
+        for c, f, g, u in zip(ctxs, fs, gs, us):
+            c._field(f, "f"), c._field(g, "g_nodes"), c._field(u, "u")
+        arr = lambda ts: (_P * n)(*[_P(t.data_ptr()) if t is not None and t.numel() else None for t in ts])
+        self._keep = (list(ctxs), list(fs), list(gs), list(gis), list(us))
+        self.n = n
+        olist = (Opts * n)(*opts)
+        h = _P()
+        _check(lib().cfp_batch_create((_P * n)(*[c._h for c in ctxs]), n, arr(fs), arr(gs), arr(gis), arr(us),
+                                      float(tol), olist, C.byref(h)), "cfp_batch_create")
+        self._h = h
+
+    def run(self, check=True):
+        infos = (Info * self.n)()
+        st = lib().cfp_batch_run(self._h, infos)
+        if check:
+            _check(st, "cfp_batch_run")
+        return [infos[m] for m in range(self.n)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cfp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 class Context:
@@ -270,6 +314,12 @@ class Context:
         _check(lib().cfp_tune_apply(self._h, int(precision), int(kernel), int(rows), int(planes), C.byref(ms)),
                "cfp_tune_apply")
         return ms.value
+
+    def apply_shape(self, precision=PREC_MIXED):
+        """cfp_apply_shape: (kernel, rows, planes) the apply runs with."""
+        k, r, q = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().cfp_apply_shape(self._h, int(precision), C.byref(k), C.byref(r), C.byref(q)), "cfp_apply_shape")
+        return k.value, r.value, q.value
 
     def vec_dot(self, a, b):
         out = C.c_double()

@@ -133,9 +133,14 @@ cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny, cons
     if (c->dwait) chk(cudaMemsetAsync(c->dwait, 0, sizeof(int), c->stream), "cudaMemsetAsync");
     chk(cudaMalloc(&c->kst, sizeof(KState) * 2), "cudaMalloc");
     chk(cudaMallocHost(&c->hkst, sizeof(KState) * 2), "cudaMallocHost");
-    chk(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
-    chk(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "cudaEventCreateWithFlags");
-    chk(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "cudaEventCreateWithFlags");
+    chk(cudaMalloc(&c->rst, sizeof(RState)), "cudaMalloc");
+    chk(cudaMallocHost(&c->hrst, sizeof(RState)), "cudaMallocHost");
+    for (int q = 0; q < 3; ++q) {
+        chk(cudaStreamCreateWithFlags(&c->auxs[q], cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
+        chk(cudaEventCreateWithFlags(&c->evfs[q], cudaEventDisableTiming), "cudaEventCreateWithFlags");
+        chk(cudaEventCreateWithFlags(&c->evjs[q], cudaEventDisableTiming), "cudaEventCreateWithFlags");
+    }
+    use_aux(c, 0);
     if (st == CFP_OK) {
         for (int d = 0; d < 3; ++d)
             chk(cudaMemcpyAsync(c->dX[d], src[d], sizeof(double) * n[d], cudaMemcpyHostToDevice, c->stream),
@@ -180,13 +185,16 @@ void cfp_ctx_destroy(cfp_ctx* c) {
     void* ptrs[] = {c->dcoef64, c->dcoef32, c->dX[0], c->dX[1], c->dX[2], c->dbodies, c->dbound2, c->type, c->slot, c->irr_lin,
                     c->ibi_off, c->ibi_xyz, c->corr_ptr, c->corr_off, c->corr_val, c->corr_val32, c->bib_ptr,
                     c->bib_idx, c->bib_val, c->krow, c->krow32, c->side_scratch, c->scan_bsum, c->dtotal, c->derr, c->dwait, c->nn_wflip, c->v64, c->v32,
-                    c->partial, c->kst, c->hs_f, c->hs_g, c->hs_u, c->hs_gi};
+                    c->partial, c->kst, c->rst, c->hs_f, c->hs_g, c->hs_u, c->hs_gi};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->hkst) cudaFreeHost(c->hkst);
-    if (c->aux) cudaStreamSynchronize(c->aux), cudaStreamDestroy(c->aux);
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->hrst) cudaFreeHost(c->hrst);
+    for (int q = 0; q < 3; ++q) {
+        if (c->auxs[q]) cudaStreamSynchronize(c->auxs[q]), cudaStreamDestroy(c->auxs[q]);
+        if (c->evfs[q]) cudaEventDestroy(c->evfs[q]);
+        if (c->evjs[q]) cudaEventDestroy(c->evjs[q]);
+    }
     delete c;
 }
 
@@ -353,6 +361,18 @@ int64_t cfp_launch_count(const cfp_ctx* c) { return c ? c->launches : 0; }
 cfp_status cfp_time_kernel(cfp_ctx* c, int kernel, int precision, int reps, double* ms, double* bytes) {
     CFP_TRY(need_classified(c));
     return time_kernel(c, kernel, precision, reps, ms, bytes);
+}
+
+cfp_status cfp_apply_shape(const cfp_ctx* c, int precision, int* kernel, int* rows, int* planes) {
+    if (!c) return fail(CFP_EINVAL, "null context");
+    if (precision != CFP_PREC_FP64 && precision != CFP_PREC_MIXED) return fail(CFP_EINVAL, "bad precision");
+    const int q = precision == CFP_PREC_MIXED ? 1 : 0;
+    int k = 0, r = 0, p = 0;
+    apply_shape(c, q, &k, &r, &p);
+    if (kernel) *kernel = k;
+    if (rows) *rows = r;
+    if (planes) *planes = p;
+    return CFP_OK;
 }
 
 cfp_status cfp_tune_apply(cfp_ctx* c, int precision, int kernel, int rows, int planes, double* ms) {

@@ -795,6 +795,7 @@ cfp_status classify(cfp_ctx* c) {
     const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
     const int64_t N = c->N;
     c->classified = false;
+    c->generation += 1;
     free_ptr(c->irr_lin);
     free_ptr(c->ibi_off);
     free_ptr(c->ibi_xyz);

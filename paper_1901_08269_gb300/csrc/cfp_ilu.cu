@@ -178,6 +178,7 @@ float* ilu_pivots_of<float>(cfp_ctx* c) { return c->ilu32; }
 }  // namespace
 
 void free_ilu(cfp_ctx* c) {
+    if (c->ilu64 || c->ilu32) c->generation += 1;
     if (c->ilu64) cudaFree(c->ilu64);
     if (c->ilu32) cudaFree(c->ilu32);
     c->ilu64 = nullptr;

@@ -104,6 +104,23 @@ struct KState {
 
 enum { FLAG_RUN = 0, FLAG_CONV = 1, FLAG_BREAK = 2, FLAG_NAN = 3, FLAG_MAXIT = 4 };
 
+// Device-resident scalars of one mixed-precision solve driven on the device
+// (the refinement loop of a captured solve graph): the same quantities and
+// decisions as the host-driven refinement loop.
+struct RState {
+    double b2;          // ||rhs||^2
+    double r2;          // ||rhs - B x||^2 of the current iterate
+    double rel;         // sqrt(r2 / b2)
+    double prev;        // smallest rel so far
+    double scale;       // 1 / sqrt(r2): the FP32 right-hand side's scaling
+    double tol, inner_tol;
+    int refinements, total, maxit, max_refine, max_restarts, stall;
+    int status;         // cfp_status; RSTATE_RUN while the loop goes on
+    int outer;          // refinement bodies executed
+    long long inner_execs;  // BiCGSTAB bodies executed over all steps
+};
+constexpr int RSTATE_RUN = -1;
+
 // First device error of the set-up kernels.
 struct DevError {
     int code;    // cfp_status, 0 = none
@@ -171,7 +188,11 @@ struct cfp_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     // a second stream and two events: the apply forks its irregular rows
-    // onto `aux` to run beside the regular rows, and joins back
+    // onto `aux` to run beside the regular rows, and joins back.  Three sets,
+    // one per capture level of a device-driven solve (the graph, the
+    // refinement body, the BiCGSTAB body); aux / ev_* are the set in use.
+    cudaStream_t auxs[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t evfs[3] = {nullptr, nullptr, nullptr}, evjs[3] = {nullptr, nullptr, nullptr};
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<double> X[3];
@@ -222,6 +243,8 @@ struct cfp_ctx {
     int64_t partial_cap = 0;
     cfp::KState* kst = nullptr;   // [0]: FP64 run, [1]: FP32 run
     cfp::KState* hkst = nullptr;  // pinned host mirror
+    cfp::RState* rst = nullptr;   // device-driven refinement loop
+    cfp::RState* hrst = nullptr;  // pinned host mirror
 
     // host-buffer solve
     double* hs_f = nullptr;
@@ -232,6 +255,10 @@ struct cfp_ctx {
 
     // kernels enqueued since the context was created
     int64_t launches = 0;
+    // moves whenever a buffer or kernel choice that captured graphs hold is
+    // replaced (classification, multigrid / ILU data freed, the partials
+    // reallocated, a new apply shape): graphs of other objects recapture
+    int64_t generation = 0;
 
     // the apply's kernel and tile shape per precision (0 FP64, 1 FP32):
     // CFP_APPLY_STREAM (rows per thread 2 or 4) or CFP_APPLY_RING (FP32, 8
@@ -256,6 +283,7 @@ struct cfp_ctx {
     // graphs: [precision][sweeps-config]
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int gsweeps[2] = {-1, -1};
+    int64_t ggen[2] = {-1, -1};
     int gprecond[2] = {-1, -1};
     int64_t body_launches = 0;
     int gmgs[2] = {-1, -1};
@@ -267,6 +295,12 @@ constexpr int kNV64 = 12;  // x r rh p ph v s sh t rhs tmp tmp2
 // distance between two work fields in v64 / v32: N rounded up to 64 entries,
 // so that every field starts 256-byte aligned (bulk copies want 16)
 inline int64_t vstride(const cfp_ctx* c) { return (c->N + 63) / 64 * 64; }
+// selects the stream and events the apply forks its irregular rows onto
+inline void use_aux(cfp_ctx* c, int q) {
+    c->aux = c->auxs[q];
+    c->ev_fork = c->evfs[q];
+    c->ev_join = c->evjs[q];
+}
 constexpr int kNV32 = 9;   // x r rh p ph v s sh t
 enum { V_X = 0, V_R, V_RH, V_P, V_PH, V_V, V_S, V_SH, V_T, V_RHS, V_TMP, V_TMP2 };
 
@@ -326,6 +360,8 @@ cfp_status time_kernel(cfp_ctx* c, int kernel, int prec, int reps, double* ms, d
 cfp_status tune_apply(cfp_ctx* c, int prec, int kind, int rows, int planes, int reps, double* best_ms);
 // sets up the FP32 apply ring (shared-memory limit, persistent grid); false if unusable
 bool setup_apply_ring(cfp_ctx* c);
+// the kernel and tile shape the apply of precision q (0 FP64, 1 FP32) runs with
+void apply_shape(const cfp_ctx* c, int q, int* kernel, int* rows, int* planes);
 // phi = P(rho) in FP32 (the mixed solve's inner preconditioner) for FP64
 // fields: rho rounded to FP32, phi widened back; phi zeroed first
 cfp_status precondition32(cfp_ctx* c, int sweeps, const double* rho, double* phi);

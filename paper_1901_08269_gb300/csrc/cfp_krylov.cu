@@ -275,7 +275,7 @@ int64_t body_launches(cfp_ctx* c) { return c->body_launches; }
 template <class T>
 cfp_status build_graph(cfp_ctx* c, int prec, int sweeps) {
     if (c->gexec[prec] && c->gsweeps[prec] == sweeps && c->gprecond[prec] == c->precond_kind &&
-        c->gmgs[prec] == mg_key(c))
+        c->gmgs[prec] == mg_key(c) && c->ggen[prec] == c->generation)
         return CFP_OK;
     if (c->gexec[prec]) {
         cudaGraphExecDestroy(c->gexec[prec]);
@@ -314,6 +314,7 @@ cfp_status build_graph(cfp_ctx* c, int prec, int sweeps) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     c->gexec[prec] = exec;
+    c->ggen[prec] = c->generation;
     c->gsweeps[prec] = sweeps;
     c->gprecond[prec] = c->precond_kind;
     c->gmgs[prec] = mg_key(c);
@@ -402,6 +403,7 @@ __global__ void k_axpby(double alpha, const double* x, double beta, double* y, i
 cfp_status ensure_partial(cfp_ctx* c) {
     const int64_t need = 2 * (int64_t)std::max(apply_blocks(c), kUpdBlocks);
     if (c->partial_cap < need) {
+        c->generation += 1;
         if (c->partial) cudaFree(c->partial);
         c->partial = nullptr;
         CFP_CUDA(cudaMalloc(&c->partial, sizeof(double) * need));
@@ -519,6 +521,7 @@ cfp_status tune_apply(cfp_ctx* c, int prec, int kind, int rows, int planes, int 
     c->apply_kind[q] = bs.kind;
     c->apply_ty[q] = bs.ty;
     c->apply_kc[q] = bs.kc;
+    c->generation += 1;
     if (best_ms) *best_ms = best;
     return CFP_OK;
 }
@@ -700,3 +703,292 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
                                                        : "no convergence within the iteration cap");
     return CFP_OK;
 }
+
+// --------------------------------------------- the solve driven on the device
+// The mixed-precision solve of solve_impl with its refinement loop moved onto
+// the device: every decision the host loop takes (the FP32 right-hand side's
+// scaling, the inner tolerance, the stopping and stall tests) is taken by a
+// one-block kernel on the RState of the context, the refinement loop is a
+// while node of a CUDA graph and the BiCGSTAB loop a while node inside its
+// body.  The same kernels run in the same order on the same values, so the
+// result is bitwise the one solve_impl gives; a whole solve is one graph
+// launch.
+namespace cfp {
+namespace {
+
+__device__ int status_of_flag(int flag) {
+    return flag == FLAG_NAN ? CFP_ENAN : flag == FLAG_BREAK ? CFP_EBREAKDOWN : CFP_ENOCONV;
+}
+
+// before the loop: ||rhs||^2 and the first residual's ||r||^2 from their
+// slots; the outcomes the host loop settles before its first step
+__global__ void k_ref_setup(RState* R, const double* b2s, const double* r2s, double tol, double inner_tol, int maxit,
+                            int max_refine, int max_restarts, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    const double b2 = *b2s;
+    R->b2 = b2;
+    R->tol = tol;
+    R->inner_tol = inner_tol;
+    R->maxit = maxit;
+    R->max_refine = max_refine;
+    R->max_restarts = max_restarts;
+    R->refinements = R->total = R->stall = R->outer = 0;
+    R->inner_execs = 0;
+    R->prev = INFINITY;
+    R->scale = 1.0;
+    if (!isfinite(b2)) {
+        R->status = CFP_ENAN;
+        R->rel = NAN;
+    } else if (b2 == 0.0) {
+        R->status = CFP_OK;  // the solution is zero (k_zero_if)
+        R->rel = 0.0;
+        R->r2 = 0.0;
+    } else {
+        R->r2 = *r2s;
+        R->rel = sqrt(R->r2 / b2);
+        if (!(R->rel > tol && isfinite(R->rel))) R->status = isfinite(R->rel) ? CFP_OK : CFP_ENAN;
+        else if (max_refine <= 0 || maxit <= 0) R->status = CFP_ENOCONV;
+        else R->status = RSTATE_RUN;
+    }
+    cudaGraphSetConditional(h, R->status == RSTATE_RUN ? 1u : 0u);
+}
+
+// a refinement step's start: the scaling and the inner run's scalars
+__global__ void k_ref_begin(RState* R, KState* st) {
+    if (threadIdx.x != 0) return;
+    R->scale = 1.0 / sqrt(R->r2);
+    const double need = 0.3 * R->tol / R->rel;
+    const double it = need < R->inner_tol && need >= R->inner_tol / 8 ? need : R->inner_tol;
+    memset(st, 0, sizeof(KState));
+    st->stop2 = it * it;
+    st->maxit = max(1, R->maxit - R->total);
+}
+
+__global__ void k_to32_ref(const double* __restrict__ in, float* __restrict__ out, const RState* __restrict__ R,
+                           int64_t N) {
+    const double scale = R->scale;
+    GRID_STRIDE(l, N) out[l] = (float)(in[l] * scale);
+}
+
+// k_fin_init, and the inner while node's condition
+__global__ void k_fin_init_cond(KState* st, const double* partial, int nb, cudaGraphConditionalHandle h) {
+    double rr, z;
+    sum_partials(partial, nb, rr, z);
+    if (threadIdx.x == 0) {
+        st->rr = rr;
+        st->rho = rr;
+        st->iter = 0;
+        st->flag = !isfinite(rr) ? FLAG_NAN : (rr <= st->stop2 ? FLAG_CONV : FLAG_RUN);
+        cudaGraphSetConditional(h, st->flag == FLAG_RUN ? 1u : 0u);
+    }
+}
+
+// after the inner run: its iterations, a non-finite inner result
+__global__ void k_ref_mid(RState* R, const KState* st) {
+    if (threadIdx.x != 0) return;
+    R->total += st->iter;
+    R->refinements += 1;
+    R->inner_execs += st->execs;
+    if (st->flag == FLAG_NAN) R->status = CFP_ENAN;
+}
+
+__global__ void k_add32_ref(double* __restrict__ x, const float* __restrict__ e, const RState* __restrict__ R,
+                            int64_t N) {
+    if (R->status != RSTATE_RUN) return;
+    const double inv = 1.0 / R->scale;
+    GRID_STRIDE(l, N) x[l] += (double)e[l] * inv;
+}
+
+// a step's end: the new residual, the stall and stopping tests, the outer
+// while node's condition
+__global__ void k_ref_end(RState* R, const KState* st, const double* r2s, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    R->outer += 1;
+    if (R->status == RSTATE_RUN) {
+        R->r2 = *r2s;
+        R->rel = sqrt(R->r2 / R->b2);
+        const int flag = st->flag == FLAG_RUN ? FLAG_MAXIT : st->flag;
+        if (!(R->rel < 0.9 * R->prev) && ++R->stall > R->max_restarts) R->status = status_of_flag(flag);
+        R->prev = fmin(R->prev, R->rel);
+        if (R->status == RSTATE_RUN) {
+            if (!(R->rel > R->tol && isfinite(R->rel))) R->status = isfinite(R->rel) ? CFP_OK : CFP_ENAN;
+            else if (R->refinements >= R->max_refine || R->total >= R->maxit) R->status = CFP_ENOCONV;
+        }
+        if (!isfinite(R->rel)) R->status = CFP_ENAN;
+    }
+    cudaGraphSetConditional(h, R->status == RSTATE_RUN ? 1u : 0u);
+}
+
+__global__ void k_zero_if(const RState* __restrict__ R, double* __restrict__ x, int64_t N) {
+    if (!(R->status == CFP_OK && R->b2 == 0.0)) return;
+    GRID_STRIDE(l, N) x[l] = 0.0;
+}
+
+// ||b - B x||^2 into slot 6 and out = b - B x, enqueued on s
+void enqueue_residual(cfp_ctx* c, const double* b, const double* x, double* out, cudaStream_t s) {
+    double* tmp = c->v64 + V_TMP2 * vstride(c);
+    launch_apply<double>(c, x, tmp, nullptr, 0, nullptr, s, nullptr);
+    k_resid<<<kUpdBlocks, kUpdThreads, 0, s>>>(b, tmp, out, c->partial, c->N);
+    k_fin_store<<<1, 256, 0, s>>>(c->partial, kUpdBlocks, scalar_slot(c, 6));
+    c->launches += 2;
+}
+
+// a while node after the current capture dependencies of s, its body graph
+// and the stream capturing into it; the node becomes s's dependency
+cfp_status add_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    CFP_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &graph, &deps, &edges, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return fail(CFP_ECUDA, "stream is not capturing");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CFP_CUDA(cudaGraphAddNode(&node, graph, deps, edges, nd, &cp));
+    CFP_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    *body = cp.conditional.phGraph_out[0];
+    return CFP_OK;
+}
+
+cfp_status capture_graph_of(cudaStream_t s, cudaGraph_t* g) {
+    cudaStreamCaptureStatus cs;
+    CFP_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) return fail(CFP_ECUDA, "stream is not capturing");
+    return CFP_OK;
+}
+
+// capture `fill` on a fresh stream into `body` (the body graph of a while node)
+template <class F>
+cfp_status capture_body(cudaGraph_t body, F&& fill) {
+    cudaStream_t cs;
+    CFP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    cfp_status st = e == cudaSuccess ? CFP_OK : cuda_fail(e, "cudaStreamBeginCaptureToGraph");
+    if (st == CFP_OK) {
+        st = fill(cs);
+        cudaGraph_t out = nullptr;
+        e = cudaStreamEndCapture(cs, &out);
+        if (st == CFP_OK && e != cudaSuccess) st = cuda_fail(e, "capturing a loop body");
+    }
+    cudaStreamDestroy(cs);
+    return st;
+}
+
+}  // namespace
+
+// The whole mixed-precision solve of c (right-hand side, refinement loop,
+// solution) enqueued on the capturing stream s.  The context must be
+// classified with its work space, multigrid hierarchy and graphs' settings
+// prepared for opts (prepare_device_solve).  counts: the kernels outside
+// the loops, per refinement body (outside the BiCGSTAB loop), per BiCGSTAB
+// body.
+cfp_status capture_device_solve(cfp_ctx* c, cudaStream_t s, const double* f, const double* g, const double* gi,
+                                double* u, double tol, const cfp_opts& opts, int64_t counts[3]) {
+    const int64_t l0 = c->launches;
+    int64_t l_body0 = 0, l_in0 = 0, l_in1 = 0, l_body1 = 0;
+    const int64_t N = c->N;
+    Vecs<float> V = vecs<float>(c);
+    double* rhs = c->v64 + V_RHS * vstride(c);
+    double* tmp = c->v64 + V_TMP * vstride(c);
+    double* X = c->v64 + V_X * vstride(c);
+    double* gb = c->v64 + V_TMP * vstride(c);
+    double* bg = c->v64 + V_TMP2 * vstride(c);
+    double* qf = c->v64 + V_T * vstride(c);
+    float* b32 = c->v32 + kNV32 * vstride(c);
+    float* e32 = c->v32;
+    KState* st = c->kst + 1;
+    use_aux(c, 0);
+    // the right-hand side (cfp_assemble_rhs), the masked initial iterate, ||rhs||^2, the first residual
+    launch_boundary_lift(c, g, gb, s);
+    launch_apply_lift(c, gb, bg, s);
+    launch_qf(c, f, qf, s);
+    launch_rhs_finish(c, qf, bg, c->n_ibi ? gi : c->ibi_xyz, rhs, s);
+    launch_mask_unknowns(c, u, X, s);
+    k_dot<<<kUpdBlocks, kUpdThreads, 0, s>>>(rhs, rhs, c->partial, N);
+    k_fin_store<<<1, 256, 0, s>>>(c->partial, kUpdBlocks, scalar_slot(c, 7));
+    c->launches += 2;
+    enqueue_residual(c, rhs, X, tmp, s);
+    cudaGraph_t graph = nullptr;
+    CFP_TRY(capture_graph_of(s, &graph));
+    cudaGraphConditionalHandle h_out;
+    CFP_CUDA(cudaGraphConditionalHandleCreate(&h_out, graph, 0, cudaGraphCondAssignDefault));
+    k_ref_setup<<<1, 32, 0, s>>>(c->rst, scalar_slot(c, 7), scalar_slot(c, 6), tol, opts.inner_tol, opts.maxit,
+                                 opts.max_refine, opts.max_restarts, h_out);
+    c->launches += 1;
+    CFP_CUDA(cudaGetLastError());
+    cudaGraph_t outer = nullptr;
+    CFP_TRY(add_while(s, h_out, &outer));
+    // a refinement step; its streams fork the irregular rows onto aux[1] (and
+    // aux[2] inside the BiCGSTAB body), streams of their own capture
+    const int sweeps = opts.sweeps;
+    cfp_status rs = capture_body(outer, [&](cudaStream_t cs) -> cfp_status {
+        use_aux(c, 1);
+        l_body0 = c->launches;
+        k_ref_begin<<<1, 32, 0, cs>>>(c->rst, st);
+        k_to32_ref<<<kUpdBlocks, kUpdThreads, 0, cs>>>(tmp, b32, c->rst, N);
+        k_zero<float><<<kUpdBlocks, kUpdThreads, 0, cs>>>(e32, N);
+        k_init_r<float><<<kUpdBlocks, kUpdThreads, 0, cs>>>(b32, nullptr, V.r, V.rh, V.p, c->partial, N);
+        cudaGraphConditionalHandle h_in;
+        CFP_CUDA(cudaGraphConditionalHandleCreate(&h_in, outer, 0, cudaGraphCondAssignDefault));
+        k_fin_init_cond<<<1, 256, 0, cs>>>(st, c->partial, kUpdBlocks, h_in);
+        c->launches += 5;
+        CFP_CUDA(cudaGetLastError());
+        cudaGraph_t inner = nullptr;
+        CFP_TRY(add_while(cs, h_in, &inner));
+        l_in0 = c->launches;
+        CFP_TRY(capture_body(inner, [&](cudaStream_t cs2) -> cfp_status {
+            use_aux(c, 2);
+            enqueue_body<float>(c, 1, sweeps, cs2, h_in, 1);
+            use_aux(c, 1);
+            CFP_CUDA(cudaGetLastError());
+            return CFP_OK;
+        }));
+        l_in1 = c->launches;
+        k_ref_mid<<<1, 32, 0, cs>>>(c->rst, st);
+        k_add32_ref<<<kUpdBlocks, kUpdThreads, 0, cs>>>(X, e32, c->rst, N);
+        enqueue_residual(c, rhs, X, tmp, cs);
+        k_ref_end<<<1, 32, 0, cs>>>(c->rst, st, scalar_slot(c, 6), h_out);
+        c->launches += 3;
+        l_body1 = c->launches;
+        CFP_CUDA(cudaGetLastError());
+        return CFP_OK;
+    });
+    use_aux(c, 0);
+    CFP_TRY(rs);
+    k_zero_if<<<kUpdBlocks, kUpdThreads, 0, s>>>(c->rst, X, N);
+    c->launches += 1;
+    launch_finish_solution(c, X, g, u, s);
+    CFP_CUDA(cudaGetLastError());
+    counts[2] = l_in1 - l_in0;
+    counts[1] = (l_in0 - l_body0) + (l_body1 - l_in1);
+    counts[0] = (c->launches - l0) - (l_body1 - l_body0);
+    c->launches = l0;  // counted per executed body after a run
+    return CFP_OK;
+}
+
+// What capture_device_solve needs in place before any capture: the
+// classification, the work space, the preconditioner's data for opts and
+// the settings solve_impl would take from opts.
+cfp_status prepare_device_solve(cfp_ctx* c, const cfp_opts& opts) {
+    if (opts.precision != CFP_PREC_MIXED) return fail(CFP_EINVAL, "the device-driven solve is mixed precision");
+    if (opts.maxit < 1 || opts.sweeps < 0) return fail(CFP_EINVAL, "bad maxit or sweeps");
+    if (opts.precond != CFP_PRECOND_RBGS && opts.precond != CFP_PRECOND_MG && opts.precond != CFP_PRECOND_ILU)
+        return fail(CFP_EINVAL, "unknown preconditioner");
+    if (!c->classified) CFP_TRY(classify(c));
+    c->precond_kind = opts.precond;
+    c->mg_smooth = std::max(1, opts.mg_smooth);
+    c->mg_post = opts.mg_post > 0 ? opts.mg_post : c->mg_smooth;
+    c->mg_tma = opts.mg_tma != 0;
+    if (c->precond_kind == CFP_PRECOND_MG || (c->precond_kind == CFP_PRECOND_RBGS && opts.sweeps > 0))
+        CFP_TRY(ensure_mg(c, 1));
+    if (c->precond_kind == CFP_PRECOND_ILU) CFP_TRY(ensure_ilu(c, 1));
+    CFP_TRY(ensure_work(c, true));
+    return CFP_OK;
+}
+
+}  // namespace cfp

@@ -905,6 +905,7 @@ void smooth(cfp_ctx* c, int l, const Side<T>& S, int sweeps, int first_red, int 
 }  // namespace
 
 void free_mg(cfp_ctx* c) {
+    if (!c->mg.empty()) c->generation += 1;
     for (MgLevel& L : c->mg) {
         void* ptrs[] = {L.coef64, L.coef32, L.type, L.stype, L.s64, L.s32, L.pk64, L.pk32,
                         L.ip64, L.ip32, L.rw64, L.rw32, L.fix};

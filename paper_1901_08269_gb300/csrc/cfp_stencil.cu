@@ -870,6 +870,18 @@ int apply_kind(const cfp_ctx* c, int q) {
 int apply_rows(const cfp_ctx* c, int q) { return c->apply_ty[q] ? c->apply_ty[q] : (q ? 2 : 4); }
 int apply_planes(const cfp_ctx* c, int q) { return c->apply_kc[q] ? c->apply_kc[q] : 64; }
 
+}  // namespace
+
+// the kernel and tile shape the apply of precision q runs with
+void apply_shape(const cfp_ctx* c, int q, int* kernel, int* rows, int* planes) {
+    *kernel = apply_kind(c, q);
+    *rows = *kernel == CFP_APPLY_RING ? 2 : apply_rows(c, q);
+    *planes = apply_planes(c, q);
+    if (*kernel == CFP_APPLY_RING && *planes < 32) *planes = 32;
+}
+
+namespace {
+
 // the ring's tiles: 512 columns x 2 rows x kc planes
 void ring_tiles(const cfp_ctx* c, int kc, int* ntx, int* nty, int* ntz) {
     *ntx = (c->n[0] - 2 + kRingTX - 1) / kRingTX;
