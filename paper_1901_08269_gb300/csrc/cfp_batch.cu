@@ -142,10 +142,6 @@ namespace {
 
 cfp_status batch_capture(cfp_batch* b) {
     const int n = (int)b->ctxs.size();
-    if (b->exec) {
-        cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
-    }
     for (int m = 0; m < n; ++m) {
         cfp_ctx* c = b->ctxs[m];
         CFP_TRY(prepare_device_solve(c, b->opts[m]));
@@ -180,9 +176,23 @@ cfp_status batch_capture(cfp_batch* b) {
             if (st == CFP_OK && e != cudaSuccess) st = cuda_fail(e, "capturing the batch");
         }
     }
-    if (st == CFP_OK) {
+    if (st == CFP_OK && b->exec) {
+        // the same topology (the usual case: the same problems reclassified)
+        // updates the instantiated graph in place, cheaper than a new one
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(b->exec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+    }
+    if (st == CFP_OK && !b->exec) {
         const cudaError_t e = cudaGraphInstantiate(&b->exec, graph, 0);
         if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphInstantiate (batch)");
+    }
+    if (st != CFP_OK && b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
     }
     if (graph) cudaGraphDestroy(graph);
     for (cudaStream_t s : ss)

@@ -233,9 +233,9 @@ template <class F, class S>
 cfp_status scan(cfp_ctx* c, F f, S sink, int64_t n, long long* dtotal, long long* htotal) {
     const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
     if (nb > c->scan_cap) {
-        if (c->scan_bsum) cudaFree(c->scan_bsum);
+        pool_free(c->scan_bsum, c->stream);
         c->scan_bsum = nullptr;
-        CFP_CUDA(cudaMalloc(&c->scan_bsum, sizeof(int) * std::max<int64_t>(nb, 1)));
+        CFP_CUDA(pool_malloc(&c->scan_bsum, sizeof(int) * std::max<int64_t>(nb, 1), c->stream));
         c->scan_cap = nb;
     }
     if (nb > 0) {
@@ -784,6 +784,13 @@ void free_ptr(T*& p) {
     p = nullptr;
 }
 
+// a classification's buffer back to the pool, ordered on the context's stream
+template <class T>
+void pool_free_ptr(cfp_ctx* c, T*& p) {
+    pool_free(p, c->stream);
+    p = nullptr;
+}
+
 unsigned grid_for(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
@@ -796,18 +803,18 @@ cfp_status classify(cfp_ctx* c) {
     const int64_t N = c->N;
     c->classified = false;
     c->generation += 1;
-    free_ptr(c->irr_lin);
-    free_ptr(c->ibi_off);
-    free_ptr(c->ibi_xyz);
-    free_ptr(c->corr_ptr);
-    free_ptr(c->corr_off);
-    free_ptr(c->corr_val);
-    free_ptr(c->corr_val32);
-    free_ptr(c->bib_ptr);
-    free_ptr(c->bib_idx);
-    free_ptr(c->bib_val);
-    free_ptr(c->krow);
-    free_ptr(c->krow32);
+    pool_free_ptr(c, c->irr_lin);
+    pool_free_ptr(c, c->ibi_off);
+    pool_free_ptr(c, c->ibi_xyz);
+    pool_free_ptr(c, c->corr_ptr);
+    pool_free_ptr(c, c->corr_off);
+    pool_free_ptr(c, c->corr_val);
+    pool_free_ptr(c, c->corr_val32);
+    pool_free_ptr(c, c->bib_ptr);
+    pool_free_ptr(c, c->bib_idx);
+    pool_free_ptr(c, c->bib_val);
+    pool_free_ptr(c, c->krow);
+    pool_free_ptr(c, c->krow32);
     c->gsweeps[0] = c->gsweeps[1] = -1;  // side data changes: rebuild graphs
     free_mg(c);
     free_ilu(c);
@@ -836,8 +843,8 @@ cfp_status classify(cfp_ctx* c) {
         long long nirr = 0;
         const int64_t nb = (N + kScanChunk - 1) / kScanChunk;
         if (nb > c->scan_cap) {
-            free_ptr(c->scan_bsum);
-            CFP_CUDA(cudaMalloc(&c->scan_bsum, sizeof(int) * nb));
+            pool_free_ptr(c, c->scan_bsum);
+            CFP_CUDA(pool_malloc(&c->scan_bsum, sizeof(int) * nb, c->stream));
             c->scan_cap = nb;
         }
         k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(FlagIrregular{c->type}, N, c->scan_bsum);
@@ -847,7 +854,7 @@ cfp_status classify(cfp_ctx* c) {
         CFP_CUDA(cudaMemcpyAsync(&nirr, c->dtotal, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
         CFP_CUDA(cudaStreamSynchronize(c->stream));
         c->n_irr = nirr;
-        CFP_CUDA(cudaMalloc(&c->irr_lin, sizeof(int32_t) * std::max<long long>(nirr, 1)));
+        CFP_CUDA(pool_malloc(&c->irr_lin, sizeof(int32_t) * std::max<long long>(nirr, 1), c->stream));
         k_scan_scatter<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(FlagIrregular{c->type},
                                                                       SinkSlots{c->slot, c->irr_lin}, N,
                                                                       c->scan_bsum);
@@ -865,24 +872,24 @@ cfp_status classify(cfp_ctx* c) {
     // IBI list: per irregular point, one IBI per solid axis neighbour
     int* cnt = nullptr;
     int* cnt2 = nullptr;
-    CFP_CUDA(cudaMalloc(&cnt, sizeof(int) * (nirr + 1)));
-    CFP_CUDA(cudaMalloc(&cnt2, sizeof(int) * (nirr + 1)));
-    CFP_CUDA(cudaMalloc(&c->ibi_off, sizeof(int32_t) * (nirr + 1)));
+    CFP_CUDA(pool_malloc(&cnt, sizeof(int) * (nirr + 1), c->stream));
+    CFP_CUDA(pool_malloc(&cnt2, sizeof(int) * (nirr + 1), c->stream));
+    CFP_CUDA(pool_malloc(&c->ibi_off, sizeof(int32_t) * (nirr + 1), c->stream));
     if (nirr) k_ibi_count<<<grid_for(nirr, 256), 256, 0, c->stream>>>(ia, cnt);
     if (nirr) c->launches += 1;
     CFP_TRY(scan(c, FetchInt{cnt}, SinkOffsets{c->ibi_off}, nirr, c->dtotal, &h));
     c->n_ibi = h;
     CFP_CUDA(cudaMemcpyAsync(c->ibi_off + nirr, c->dtotal, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
-    CFP_CUDA(cudaMalloc(&c->ibi_xyz, sizeof(double) * 3 * std::max<int64_t>(c->n_ibi, 1)));
+    CFP_CUDA(pool_malloc(&c->ibi_xyz, sizeof(double) * 3 * std::max<int64_t>(c->n_ibi, 1), c->stream));
     if (c->n_ibi > 0) {
         int32_t* isrc = nullptr;
-        CFP_CUDA(cudaMalloc(&isrc, sizeof(int32_t) * c->n_ibi));
+        CFP_CUDA(pool_malloc(&isrc, sizeof(int32_t) * c->n_ibi, c->stream));
         k_ibi_map<<<grid_for(nirr, 256), 256, 0, c->stream>>>(ia, c->ibi_off, isrc);
         k_ibi_roots<<<grid_for(c->n_ibi, 128), 128, 0, c->stream>>>(ia, g, isrc, c->n_ibi, c->ibi_xyz);
         c->launches += 2;
         CFP_CUDA(cudaGetLastError());
         CFP_CUDA(cudaStreamSynchronize(c->stream));
-        cudaFree(isrc);
+        pool_free(isrc, c->stream);
     }
     CFP_CUDA(cudaGetLastError());
 
@@ -904,18 +911,18 @@ cfp_status classify(cfp_ctx* c) {
     const size_t need = (size_t)nsl * (kMaxRaw * (sizeof(int32_t) + sizeof(double)) +
                                        kMaxBib * (sizeof(int32_t) + sizeof(double)));
     if (c->side_scratch_bytes < need) {
-        if (c->side_scratch) cudaFree(c->side_scratch);
+        pool_free(c->side_scratch, c->stream);
         c->side_scratch = nullptr;
         c->side_scratch_bytes = 0;
-        CFP_CUDA(cudaMalloc(&c->side_scratch, need));
+        CFP_CUDA(pool_malloc(&c->side_scratch, need, c->stream));
         c->side_scratch_bytes = need;
     }
     double* tval = static_cast<double*>(c->side_scratch);
     double* tbval = tval + (size_t)nsl * kMaxRaw;
     int32_t* toff = reinterpret_cast<int32_t*>(tbval + (size_t)nsl * kMaxBib);
     int32_t* tbidx = toff + (size_t)nsl * kMaxRaw;
-    CFP_CUDA(cudaMalloc(&c->krow, sizeof(double) * 7 * std::max<int64_t>(nirr, 1)));
-    CFP_CUDA(cudaMalloc(&c->krow32, sizeof(float) * 7 * std::max<int64_t>(nirr, 1)));
+    CFP_CUDA(pool_malloc(&c->krow, sizeof(double) * 7 * std::max<int64_t>(nirr, 1), c->stream));
+    CFP_CUDA(pool_malloc(&c->krow32, sizeof(float) * 7 * std::max<int64_t>(nirr, 1), c->stream));
     if (nirr)
         k_side<<<grid_for(nirr, 64), 64, 0, c->stream>>>(S, cnt, cnt2, toff, tval, tbidx, tbval, c->krow, ndeg,
                                                         c->derr);
@@ -933,8 +940,8 @@ cfp_status classify(cfp_ctx* c) {
     CFP_CUDA(cudaStreamSynchronize(c->stream));
     c->n_deg = hdeg;
     if (he.code) {
-        cudaFree(cnt);
-        cudaFree(cnt2);
+        pool_free(cnt, c->stream);
+        pool_free(cnt2, c->stream);
         const int i = he.lin % nx, j = (he.lin / nx) % ny, k = he.lin / (nx * ny);
         const char* why = he.detail == DETAIL_BOXIBI ? "a modified stencil needs an IBI at a box node"
                         : he.detail == DETAIL_FEWPOINTS ? "fewer than three points for a modified operator"
@@ -945,19 +952,19 @@ cfp_status classify(cfp_ctx* c) {
         return fail(CFP_EGEOM, std::string("unsupported geometry at irregular point (") + std::to_string(i) + "," +
                                    std::to_string(j) + "," + std::to_string(k) + "): " + why);
     }
-    CFP_CUDA(cudaMalloc(&c->corr_ptr, sizeof(int32_t) * (nirr + 1)));
-    CFP_CUDA(cudaMalloc(&c->bib_ptr, sizeof(int32_t) * (nirr + 1)));
+    CFP_CUDA(pool_malloc(&c->corr_ptr, sizeof(int32_t) * (nirr + 1), c->stream));
+    CFP_CUDA(pool_malloc(&c->bib_ptr, sizeof(int32_t) * (nirr + 1), c->stream));
     CFP_TRY(scan(c, FetchInt{cnt}, SinkOffsets{c->corr_ptr}, nirr, c->dtotal, &h));
     c->n_corr = h;
     CFP_CUDA(cudaMemcpyAsync(c->corr_ptr + nirr, c->dtotal, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
     CFP_TRY(scan(c, FetchInt{cnt2}, SinkOffsets{c->bib_ptr}, nirr, c->dtotal, &h));
     c->n_bib = h;
     CFP_CUDA(cudaMemcpyAsync(c->bib_ptr + nirr, c->dtotal, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
-    CFP_CUDA(cudaMalloc(&c->corr_off, sizeof(int32_t) * std::max<int64_t>(c->n_corr, 1)));
-    CFP_CUDA(cudaMalloc(&c->corr_val, sizeof(double) * std::max<int64_t>(c->n_corr, 1)));
-    CFP_CUDA(cudaMalloc(&c->corr_val32, sizeof(float) * std::max<int64_t>(c->n_corr, 1)));
-    CFP_CUDA(cudaMalloc(&c->bib_idx, sizeof(int32_t) * std::max<int64_t>(c->n_bib, 1)));
-    CFP_CUDA(cudaMalloc(&c->bib_val, sizeof(double) * std::max<int64_t>(c->n_bib, 1)));
+    CFP_CUDA(pool_malloc(&c->corr_off, sizeof(int32_t) * std::max<int64_t>(c->n_corr, 1), c->stream));
+    CFP_CUDA(pool_malloc(&c->corr_val, sizeof(double) * std::max<int64_t>(c->n_corr, 1), c->stream));
+    CFP_CUDA(pool_malloc(&c->corr_val32, sizeof(float) * std::max<int64_t>(c->n_corr, 1), c->stream));
+    CFP_CUDA(pool_malloc(&c->bib_idx, sizeof(int32_t) * std::max<int64_t>(c->n_bib, 1), c->stream));
+    CFP_CUDA(pool_malloc(&c->bib_val, sizeof(double) * std::max<int64_t>(c->n_bib, 1), c->stream));
     if (nirr)
         k_side_compact<<<grid_for(32 * nirr, 256), 256, 0, c->stream>>>(nirr, cnt, cnt2, toff, tval, tbidx, tbval,
                                                                         c->corr_ptr, c->corr_off, c->corr_val,
@@ -967,8 +974,8 @@ cfp_status classify(cfp_ctx* c) {
     c->launches += nirr ? 2 : 0;
     CFP_CUDA(cudaGetLastError());
     CFP_CUDA(cudaStreamSynchronize(c->stream));
-    cudaFree(cnt);
-    cudaFree(cnt2);
+    pool_free(cnt, c->stream);
+    pool_free(cnt2, c->stream);
     c->classified = true;
     c->class_status = CFP_OK;
     return CFP_OK;

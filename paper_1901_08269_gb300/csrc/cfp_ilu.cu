@@ -179,8 +179,8 @@ float* ilu_pivots_of<float>(cfp_ctx* c) { return c->ilu32; }
 
 void free_ilu(cfp_ctx* c) {
     if (c->ilu64 || c->ilu32) c->generation += 1;
-    if (c->ilu64) cudaFree(c->ilu64);
-    if (c->ilu32) cudaFree(c->ilu32);
+    pool_free(c->ilu64, c->stream);
+    pool_free(c->ilu32, c->stream);
     c->ilu64 = nullptr;
     c->ilu32 = nullptr;
 }
@@ -190,7 +190,7 @@ void free_ilu(cfp_ctx* c) {
 cfp_status ensure_ilu(cfp_ctx* c, int prec) {
     const int64_t N = c->N;
     if (!c->ilu64) {
-        CFP_CUDA(cudaMalloc(&c->ilu64, sizeof(double) * 2 * N));  // [pivots | w]
+        CFP_CUDA(pool_malloc(&c->ilu64, sizeof(double) * 2 * N, c->stream));  // [pivots | w]
         CFP_CUDA(cudaMemsetAsync(c->ilu64, 0, sizeof(double) * 2 * N, c->stream));
         const Grid<double> G = grid_view<double>(c);
         const Side<double> S = side_view<double>(c);
@@ -205,7 +205,7 @@ cfp_status ensure_ilu(cfp_ctx* c, int prec) {
         c->launches += nh;
     }
     if (prec == 1 && !c->ilu32) {
-        CFP_CUDA(cudaMalloc(&c->ilu32, sizeof(float) * 2 * N));
+        CFP_CUDA(pool_malloc(&c->ilu32, sizeof(float) * 2 * N, c->stream));
         CFP_CUDA(cudaMemsetAsync(c->ilu32, 0, sizeof(float) * 2 * N, c->stream));
         const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 152 * 16));
         k_ilu_to32<<<nb, 256, 0, c->stream>>>(c->type, c->ilu64, c->ilu32, N);

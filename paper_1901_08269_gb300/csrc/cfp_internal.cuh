@@ -295,6 +295,19 @@ constexpr int kNV64 = 12;  // x r rh p ph v s sh t rhs tmp tmp2
 // distance between two work fields in v64 / v32: N rounded up to 64 entries,
 // so that every field starts 256-byte aligned (bulk copies want 16)
 inline int64_t vstride(const cfp_ctx* c) { return (c->N + 63) / 64 * 64; }
+// Stream-ordered allocation from the library's memory pool of the current
+// device (freed blocks stay in the pool for reuse), for the buffers that a
+// classification and the preconditioners' set-up replace: unlike cudaMalloc
+// and cudaFree, neither synchronises the device, so contexts classify in
+// parallel beside running work.  The memory is ordered on stream s.
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s);
+template <class T>
+inline cudaError_t pool_malloc(T** p, size_t bytes, cudaStream_t s) {
+    return pool_malloc(reinterpret_cast<void**>(p), bytes, s);
+}
+inline void pool_free(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
 // selects the stream and events the apply forks its irregular rows onto
 inline void use_aux(cfp_ctx* c, int q) {
     c->aux = c->auxs[q];

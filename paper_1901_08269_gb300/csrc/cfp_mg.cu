@@ -909,8 +909,7 @@ void free_mg(cfp_ctx* c) {
     for (MgLevel& L : c->mg) {
         void* ptrs[] = {L.coef64, L.coef32, L.type, L.stype, L.s64, L.s32, L.pk64, L.pk32,
                         L.ip64, L.ip32, L.rw64, L.rw32, L.fix};
-        for (void* p : ptrs)
-            if (p) cudaFree(p);
+        for (void* p : ptrs) pool_free(p, c->stream);
     }
     c->mg.clear();
 }
@@ -996,14 +995,14 @@ cfp_status build_levels(cfp_ctx* c) {
                         rwf[L.coff[d] + I].w[q] = wfl;
                     }
             }
-            CFP_CUDA(cudaMalloc(&L.ip64, sizeof(IpPk<double>) * tot));
-            CFP_CUDA(cudaMalloc(&L.ip32, sizeof(IpPk<float>) * tot));
-            CFP_CUDA(cudaMalloc(&L.rw64, sizeof(RwPk<double>) * ctot));
-            CFP_CUDA(cudaMalloc(&L.rw32, sizeof(RwPk<float>) * ctot));
-            CFP_CUDA(cudaMemcpy(L.ip64, ipd.data(), sizeof(IpPk<double>) * tot, cudaMemcpyHostToDevice));
-            CFP_CUDA(cudaMemcpy(L.ip32, ipf.data(), sizeof(IpPk<float>) * tot, cudaMemcpyHostToDevice));
-            CFP_CUDA(cudaMemcpy(L.rw64, rwd.data(), sizeof(RwPk<double>) * ctot, cudaMemcpyHostToDevice));
-            CFP_CUDA(cudaMemcpy(L.rw32, rwf.data(), sizeof(RwPk<float>) * ctot, cudaMemcpyHostToDevice));
+            CFP_CUDA(pool_malloc(&L.ip64, sizeof(IpPk<double>) * tot, c->stream));
+            CFP_CUDA(pool_malloc(&L.ip32, sizeof(IpPk<float>) * tot, c->stream));
+            CFP_CUDA(pool_malloc(&L.rw64, sizeof(RwPk<double>) * ctot, c->stream));
+            CFP_CUDA(pool_malloc(&L.rw32, sizeof(RwPk<float>) * ctot, c->stream));
+            CFP_CUDA(cudaMemcpyAsync(L.ip64, ipd.data(), sizeof(IpPk<double>) * tot, cudaMemcpyHostToDevice, c->stream));
+            CFP_CUDA(cudaMemcpyAsync(L.ip32, ipf.data(), sizeof(IpPk<float>) * tot, cudaMemcpyHostToDevice, c->stream));
+            CFP_CUDA(cudaMemcpyAsync(L.rw64, rwd.data(), sizeof(RwPk<double>) * ctot, cudaMemcpyHostToDevice, c->stream));
+            CFP_CUDA(cudaMemcpyAsync(L.rw32, rwf.data(), sizeof(RwPk<float>) * ctot, cudaMemcpyHostToDevice, c->stream));
         }
         L.hp = ((L.n[0] + 1) / 2 + 15) / 16 * 16;
         L.Nh = (int64_t)L.hp * L.n[1] * L.n[2];
@@ -1027,11 +1026,11 @@ cfp_status build_levels(cfp_ctx* c) {
                 off += 8 * (int64_t)n;
             }
             std::vector<float> cf32(cf.begin(), cf.end());
-            CFP_CUDA(cudaMalloc(&L.coef64, sizeof(double) * nco));
-            CFP_CUDA(cudaMalloc(&L.coef32, sizeof(float) * nco));
-            CFP_CUDA(cudaMemcpy(L.coef64, cf.data(), sizeof(double) * nco, cudaMemcpyHostToDevice));
-            CFP_CUDA(cudaMemcpy(L.coef32, cf32.data(), sizeof(float) * nco, cudaMemcpyHostToDevice));
-            CFP_CUDA(cudaMalloc(&L.type, (size_t)L.N));
+            CFP_CUDA(pool_malloc(&L.coef64, sizeof(double) * nco, c->stream));
+            CFP_CUDA(pool_malloc(&L.coef32, sizeof(float) * nco, c->stream));
+            CFP_CUDA(cudaMemcpyAsync(L.coef64, cf.data(), sizeof(double) * nco, cudaMemcpyHostToDevice, c->stream));
+            CFP_CUDA(cudaMemcpyAsync(L.coef32, cf32.data(), sizeof(float) * nco, cudaMemcpyHostToDevice, c->stream));
+            CFP_CUDA(pool_malloc(&L.type, (size_t)L.N, c->stream));
             const MgLevel& Fp = c->mg[l - 1];
             const uint8_t* ft = l == 1 ? c->type : Fp.type;
             k_inject_type<<<flat_blocks(L.N), 256, 0, c->stream>>>(ft, Fp.n[0], Fp.n[1], Fp.n[2], L.type, L.n[0],
@@ -1039,13 +1038,13 @@ cfp_status build_levels(cfp_ctx* c) {
             CFP_CUDA(cudaGetLastError());
             nat = L.type;
         }
-        CFP_CUDA(cudaMalloc(&L.stype, (size_t)(2 * L.Nh)));
+        CFP_CUDA(pool_malloc(&L.stype, (size_t)(2 * L.Nh), c->stream));
         k_split_type<<<flat_blocks(2 * L.Nh), 256, 0, c->stream>>>(nat, L.n[0], L.n[1], L.n[2], L.hp, L.stype);
         CFP_CUDA(cudaGetLastError());
         // packed K coefficients of the level, both precisions
         const int ntot = L.n[0] + L.n[1] + L.n[2];
-        CFP_CUDA(cudaMalloc(&L.pk64, sizeof(PkD) * ntot));
-        CFP_CUDA(cudaMalloc(&L.pk32, sizeof(float4) * ntot));
+        CFP_CUDA(pool_malloc(&L.pk64, sizeof(PkD) * ntot, c->stream));
+        CFP_CUDA(pool_malloc(&L.pk32, sizeof(float4) * ntot, c->stream));
         const unsigned pb = (unsigned)((ntot + 127) / 128);
         k_pack_coefs<double><<<pb, 128, 0, c->stream>>>(level_grid_view<double>(c, L, l), static_cast<PkD*>(L.pk64));
         k_pack_coefs<float><<<pb, 128, 0, c->stream>>>(level_grid_view<float>(c, L, l), static_cast<float4*>(L.pk32));
@@ -1054,7 +1053,7 @@ cfp_status build_levels(cfp_ctx* c) {
     // the fine level's irregular nodes split by colour, for the follow-ups
     MgLevel& L0 = c->mg[0];
     if (c->n_irr > 0) {
-        CFP_CUDA(cudaMalloc(&L0.fix, sizeof(FixPt) * 2 * c->n_irr));
+        CFP_CUDA(pool_malloc(&L0.fix, sizeof(FixPt) * 2 * c->n_irr, c->stream));
         int* count = reinterpret_cast<int*>(c->dtotal + 5);  // scratch of the context
         CFP_CUDA(cudaMemsetAsync(count, 0, 2 * sizeof(int), c->stream));
         k_fix_list<<<flat_blocks(c->n_irr), 256, 0, c->stream>>>(c->irr_lin, c->n_irr, L0.n[0], L0.n[1], L0.hp,
@@ -1157,11 +1156,11 @@ cfp_status ensure_mg(cfp_ctx* c, int prec) {
     for (MgLevel& L : c->mg) {
         const size_t n = (size_t)kSplitVecs * L.Nh;
         if (prec == 0 && !L.s64) {
-            CFP_CUDA(cudaMalloc(&L.s64, sizeof(double) * n));
+            CFP_CUDA(pool_malloc(&L.s64, sizeof(double) * n, c->stream));
             CFP_CUDA(cudaMemsetAsync(L.s64, 0, sizeof(double) * n, c->stream));
         }
         if (prec == 1 && !L.s32) {
-            CFP_CUDA(cudaMalloc(&L.s32, sizeof(float) * n));
+            CFP_CUDA(pool_malloc(&L.s32, sizeof(float) * n, c->stream));
             CFP_CUDA(cudaMemsetAsync(L.s32, 0, sizeof(float) * n, c->stream));
             k_mark_b<<<flat_blocks(2 * L.Nh), 256, 0, c->stream>>>(L.stype, L.s32 + 2 * L.Nh, 2 * L.Nh);
             CFP_CUDA(cudaGetLastError());
