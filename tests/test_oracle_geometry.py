@@ -1,5 +1,6 @@
 """Pins of the oracle's point classification and IBI location (Sec. 2):
-brute force on tiny grids, octant symmetry, closed-form sphere roots."""
+brute force on tiny grids, octant symmetry, closed-form roots along grid
+lines: the sphere and rotated ellipsoid quadratics, the rotated torus quartic."""
 import math
 
 import numpy as np
@@ -97,6 +98,69 @@ def test_ibi_sphere_closed_form():
         assert abs(xyz[q, ax] - inside[0]) < 1e-13, (q, xyz[q, ax], inside)
         for a in other:
             assert xyz[q, a] == node[q, a]
+
+
+def _line_roots(body, node, ax):
+    """Roots t of the body's level set along node + t e_ax, from the closed
+    form: a quadratic for the ellipsoid, the quartic
+    (|q|^2 + R^2 - r^2)^2 = 4 R^2 (q_x^2 + q_y^2) for the torus, where
+    q(t) = R^T (node + t e_ax - c) is linear in t (numpy's companion-matrix
+    roots, then Newton steps on the same polynomial)."""
+    Rm = np.asarray(body["R"], float)
+    q0 = Rm.T @ (np.asarray(node, float) - np.asarray(body["c"], float))
+    d = Rm.T[:, ax]
+    if body["kind"] == "ellipsoid":
+        a = np.asarray(body["p"], float)
+        A, B, C = np.sum(d * d / a ** 2), 2 * np.sum(q0 * d / a ** 2), np.sum(q0 * q0 / a ** 2) - 1.0
+        disc = B * B - 4 * A * C
+        if disc < 0:
+            return []
+        sq = math.sqrt(disc)
+        return [(-B + sq) / (2 * A), (-B - sq) / (2 * A)]
+    Rmaj, rmin = body["p"][0], body["p"][1]
+    quad = np.array([d @ d, 2 * (q0 @ d), q0 @ q0 + Rmaj ** 2 - rmin ** 2])
+    rho2 = np.array([d[0] ** 2 + d[1] ** 2, 2 * (q0[0] * d[0] + q0[1] * d[1]), q0[0] ** 2 + q0[1] ** 2])
+    poly = np.polysub(np.polymul(quad, quad), 4 * Rmaj ** 2 * np.concatenate([[0, 0], rho2]))
+    dpoly = np.polyder(poly)
+    out = []
+    for t in np.roots(poly):
+        if abs(t.imag) > 1e-6:
+            continue
+        t = t.real
+        for _ in range(4):
+            t -= np.polyval(poly, t) / np.polyval(dpoly, t)
+        out.append(t)
+    return out
+
+
+@pytest.mark.parametrize("body", [
+    W.ellipsoid((0.021, -0.013, 0.034), (0.52, 0.31, 0.4), W.rot_euler(0.4, -0.7, 0.2)),
+    W.torus((0.02, 0.01, -0.03), 0.45, 0.16, W.rot_euler(0.1, 0.5, 0.3)),
+])
+def test_ibi_rotated_ellipsoid_and_torus_closed_forms(body):
+    # every IBI coordinate the oracle's scan-and-bisection finds must be a root
+    # of the body's own polynomial along that grid line, inside the segment
+    x = W.tanh_grid(-1, 1, 25, 0.7)
+    P = O.Problem(x, x, x, [body])
+    P.classify()
+    key, tt, xyz = P.ibi()
+    assert len(key) > 100 and np.all((tt > 0) & (tt <= 1))
+    n = x.size
+    lin, d = key // 6, key % 6
+    i, j, k = lin % n, (lin // n) % n, lin // (n * n)
+    node = np.stack([x[i], x[j], x[k]], -1)
+    for q in range(len(key)):
+        ax, sgn = d[q] // 2, (1 if d[q] % 2 else -1)
+        idx = (i[q], j[q], k[q])
+        xa, xb = x[idx[ax]], x[idx[ax] + sgn]
+        lo, hi = min(xa, xb), max(xa, xb)
+        roots = [node[q, ax] + t for t in _line_roots(body, node[q], ax)]
+        inside = [v for v in roots if lo - 1e-12 <= v <= hi + 1e-12]
+        assert inside, q
+        assert min(abs(xyz[q, ax] - v) for v in inside) < 1e-12, (q, xyz[q, ax], inside)
+        for a in range(3):
+            if a != ax:
+                assert xyz[q, a] == node[q, a]
 
 
 def test_irregular_count_growth():
