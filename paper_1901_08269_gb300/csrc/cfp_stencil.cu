@@ -653,8 +653,19 @@ __global__ void __launch_bounds__(128)
             Q[dz] = fmat(cy, XL[2], fmat(ay, XL[0], XL[1]));
         }
         T v = fmat(cz, P[2], fmat(az, P[0], P[1])) + fmat(crz, Q[2], fmat(brz, Q[1], mult(arz, Q[0])));
+        // the corrections, summed in entry order; the loads of four entries
+        // are issued before their products are added (the gather is
+        // latency-bound, and beside the ring kernel few of these CTAs fit)
         T cor = T(0);
-        for (int e = S.corr_ptr[s]; e < S.corr_ptr[s + 1]; ++e) cor = fmat(S.corr_val[e], x[l + S.corr_off[e]], cor);
+        const int e1 = S.corr_ptr[s + 1];
+        int e = S.corr_ptr[s];
+        for (; e + 4 <= e1; e += 4) {
+            const int o0 = S.corr_off[e], o1 = S.corr_off[e + 1], o2 = S.corr_off[e + 2], o3 = S.corr_off[e + 3];
+            const T w0 = S.corr_val[e], w1 = S.corr_val[e + 1], w2 = S.corr_val[e + 2], w3 = S.corr_val[e + 3];
+            const T x0 = x[l + o0], x1 = x[l + o1], x2 = x[l + o2], x3 = x[l + o3];
+            cor = fmat(w3, x3, fmat(w2, x2, fmat(w1, x1, fmat(w0, x0, cor))));
+        }
+        for (; e < e1; ++e) cor = fmat(S.corr_val[e], x[l + S.corr_off[e]], cor);
         v = v + cor;
         y[l] = v;
         if (DOT >= 1) acc0 += (double)d0[l] * (double)v;
