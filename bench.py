@@ -81,6 +81,9 @@ def parse():
                          "at --n^3 (--reps launches each); "
                          "few launches, so it is the command the ncu captures of those kernels run")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--apply-tile", default=None,
+                    help="--kernels: the apply's kernel,rows,planes for cfp_tune_apply (1: streaming, 2: the "
+                         "bulk-copy ring with rows 2), e.g. 2,2,64; default: the context's own choice")
     ap.add_argument("--seed", type=int, default=20261203)
     return ap.parse_args()
 
@@ -304,6 +307,10 @@ def kernel_arm(args):
     ids = {"rbgs": cfp.KERNEL_RBGS, "mg_sweep": cfp.KERNEL_MG_SWEEP, "apply": cfp.KERNEL_APPLY,
            "update": cfp.KERNEL_UPDATE}
     out = {"mode": "kernels", "n": args.n, "precision": args.precision, "reps": args.reps}
+    if args.apply_tile:
+        k, r, q = (int(v) for v in args.apply_tile.split(","))
+        ctx.tune_apply(prec, r, q, kernel=k)
+    out["apply_tile"] = ctx.apply_shape(prec)
     for name in args.kernels.split(","):
         if name.startswith("nn_conv") or name.startswith("nn_wgrad"):
             # nn_conv / nn_wgrad: 16 -> 16 channels; nn_conv64 / nn_wgrad128: c -> c

@@ -102,9 +102,11 @@ typedef struct {
     int mg_tma;        /* 1 (default): the FP32 red-black half-sweeps of the
                           multigrid levels (and of the fine level's sweeps)
                           with at least 192 nodes per row stream their tiles
-                          through shared memory with TMA bulk-tensor copies;
-                          0: plain loads.  Same arithmetic, bitwise equal
-                          results                                          */
+                          through shared memory with TMA bulk-tensor copies,
+                          and a coarse level of at most 2^15 nodes does all
+                          sweeps of a smoothing in one single-CTA launch;
+                          0: plain loads, one launch per half-sweep.  Same
+                          arithmetic, bitwise equal results               */
 } cfp_opts;
 
 typedef struct {

@@ -131,6 +131,20 @@ __device__ __forceinline__ bool is_unknown(uint8_t t) { return t == CFP_REGULAR 
 // 1 / d; the diagonal of K is a normal number), a single instruction where the
 // correctly rounded one costs a short sequence: the FP32 smoother is the inner
 // preconditioner of the mixed solve, whose FP64 refinement removes the error.
+// The off-diagonal sum of a half-sweep node,
+//   (cx_lo xm + cx_hi xp) + (cy_lo ym + cy_hi yp) + (cz_lo zm + cz_hi zp),
+// each pair one product and one fused multiply-add in this order: written
+// out so that every kernel that updates a node (one launch per half-sweep,
+// the TMA pipeline, the single-CTA smoothing) rounds it the same way.
+__device__ __forceinline__ float rb_pair(float a, float x, float b, float y) { return __fmaf_rn(b, y, __fmul_rn(a, x)); }
+__device__ __forceinline__ double rb_pair(double a, double x, double b, double y) {
+    return __fma_rn(b, y, __dmul_rn(a, x));
+}
+template <class T>
+__device__ __forceinline__ T rb_sum(T cxl, T cxh, T cyl, T cyh, T czl, T czh, T xm, T xp, T ym, T yp, T zm, T zp) {
+    return (rb_pair(cxl, xm, cxh, xp) + rb_pair(cyl, ym, cyh, yp)) + rb_pair(czl, zm, czh, zp);
+}
+
 __device__ __forceinline__ float times_rcp(float x, float d) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
@@ -201,7 +215,7 @@ __global__ void __launch_bounds__(kSplitThreads)
         live[q] = inz[q] && i >= 1 && i <= nx - 2 && is_unknown(t);
         T v = bv[q];
         if (MODE == 0 || MODE == 3)
-            v -= (ckx.x * xm + ckx.z * xp) + (cky.x * ym + cky.z * yp) + (ckz.x * zm + ckz.z * zp);
+            v -= rb_sum(ckx.x, ckx.z, cky.x, cky.z, ckz.x, ckz.z, xm, xp, ym, yp, zm, zp);
         val[q] = times_rcp(v, dg);
         xo[q] = par ? xm : xp;  // MODE 3: the other node of the pair
         oo[q] = o;
@@ -224,6 +238,60 @@ __global__ void __launch_bounds__(kSplitThreads)
         } else if (live[q]) {
             H.eown[o] = val[q];
         }
+    }
+}
+
+// All the red-black sweeps of one smoothing of a small level (at most
+// kCoarseMaxNodes nodes: the coarsest level's 16 sweeps, a 17^3 level's
+// pre- or post-smoothing) in one CTA, with a CTA barrier between
+// half-sweeps, where separate launches would cost a few microseconds each
+// for a few thousand nodes.  The node update is k_sweep_split's (MODE 1 for
+// a first red half-sweep from zero, MODE 0 otherwise) with the same rb_sum
+// and reciprocal: the results are bitwise equal.
+constexpr int kCoarseThreads = 512;
+constexpr int64_t kCoarseMaxNodes = int64_t(1) << 15;
+
+template <class T>
+__global__ void __launch_bounds__(kCoarseThreads) k_smooth_cta(SLev<T> L, int sweeps, int first_red_zero) {
+    const int nx = L.nx, ny = L.ny, nz = L.nz, hp = L.hp;
+    const unsigned hs = L.hs;
+    const int mp = (nx - 2) / 2 + 1;  // pairs m with 2 m <= nx - 2
+    const int64_t items = (int64_t)mp * (ny - 2) * (nz - 2);
+    for (int q = 0; q < 2 * sweeps; ++q) {
+        const int colour = q & 1;
+        const bool zero = q == 0 && first_red_zero;
+        // plain pointers: the e arrays are written by this launch's earlier
+        // half-sweeps, so their loads must not take the non-coherent
+        // read-only path that a const __restrict__ pointer allows
+        T* eown = L.e[colour];
+        const T* eoth = L.e[1 - colour];
+        const T* bown = L.b[colour];
+        const uint8_t* ty = L.ty[colour];
+        for (int64_t it = threadIdx.x; it < items; it += blockDim.x) {
+            const int m = (int)(it % mp);
+            const int64_t rest = it / mp;
+            const int j = 1 + (int)(rest % (ny - 2)), k = 1 + (int)(rest / (ny - 2));
+            const int par = (colour + j + k) & 1;
+            const int i = 2 * m + par;
+            const unsigned o = (unsigned)k * hs + (unsigned)(j * hp + m);
+            const uint8_t t = ty[o];
+            T v = bown[o];
+            T xm = T(0), xp = T(0), ym = T(0), yp = T(0), zm = T(0), zp = T(0);
+            if (!zero) {
+                xm = eoth[o - 1 + par];
+                xp = eoth[o + par];
+                ym = eoth[o - hp];
+                yp = eoth[o + hp];
+                zm = eoth[o - hs];
+                zp = eoth[o + hs];
+            }
+            const PkT<T> ckx = L.cx[i], cky = L.cy[j], ckz = L.cz[k];
+            const T dg = ckx.y + (cky.y + ckz.y);
+            if (!zero) v -= rb_sum(ckx.x, ckx.z, cky.x, cky.z, ckz.x, ckz.z, xm, xp, ym, yp, zm, zp);
+            const T val = times_rcp(v, dg);
+            if (i >= 1 && i <= nx - 2 && is_unknown(t)) eown[o] = val;
+        }
+        __syncthreads();
     }
 }
 
@@ -447,7 +515,7 @@ __global__ void __launch_bounds__(kTmaThreads)
                     if (in && jin[ly] && unk) ep[ly * hp] = b - ke;
                 } else {
                     float v = b;
-                    v -= (cx.x * xm + cx.z * xp) + (cya[ly] * ym + cyc[ly] * yp) + (cz.x * zm + cz.z * zp);
+                    v -= rb_sum(cx.x, cx.z, cya[ly], cyc[ly], cz.x, cz.z, xm, xp, ym, yp, zm, zp);
                     if (KIND == 0) {
                         if (in && jin[ly] && unk) ep[ly * hp] = times_rcp(v, dg);
                     } else if (jin[ly]) {
@@ -896,6 +964,14 @@ template <class T>
 void smooth(cfp_ctx* c, int l, const Side<T>& S, int sweeps, int first_red, int last_black, const T* rho, T* phi,
             cudaStream_t s) {
     const SLev<T> L = slev<T>(c, l);
+    // a small coarse level (no irregular rows, plain or from-zero modes):
+    // one CTA does every half-sweep
+    if (c->mg_tma && l > 0 && c->mg[l].N <= kCoarseMaxNodes && (first_red == 0 || first_red == 1) &&
+        last_black == 0) {
+        k_smooth_cta<T><<<1, kCoarseThreads, 0, s>>>(L, sweeps, first_red);
+        c->launches += 1;
+        return;
+    }
     for (int q = 0; q < sweeps; ++q) {
         half_sweep<T>(c, l, L, S, 0, q == 0 ? first_red : 0, rho, phi, s);
         half_sweep<T>(c, l, L, S, 1, q == sweeps - 1 ? last_black : 0, rho, phi, s);
