@@ -77,7 +77,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--kernels", default=None,
                     help="time single kernels instead of the solve: a comma list of mg_sweep, rbgs, apply, "
-                         "update, nn_conv[C], nn_wgrad[C] (C -> C channels, default 16) on the config-3 geometry "
+                         "update, prolong, restrict, nn_conv[C], nn_wgrad[C] (C -> C channels, default 16) on the "
+                         "config-3 geometry "
                          "at --n^3 (--reps launches each); "
                          "few launches, so it is the command the ncu captures of those kernels run")
     ap.add_argument("--reps", type=int, default=3)
@@ -305,12 +306,11 @@ def kernel_arm(args):
     ctx.classify_points()
     prec = cfp.PREC_MIXED if args.precision == "mixed" else cfp.PREC_FP64
     ids = {"rbgs": cfp.KERNEL_RBGS, "mg_sweep": cfp.KERNEL_MG_SWEEP, "apply": cfp.KERNEL_APPLY,
-           "update": cfp.KERNEL_UPDATE}
+           "update": cfp.KERNEL_UPDATE, "prolong": cfp.KERNEL_PROLONG, "restrict": cfp.KERNEL_RESTRICT}
     out = {"mode": "kernels", "n": args.n, "precision": args.precision, "reps": args.reps}
     if args.apply_tile:
         k, r, q = (int(v) for v in args.apply_tile.split(","))
         ctx.tune_apply(prec, r, q, kernel=k)
-    out["apply_tile"] = ctx.apply_shape(prec)
     for name in args.kernels.split(","):
         if name.startswith("nn_conv") or name.startswith("nn_wgrad"):
             # nn_conv / nn_wgrad: 16 -> 16 channels; nn_conv64 / nn_wgrad128: c -> c
@@ -320,6 +320,7 @@ def kernel_arm(args):
             continue
         ms, by = ctx.time_kernel(ids[name], prec, reps=args.reps)
         out[name] = {"ms": ms, "bytes": by, "GBps": by / ms / 1e6}
+    out["apply_tile"] = ctx.apply_shape(prec)  # after the timings, which set up the ring where it applies
     ctx.close()
     print(json.dumps(out), flush=True)
     return 0

@@ -103,9 +103,11 @@ typedef struct {
                           multigrid levels (and of the fine level's sweeps)
                           with at least 192 nodes per row stream their tiles
                           through shared memory with TMA bulk-tensor copies,
-                          and a coarse level of at most 2^15 nodes does all
-                          sweeps of a smoothing in one single-CTA launch;
-                          0: plain loads, one launch per half-sweep.  Same
+                          a coarse level of at most 2^15 nodes does all
+                          sweeps of a smoothing in one single-CTA launch,
+                          and the prolongation runs one thread per coarse
+                          cell; 0: plain loads, one launch per half-sweep,
+                          one prolongation thread per fine pair.  Same
                           arithmetic, bitwise equal results               */
 } cfp_opts;
 
@@ -372,7 +374,7 @@ enum { CFP_KERNEL_APPLY = 0,    /* B x with the fused (r_hat0, v) dot, as in
                                    CFP_KERNEL_MG_SWEEP                       */
        CFP_KERNEL_UPDATE = 2,   /* the fused x/r update with two dots (lines
                                    11-12)                                    */
-       CFP_KERNEL_MG_SWEEP = 3  /* one red half-sweep on the fine level of the
+       CFP_KERNEL_MG_SWEEP = 3, /* one red half-sweep on the fine level of the
                                    multigrid preconditioner (CFP_PRECOND_MG),
                                    red and black nodes stored in separate
                                    arrays; includes the follow-up launch that
@@ -380,7 +382,13 @@ enum { CFP_KERNEL_APPLY = 0,    /* B x with the fused (r_hat0, v) dot, as in
                                    irregular nodes.  In FP32 on a fine level
                                    of >= 192 nodes per row, the TMA-fed
                                    kernel (unless the last solve or
-                                   preconditioner call set mg_tma = 0)      */ };
+                                   preconditioner call set mg_tma = 0)      */
+       CFP_KERNEL_PROLONG = 4,  /* the multigrid prolongation of the second
+                                   level's correction onto the fine level's
+                                   black nodes (trilinear in the stretched
+                                   coordinates)                              */
+       CFP_KERNEL_RESTRICT = 5  /* the full-weighting restriction of the fine
+                                   level's red residual to the second level */ };
 
 /*
  * Profiling aid: time `reps` >= 1 back-to-back launches of one kernel of the
@@ -392,8 +400,13 @@ enum { CFP_KERNEL_APPLY = 0,    /* B x with the fused (r_hat0, v) dot, as in
  *                     (minimum traffic: per interior node, apply 3 values
  *                     (x, y and the dot operand); a half-sweep 1.5 values
  *                     (rho and the new phi of its colour, phi of the other
- *                     colour); update 8 values over all nodes)
- * Requires classification.  Synchronises.  Errors: CFP_ESTATE, CFP_EINVAL,
+ *                     colour); update 8 values over all nodes; prolongation
+ *                     per fine interior node half of (type byte + e read +
+ *                     e written) plus the coarse e once (1/8 value);
+ *                     restriction half a value (the red residual) plus the
+ *                     coarse type byte and b once (1/8 each))
+ * Requires classification.  Synchronises.  Errors: CFP_ESTATE, CFP_EINVAL
+ * (also for a transfer on a grid with a single multigrid level),
  * CFP_ECUDA.
  */
 cfp_status cfp_time_kernel(cfp_ctx* ctx, int kernel, int precision, int reps,

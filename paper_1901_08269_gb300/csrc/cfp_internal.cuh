@@ -357,6 +357,9 @@ void launch_rbgs_split(cfp_ctx* c, int sweeps, const T* rho, T* phi, cudaStream_
 // one plain red half-sweep on the fine level's split vectors (timing aid)
 template <class T>
 void launch_mg_half_sweep(cfp_ctx* c, cudaStream_t s);
+// the V-cycle's restriction / prolongation between levels 0 and 1 (false: one level only)
+template <class T>
+bool launch_mg_transfer(cfp_ctx* c, bool prolong, cudaStream_t s);
 void launch_qf(cfp_ctx* c, const double* f, double* out, cudaStream_t s);
 void launch_rhs_finish(cfp_ctx* c, const double* qf, const double* bg, const double* g_ibi,
                        double* rhs, cudaStream_t s);

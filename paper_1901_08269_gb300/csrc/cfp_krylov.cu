@@ -451,6 +451,8 @@ cfp_status time_kernel_t(cfp_ctx* c, int prec, int kernel, int reps, double* ms,
     auto launch = [&]() {
         if (kernel == CFP_KERNEL_APPLY) launch_apply<T>(c, V.ph, V.v, V.rh, 1, c->partial, c->stream, nullptr);
         else if (kernel == CFP_KERNEL_RBGS || kernel == CFP_KERNEL_MG_SWEEP) launch_mg_half_sweep<T>(c, c->stream);
+        else if (kernel == CFP_KERNEL_PROLONG || kernel == CFP_KERNEL_RESTRICT)
+            launch_mg_transfer<T>(c, kernel == CFP_KERNEL_PROLONG, c->stream);
         else
             k_update_xr<T><<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(V.x, V.r, V.ph, V.sh, V.s, V.t, V.rh, st,
                                                                       c->partial, c->N);
@@ -473,7 +475,9 @@ cfp_status time_kernel_t(cfp_ctx* c, int prec, int kernel, int reps, double* ms,
     if (bytes)
         *bytes = kernel == CFP_KERNEL_APPLY ? 3.0 * w * nint
                : kernel == CFP_KERNEL_RBGS || kernel == CFP_KERNEL_MG_SWEEP ? 1.5 * w * nint
-                                           : 8.0 * w * (double)c->N;
+               : kernel == CFP_KERNEL_PROLONG ? (0.5 * (1.0 + 2.0 * w) + w / 8.0) * nint
+               : kernel == CFP_KERNEL_RESTRICT ? (0.5 * w + (1.0 + w) / 8.0) * nint
+                                               : 8.0 * w * (double)c->N;
     return CFP_OK;
 }
 }  // namespace
@@ -527,10 +531,12 @@ cfp_status tune_apply(cfp_ctx* c, int prec, int kind, int rows, int planes, int 
 }
 
 cfp_status time_kernel(cfp_ctx* c, int kernel, int prec, int reps, double* ms, double* bytes) {
-    if (kernel < CFP_KERNEL_APPLY || kernel > CFP_KERNEL_MG_SWEEP || reps < 1 || !ms)
+    if (kernel < CFP_KERNEL_APPLY || kernel > CFP_KERNEL_RESTRICT || reps < 1 || !ms)
         return fail(CFP_EINVAL, "bad kernel id, reps or output pointer");
     CFP_TRY(ensure_work(c, prec == CFP_PREC_MIXED));
-    if (kernel == CFP_KERNEL_MG_SWEEP || kernel == CFP_KERNEL_RBGS) CFP_TRY(ensure_mg(c, prec == CFP_PREC_MIXED ? 1 : 0));
+    if (kernel != CFP_KERNEL_APPLY && kernel != CFP_KERNEL_UPDATE) CFP_TRY(ensure_mg(c, prec == CFP_PREC_MIXED ? 1 : 0));
+    if ((kernel == CFP_KERNEL_PROLONG || kernel == CFP_KERNEL_RESTRICT) && c->mg.size() < 2)
+        return fail(CFP_EINVAL, "the grid has a single multigrid level: no transfer to time");
     CFP_TRY(prec == CFP_PREC_MIXED ? time_kernel_t<float>(c, 1, kernel, reps, ms, bytes)
                                    : time_kernel_t<double>(c, 0, kernel, reps, ms, bytes));
     return check_waits(c);

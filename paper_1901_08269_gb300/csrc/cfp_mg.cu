@@ -664,7 +664,9 @@ __global__ void k_restrict_split(Transfer<T> X, SLev<T> F, SLev<T> C) {
     if (I > ncx - 2) return;
     const int cc = (I + J + K) & 1;
     const unsigned oc = (unsigned)(K * ncy + J) * (unsigned)C.hp + (unsigned)(I >> 1);
-    if (!is_unknown((cc ? C.ty[1] : C.ty[0])[oc])) return;
+    // the type decides only the store, so the fine loads (in bounds for every
+    // interior coarse node) are issued beside it
+    const uint8_t tc = (cc ? C.ty[1] : C.ty[0])[oc];
     const int nfy = F.ny;
     const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
     const RwPk<T> rx = X.rw[0][I], ry = X.rw[1][J], rz = X.rw[2][K];
@@ -672,22 +674,28 @@ __global__ void k_restrict_split(Transfer<T> X, SLev<T> F, SLev<T> C) {
     const T* wy = ry.w;
     const T* wz = rz.w;
     const T* __restrict__ r0 = F.r0;
-    T s = 0, w = 0;
+    T s = 0;
+    // fine node (2I - 1 + a, 2J - 1 + b, 2K - 1 + c) is red, (i + j + k) even,
+    // exactly where a + b + c is odd: a pattern fixed at compile time, so
+    // only those 13 of the 27 terms are formed
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int k = fk - 1 + c;
+#pragma unroll
         for (int b = 0; b < 3; ++b) {
             const int j = fj - 1 + b;
             const T wyz = wy[b] * wz[c];
             const unsigned rowo = (unsigned)(k * nfy + j) * (unsigned)F.hp;
+#pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const int i = fi - 1 + a;
-                const T ww = wx[a] * wyz;
-                w += ww;
-                if (((i + j + k) & 1) == 0) s += ww * r0[rowo + (unsigned)(i >> 1)];
+                if ((a + b + c) & 1) s += (wx[a] * wyz) * r0[rowo + (unsigned)(i >> 1)];
             }
         }
     }
-    (cc ? C.b[1] : C.b[0])[oc] = s / w;
+    // P^T 1 at the node: the sum of all 27 weights, separable per axis
+    const T w = ((wx[0] + wx[1]) + wx[2]) * ((wy[0] + wy[1]) + wy[2]) * ((wz[0] + wz[1]) + wz[2]);
+    if (is_unknown(tc)) (cc ? C.b[1] : C.b[0])[oc] = s / w;
 }
 
 // e1 += P e_c at the fine black unknowns (the red values are overwritten by
@@ -739,6 +747,67 @@ __global__ void __launch_bounds__(kSplitThreads) k_prolong_split(Transfer<T> X, 
 }
 
 // packed (ka, kb, kc) per index of each axis from a level's metric arrays
+// The same e1 += P e_c with one thread per coarse cell (I, J, K): the fine
+// nodes 2I .. 2I + 1 x 2J .. 2J + 1 x 2K .. 2K + 1 interpolate between the
+// cell's eight corners (every interior fine node's lower table index is its
+// cell's), so the four black nodes of a cell share eight coarse loads, and
+// consecutive threads touch consecutive split entries.  Per node the
+// expression is k_prolong_split's.
+template <class T>
+__global__ void __launch_bounds__(128) k_prolong_cell(Transfer<T> X, SLev<T> F, SLev<T> C) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y, K = blockIdx.z;
+    if (I > C.nx - 2) return;
+    const int nx = F.nx, ny = F.ny, nz = F.nz;
+    const unsigned hc = (unsigned)C.hp;
+    // the corners: colour (I + a + J + b + K + c) & 1, entry ((K + c) ncy + J + b) hc + (I + a) >> 1
+    const int p = (I + J + K) & 1;
+    const unsigned r00 = (unsigned)(K * C.ny + J) * hc, r01 = r00 + hc, r10 = r00 + C.hs, r11 = r10 + hc;
+    const unsigned x0 = (unsigned)(I >> 1), x1 = (unsigned)((I + 1) >> 1);
+    const T* __restrict__ ea = p ? C.e[1] : C.e[0];
+    const T* __restrict__ eb = p ? C.e[0] : C.e[1];
+    const T e000 = ea[r00 + x0], e001 = eb[r00 + x1], e010 = eb[r01 + x0], e011 = ea[r01 + x1];
+    const T e100 = eb[r10 + x0], e101 = ea[r10 + x1], e110 = ea[r11 + x0], e111 = eb[r11 + x1];
+    T* __restrict__ e1 = F.e[1];
+    // every load of the four nodes first (indices clamped into the level, so
+    // each is in bounds), the decisions after: the loads overlap
+    const IpPk<T> px0 = X.ip[0][min(2 * I, nx - 1)], px1 = X.ip[0][min(2 * I + 1, nx - 1)];
+    IpPk<T> pyv[2], pzv[2];
+    unsigned o[2][2];
+    uint8_t t[2][2];
+    T f[2][2];
+    bool live[2][2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int k = 2 * K + c, kc = min(max(k, 1), nz - 2);
+        pzv[c] = X.ip[2][kc];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int j = 2 * J + b, jc = min(max(j, 1), ny - 2);
+            if (c == 0) pyv[b] = X.ip[1][jc];
+            const int i = 2 * I + ((1 + j + k) & 1);  // the black node of this row in the cell
+            o[c][b] = (unsigned)kc * F.hs + (unsigned)(jc * F.hp + I);  // pair m = I
+            t[c][b] = F.ty[1][o[c][b]];
+            f[c][b] = e1[o[c][b]];
+            live[c][b] = k >= 1 && k <= nz - 2 && j >= 1 && j <= ny - 2 && i >= 1 && i <= nx - 2;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const T az0 = pzv[c].wlo, az1 = pzv[c].whi;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            if (!live[c][b] || !is_unknown(t[c][b])) continue;
+            const T ay0 = pyv[b].wlo, ay1 = pyv[b].whi;
+            const IpPk<T>& px = ((1 + 2 * J + b + 2 * K + c) & 1) ? px1 : px0;
+            const T ax0 = px.wlo, ax1 = px.whi;
+            const T f0 = f[c][b];
+            e1[o[c][b]] = f0 + (az0 * (ay0 * (ax0 * e000 + ax1 * e001) + ay1 * (ax0 * e010 + ax1 * e011)) +
+                                az1 * (ay0 * (ax0 * e100 + ax1 * e101) + ay1 * (ax0 * e110 + ax1 * e111)));
+        }
+    }
+}
+
 template <class T>
 __global__ void k_pack_coefs(Grid<T> G, PkT<T>* __restrict__ out) {
     const int n[3] = {G.nx, G.ny, G.nz};
@@ -1250,6 +1319,19 @@ cfp_status ensure_mg(cfp_ctx* c, int prec) {
 
 // phi = V(rho): one V-cycle from zero on the level hierarchy.  phi is written
 // at every interior node of the interior rows (zero at the non-unknowns).
+// level l + 1's correction onto level l's black nodes: one thread per coarse
+// cell (k_prolong_cell) with the fast kernels, else one per fine pair
+template <class T>
+void launch_prolong(cfp_ctx* c, int l, const SLev<T>& F, const SLev<T>& C, cudaStream_t s) {
+    if (c->mg_tma) {
+        const MgLevel& Cn = c->mg[l + 1];
+        const dim3 g((unsigned)((Cn.n[0] - 1 + 127) / 128), (unsigned)(Cn.n[1] - 1), (unsigned)(Cn.n[2] - 1));
+        k_prolong_cell<T><<<g, 128, 0, s>>>(transfer<T>(c->mg[l]), F, C);
+    } else {
+        k_prolong_split<T><<<plane_grid(c->mg[l].n), plane_block(c->mg[l].n), 0, s>>>(transfer<T>(c->mg[l]), F, C);
+    }
+}
+
 template <class T>
 void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
     const int nl = (int)c->mg.size();
@@ -1283,7 +1365,7 @@ void launch_precond_mg(cfp_ctx* c, const T* rho, T* phi, cudaStream_t s) {
     // fine level writes phi
     for (int l = nl - 2; l >= 0; --l) {
         const SLev<T> F = slev<T>(c, l), C = slev<T>(c, l + 1);
-        k_prolong_split<T><<<plane_grid(c->mg[l].n), plane_block(c->mg[l].n), 0, s>>>(transfer<T>(c->mg[l]), F, C);
+        launch_prolong<T>(c, l, F, C, s);
         c->launches += 1;
         smooth<T>(c, l, l == 0 ? S0 : Sc, npost, 0, l == 0 ? 3 : 0, rho, phi, s);
     }
@@ -1300,6 +1382,24 @@ void launch_mg_half_sweep(cfp_ctx* c, cudaStream_t s) {
     half_sweep<T>(c, 0, L, side_view<T>(c), 0, 0, (const T*)nullptr, (T*)nullptr, s);
 }
 
+// one transfer between the fine level and the next: restrict (the red
+// residual to b of level 1) or prolong (level 1's correction to the fine
+// black nodes), as in the V-cycle; false without a second level
+template <class T>
+bool launch_mg_transfer(cfp_ctx* c, bool prolong, cudaStream_t s) {
+    if (c->mg.size() < 2) return false;
+    const SLev<T> F = slev<T>(c, 0), C = slev<T>(c, 1);
+    if (prolong) {
+        launch_prolong<T>(c, 0, F, C, s);
+    } else {
+        const MgLevel& Cn = c->mg[1];
+        const dim3 gr((unsigned)((Cn.n[0] - 2 + 127) / 128), (unsigned)(Cn.n[1] - 2), (unsigned)(Cn.n[2] - 2));
+        k_restrict_split<T><<<gr, 128, 0, s>>>(transfer<T>(c->mg[0]), F, C);
+    }
+    c->launches += 1;
+    return true;
+}
+
 cfp_status diag_bounded_wait(cfp_ctx* c) {
     k_wait_diag<<<1, 32, 0, c->stream>>>(c->dwait);
     c->launches += 1;
@@ -1313,5 +1413,7 @@ template void launch_mg_half_sweep<double>(cfp_ctx*, cudaStream_t);
 template void launch_rbgs_split<double>(cfp_ctx*, int, const double*, double*, cudaStream_t);
 template void launch_rbgs_split<float>(cfp_ctx*, int, const float*, float*, cudaStream_t);
 template void launch_mg_half_sweep<float>(cfp_ctx*, cudaStream_t);
+template bool launch_mg_transfer<double>(cfp_ctx*, bool, cudaStream_t);
+template bool launch_mg_transfer<float>(cfp_ctx*, bool, cudaStream_t);
 
 }  // namespace cfp

@@ -232,13 +232,23 @@ def test_kernel_timer_covers_every_kernel():
     ctx.classify_points()
     nint = 31 ** 3
     for prec, size in ((cfp.PREC_FP64, 8), (cfp.PREC_MIXED, 4)):
-        for kid, per in ((cfp.KERNEL_APPLY, 3.0 * nint), (cfp.KERNEL_RBGS, 1.5 * nint),
-                         (cfp.KERNEL_MG_SWEEP, 1.5 * nint), (cfp.KERNEL_UPDATE, 8.0 * w.N)):
+        for kid, per in ((cfp.KERNEL_APPLY, 3.0 * nint * size), (cfp.KERNEL_RBGS, 1.5 * nint * size),
+                         (cfp.KERNEL_MG_SWEEP, 1.5 * nint * size), (cfp.KERNEL_UPDATE, 8.0 * w.N * size),
+                         (cfp.KERNEL_PROLONG, (0.5 * (1 + 2 * size) + size / 8) * nint),
+                         (cfp.KERNEL_RESTRICT, (0.5 * size + (1 + size) / 8) * nint)):
             ms, by = ctx.time_kernel(kid, prec, reps=2)
-            assert ms > 0.0 and by == per * size
+            assert ms > 0.0 and by == per
     with pytest.raises(cfp.CfpError):
-        ctx.time_kernel(4, cfp.PREC_FP64, reps=1)
+        ctx.time_kernel(6, cfp.PREC_FP64, reps=1)
     ctx.close()
+    # a grid with a single multigrid level has no transfer to time
+    x = W.uniform_grid(0, 1, 9)
+    small = cfp.Context(x, x, x, [])
+    small.classify_points()
+    with pytest.raises(cfp.CfpError) as e:
+        small.time_kernel(cfp.KERNEL_PROLONG, cfp.PREC_MIXED, reps=1)
+    assert e.value.status == cfp.EINVAL
+    small.close()
 
 
 def test_bounded_wait_gives_up_and_the_context_stays_usable():
