@@ -261,9 +261,12 @@ cfp_status cfp_solve(cfp_ctx* ctx, const double* f_dev, const double* g_nodes_de
                      const cfp_opts* opts, cfp_info* info);
 
 /*
- * cfp_solve with host buffers: copies f, g (box values), g_ibi and the
- * initial guess u to context-owned device buffers, solves, copies u back.
- * The host buffers are best page-locked.  Same arguments and errors.
+ * cfp_solve with host buffers.  Page-locked buffers (cudaHostAlloc,
+ * cudaHostRegister) are used in place: the kernels read f, g (box values),
+ * g_ibi and the initial guess from host memory and the last one writes u
+ * there, each once, over the host link.  Other host memory is copied to
+ * context-owned device buffers, solved on, and u copied back.  Same
+ * arguments and errors.
  */
 cfp_status cfp_solve_host(cfp_ctx* ctx, const double* f_host,
                           const double* g_nodes_host, const double* g_ibi_host,

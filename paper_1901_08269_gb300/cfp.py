@@ -443,8 +443,9 @@ class Context:
         return ms.value, by.value
 
     def solve_host(self, f, g_nodes, g_ibi, u, tol=1e-12, opts=None, check=True, **kw):
-        """Host-buffer solve: f, g_nodes, g_ibi, u are CPU tensors (ideally
-        pinned); copies in and out happen inside the library call."""
+        """Host-buffer solve: f, g_nodes, g_ibi, u are CPU tensors; pinned
+        ones are read and written in place by the kernels, others are copied
+        in and out inside the library call."""
         o = opts if opts is not None else default_opts(**kw)
         info = Info()
         for t in (f, g_nodes, u):

@@ -255,8 +255,15 @@ cfp_status cfp_assemble_rhs(cfp_ctx* c, const double* f, const double* g, const 
     CFP_TRY(need_field(g, "g_nodes_dev"));
     CFP_TRY(need_field(rhs, "rhs_dev"));
     if (c->n_ibi > 0) CFP_TRY(need_field(gi, "g_ibi_dev"));
+    return assemble_rhs(c, f, g, gi, rhs);
+}
+
+}  // extern "C"
+
+// the right-hand side after the checks (also of the solves, whose f, g and
+// g_ibi may be page-locked host memory the kernels read in place)
+cfp_status cfp::assemble_rhs(cfp_ctx* c, const double* f, const double* g, const double* gi, double* rhs) {
     CFP_TRY(ensure_work(c, false));
-    const int64_t N = c->N;
     double* gb = c->v64 + V_TMP * vstride(c);
     double* bg = c->v64 + V_TMP2 * vstride(c);
     double* qf = c->v64 + V_T * vstride(c);
@@ -268,6 +275,8 @@ cfp_status cfp_assemble_rhs(cfp_ctx* c, const double* f, const double* g, const 
     CFP_CUDA(cudaGetLastError());
     return CFP_OK;
 }
+
+extern "C" {
 
 cfp_status cfp_apply(cfp_ctx* c, const double* x, double* y) {
     CFP_TRY(need_classified(c));
@@ -362,6 +371,31 @@ cfp_status cfp_solve_host(cfp_ctx* c, const double* f, const double* g, const do
     if (!f || !g || !u) return fail(CFP_EINVAL, "NULL host buffer");
     if (!c->classified) CFP_TRY(classify(c));
     if (c->n_ibi > 0 && !gi) return fail(CFP_EINVAL, "g_ibi_host is NULL");
+    // page-locked host buffers are read and written by the kernels in place
+    // (over the host link, once each: f by the source term, g at the box and
+    // the initial guess at the start, u written by the last kernel), with no
+    // staging copy; other host memory goes through the context's device buffers
+    auto mapped = [](const void* p) -> void* {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+    };
+    {
+        const double* df = static_cast<const double*>(mapped(f));
+        const double* dg = static_cast<const double*>(mapped(g));
+        double* du = static_cast<double*>(mapped(u));
+        const double* dgi = c->n_ibi ? static_cast<const double*>(mapped(gi)) : nullptr;
+        if (df && dg && du && (dgi || !c->n_ibi)) {
+            const cfp_status st = solve_impl(c, df, dg, dgi, du, tol, opts, info);
+            const std::string msg = g_last_error;
+            CFP_CUDA(cudaStreamSynchronize(c->stream));
+            if (st != CFP_OK) g_last_error = msg;
+            return st;
+        }
+    }
     const size_t bytes = sizeof(double) * (size_t)c->N;
     if (!c->hs_f) CFP_CUDA(cudaMalloc(&c->hs_f, bytes));
     if (!c->hs_g) CFP_CUDA(cudaMalloc(&c->hs_g, bytes));

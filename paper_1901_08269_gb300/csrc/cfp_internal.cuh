@@ -374,6 +374,8 @@ void launch_metrics(cfp_ctx* c);  // Eq. app_xxx and Eq. 2ndorder_coef per axis
 cfp_status ensure_work(cfp_ctx* c, bool need32);
 cfp_status time_kernel(cfp_ctx* c, int kernel, int prec, int reps, double* ms, double* bytes);
 cfp_status tune_apply(cfp_ctx* c, int prec, int kind, int rows, int planes, int reps, double* best_ms);
+// the right-hand side of Eq. Bu=q without the argument checks of cfp_assemble_rhs
+cfp_status assemble_rhs(cfp_ctx* c, const double* f, const double* g, const double* gi, double* rhs);
 // sets up the FP32 apply ring (shared-memory limit, persistent grid); false if unusable
 bool setup_apply_ring(cfp_ctx* c);
 // the kernel and tile shape the apply of precision q (0 FP64, 1 FP32) runs with

@@ -604,7 +604,7 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
     double* tmp = c->v64 + V_TMP * vstride(c);
     double* X = c->v64 + V_X * vstride(c);
     const auto t1 = clk::now();
-    cfp_status st = cfp_assemble_rhs(c, f, g, gi, rhs);
+    cfp_status st = assemble_rhs(c, f, g, gi, rhs);
     if (st) return st;
     launch_mask_unknowns(c, u, X, c->stream);
     double b2 = 0.0, x2 = 0.0;

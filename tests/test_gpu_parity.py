@@ -343,3 +343,25 @@ def test_multigrid_preconditioner_is_linear_and_approximates_K_inverse(name):
     p.ctx.precondition(dev(a), phi, 8)
     res_gs = np.linalg.norm((a - K @ phi.cpu().numpy())[p.unk]) / np.linalg.norm(a[p.unk])
     assert res_mg < 0.5 and res_mg < res_gs, (res_mg, res_gs)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_solve_with_host_buffers_equals_the_device_solve(pinned):
+    """cfp_solve_host on page-locked buffers (used in place by the kernels)
+    and on pageable ones (copied through the context's device buffers) gives
+    bitwise the solution of cfp_solve on device buffers, and leaves the
+    caller's inputs unchanged."""
+    p = pair("c3-bodies-65")
+    f, g = p.w.fields()
+    gi = p.w.g_at(p.oxyz)
+    u_dev = torch.zeros(p.w.N, dtype=torch.float64, device="cuda")
+    ref = p.ctx.solve(dev(f), dev(g), dev(gi), u_dev, tol=1e-12, precision=cfp.PREC_MIXED, precond=cfp.PRECOND_MG)
+    hf, hg, hgi = (torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64) for a in (f, g, gi))
+    hu = torch.zeros(p.w.N, dtype=torch.float64)
+    if pinned:
+        hf, hg, hgi, hu = (t.pin_memory() for t in (hf, hg, hgi, hu))
+    f0 = hf.clone()
+    info = p.ctx.solve_host(hf, hg, hgi, hu, tol=1e-12, precision=cfp.PREC_MIXED, precond=cfp.PRECOND_MG)
+    assert info.status == 0 and info.iterations == ref.iterations
+    assert torch.equal(hu, u_dev.cpu())
+    assert torch.equal(hf, f0)
