@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <vector>
 
+#include <cooperative_groups.h>
 #include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
 
 #include "cfp_internal.cuh"
@@ -248,12 +249,21 @@ __global__ void __launch_bounds__(kSplitThreads)
 // for a few thousand nodes.  The node update is k_sweep_split's (MODE 1 for
 // a first red half-sweep from zero, MODE 0 otherwise) with the same rb_sum
 // and reciprocal: the results are bitwise equal.
+// CLUSTER: the same with the CTAs of one thread-block cluster (up to 16,
+// one per SM) and a cluster barrier, whose release / acquire order the
+// global writes of one half-sweep before the reads of the next, for levels
+// of up to kClusterMaxNodes nodes (33^3; at 65^3, eight nodes per thread
+// and half-sweep, separate launches on the whole GPU measured faster).
 constexpr int kCoarseThreads = 512;
 constexpr int64_t kCoarseMaxNodes = int64_t(1) << 15;
+constexpr int kClusterThreads = 1024;
+constexpr int64_t kClusterMaxNodes = int64_t(1) << 16;
 
-template <class T>
-__global__ void __launch_bounds__(kCoarseThreads) k_smooth_cta(SLev<T> L, int sweeps, int first_red_zero) {
+template <class T, bool CLUSTER>
+__global__ void __launch_bounds__(CLUSTER ? kClusterThreads : kCoarseThreads)
+    k_smooth_cta(SLev<T> L, int sweeps, int first_red_zero) {
     const int nx = L.nx, ny = L.ny, nz = L.nz, hp = L.hp;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
     const unsigned hs = L.hs;
     const int mp = (nx - 2) / 2 + 1;  // pairs m with 2 m <= nx - 2
     const int64_t items = (int64_t)mp * (ny - 2) * (nz - 2);
@@ -263,11 +273,11 @@ __global__ void __launch_bounds__(kCoarseThreads) k_smooth_cta(SLev<T> L, int sw
         // plain pointers: the e arrays are written by this launch's earlier
         // half-sweeps, so their loads must not take the non-coherent
         // read-only path that a const __restrict__ pointer allows
-        T* eown = L.e[colour];
-        const T* eoth = L.e[1 - colour];
-        const T* bown = L.b[colour];
-        const uint8_t* ty = L.ty[colour];
-        for (int64_t it = threadIdx.x; it < items; it += blockDim.x) {
+        T* eown = colour ? L.e[1] : L.e[0];
+        const T* eoth = colour ? L.e[0] : L.e[1];
+        const T* bown = colour ? L.b[1] : L.b[0];
+        const uint8_t* ty = colour ? L.ty[1] : L.ty[0];
+        for (int64_t it = t0; it < items; it += nt) {
             const int m = (int)(it % mp);
             const int64_t rest = it / mp;
             const int j = 1 + (int)(rest % (ny - 2)), k = 1 + (int)(rest / (ny - 2));
@@ -291,7 +301,8 @@ __global__ void __launch_bounds__(kCoarseThreads) k_smooth_cta(SLev<T> L, int sw
             const T val = times_rcp(v, dg);
             if (i >= 1 && i <= nx - 2 && is_unknown(t)) eown[o] = val;
         }
-        __syncthreads();
+        if (CLUSTER) cooperative_groups::this_cluster().sync();
+        else __syncthreads();
     }
 }
 
@@ -1027,6 +1038,32 @@ void half_sweep(cfp_ctx* c, int l, const SLev<T>& L, const Side<T>& S, int colou
     }
 }
 
+// The cluster of k_smooth_cta<T, true>: 16 CTAs where the device schedules
+// such a cluster (a non-portable size), else 8, else 0 (not used); found once.
+template <class T>
+int smooth_cluster_size() {
+    static const int size = []() {
+        cudaFuncSetAttribute(k_smooth_cta<T, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        for (int cl : {16, 8}) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)cl);
+            cfg.blockDim = dim3(kClusterThreads);
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = (unsigned)cl;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, k_smooth_cta<T, true>, &cfg) == cudaSuccess && n >= 1) return cl;
+            cudaGetLastError();
+        }
+        return 0;
+    }();
+    return size;
+}
+
 // `sweeps` red-black sweeps at level l.  first_red / last_black: the modes of
 // the first red and the last black half-sweep.
 template <class T>
@@ -1037,7 +1074,26 @@ void smooth(cfp_ctx* c, int l, const Side<T>& S, int sweeps, int first_red, int 
     // one CTA does every half-sweep
     if (c->mg_tma && l > 0 && c->mg[l].N <= kCoarseMaxNodes && (first_red == 0 || first_red == 1) &&
         last_black == 0) {
-        k_smooth_cta<T><<<1, kCoarseThreads, 0, s>>>(L, sweeps, first_red);
+        k_smooth_cta<T, false><<<1, kCoarseThreads, 0, s>>>(L, sweeps, first_red);
+        c->launches += 1;
+        return;
+    }
+    // a mid-size coarse level: one thread-block cluster does every half-sweep
+    const int cl = smooth_cluster_size<T>();
+    if (cl > 0 && c->mg_tma && l > 0 && c->mg[l].N <= kClusterMaxNodes && (first_red == 0 || first_red == 1) &&
+        last_black == 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)cl);
+        cfg.blockDim = dim3(kClusterThreads);
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)cl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_smooth_cta<T, true>, L, sweeps, first_red);
         c->launches += 1;
         return;
     }
