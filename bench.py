@@ -306,7 +306,8 @@ def kernel_arm(args):
     ctx.classify_points()
     prec = cfp.PREC_MIXED if args.precision == "mixed" else cfp.PREC_FP64
     ids = {"rbgs": cfp.KERNEL_RBGS, "mg_sweep": cfp.KERNEL_MG_SWEEP, "apply": cfp.KERNEL_APPLY,
-           "update": cfp.KERNEL_UPDATE, "prolong": cfp.KERNEL_PROLONG, "restrict": cfp.KERNEL_RESTRICT}
+           "update": cfp.KERNEL_UPDATE, "prolong": cfp.KERNEL_PROLONG, "restrict": cfp.KERNEL_RESTRICT,
+           "mg_pair": cfp.KERNEL_MG_PAIR}
     out = {"mode": "kernels", "n": args.n, "precision": args.precision, "reps": args.reps}
     if args.apply_tile:
         k, r, q = (int(v) for v in args.apply_tile.split(","))

@@ -107,8 +107,13 @@ typedef struct {
                           sweeps of a smoothing in one single-CTA launch,
                           and the prolongation runs one thread per coarse
                           cell; 0: plain loads, one launch per half-sweep,
-                          one prolongation thread per fine pair.  Same
-                          arithmetic, bitwise equal results               */
+                          one prolongation thread per fine pair; 2: as 1,
+                          and on those levels the black half-sweep of each
+                          sweep and the red half-sweep of the next run as
+                          one fused pass (10 instead of 12 bytes per node
+                          in FP32; measured slower than the two passes at
+                          513^3, hence not the default).  Same arithmetic,
+                          bitwise equal results                           */
 } cfp_opts;
 
 typedef struct {
@@ -390,8 +395,15 @@ enum { CFP_KERNEL_APPLY = 0,    /* B x with the fused (r_hat0, v) dot, as in
                                    level's correction onto the fine level's
                                    black nodes (trilinear in the stretched
                                    coordinates)                              */
-       CFP_KERNEL_RESTRICT = 5  /* the full-weighting restriction of the fine
-                                   level's red residual to the second level */ };
+       CFP_KERNEL_RESTRICT = 5, /* the full-weighting restriction of the fine
+                                   level's red residual to the second level */
+       CFP_KERNEL_MG_PAIR = 6   /* the fused pass of a black half-sweep and
+                                   the next red one on the fine level (FP32
+                                   only, a fine level of >= 192 nodes per
+                                   row, mg_tma on), with the Shortley-Weller
+                                   rows of the irregular nodes; algorithmic
+                                   bytes 2.5 x 4 per interior node (old red,
+                                   both b, the new black and red values)    */ };
 
 /*
  * Profiling aid: time `reps` >= 1 back-to-back launches of one kernel of the

@@ -59,6 +59,7 @@ EXPORTS = ["cfp_default_opts", "cfp_last_error", "cfp_ctx_create", "cfp_ctx_dest
 NN_RELU, NN_MASK, NN_OUT_F32, NN_ACCUM, NN_DGRAD = 1, 2, 4, 8, 16
 NN_INJECT, NN_PROLONG_ADD, NN_PROLONG_T, NN_SKIP_GRAD = 0, 1, 2, 3
 KERNEL_APPLY, KERNEL_RBGS, KERNEL_UPDATE, KERNEL_MG_SWEEP, KERNEL_PROLONG, KERNEL_RESTRICT = 0, 1, 2, 3, 4, 5
+KERNEL_MG_PAIR = 6
 APPLY_STREAM, APPLY_RING = 1, 2
 
 

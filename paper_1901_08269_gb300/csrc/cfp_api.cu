@@ -336,6 +336,7 @@ cfp_status cfp_precondition_ex(cfp_ctx* c, const cfp_opts* o, const double* rho,
     c->mg_smooth = std::max(1, opts.mg_smooth);
     c->mg_post = opts.mg_post > 0 ? opts.mg_post : c->mg_smooth;
     c->mg_tma = opts.mg_tma != 0;
+    c->mg_fuse = opts.mg_tma == 2;
     cfp_status st = CFP_OK;
     if (c->precond_kind == CFP_PRECOND_MG || (c->precond_kind == CFP_PRECOND_RBGS && opts.sweeps > 0))
         st = ensure_mg(c, prec);

@@ -427,6 +427,7 @@ extern "C" cfp_status cfp_solve_fgmres(cfp_ctx* c, cfp_unet* net, const double* 
     c->mg_smooth = std::max(1, opts.mg_smooth);
     c->mg_post = opts.mg_post > 0 ? opts.mg_post : c->mg_smooth;
     c->mg_tma = opts.mg_tma != 0;
+    c->mg_fuse = opts.mg_tma == 2;
     const bool mixed = opts.precision == CFP_PREC_MIXED;
     if (c->precond_kind == CFP_PRECOND_MG || opts.sweeps > 0) CFP_TRY(ensure_mg(c, mixed ? 1 : 0));
     CFP_TRY(ensure_work(c, mixed));

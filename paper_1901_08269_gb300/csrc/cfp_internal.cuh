@@ -173,9 +173,23 @@ struct MgLevel {
     int tma = 0;
     int tma_grid[3] = {0, 0, 0};
     CUtensorMap tm32[5];
+    // The fused black-then-red pass (FP32, TMA levels) writes the red iterate
+    // into a second red array (entry 5 Nh of s32); red_cur (host, set while
+    // launches are issued) names the array that holds the current red values:
+    // 0 the split array, 1 the second one.  tmalt: the maps of tm32[2] and
+    // tm32[4] on the second array; tmp: the fused pass's maps (red e of each
+    // array, black b, red b, with the fused pass's boxes).
+    int red_cur = 0;
+    int pair = 0;
+    int pair_grid = 0;
+    CUtensorMap tmalt[2];
+    CUtensorMap tmp[4];
     // level 0: the irregular nodes of each colour (natural index, split
-    // offset, slot, parity), colour c at fix + c * n_irr, nfix[c] of them
+    // offset, slot, parity) in ascending natural index, colour c at fix +
+    // c * n_irr, nfix[c] of them; fixrows + c * (n[1] n[2] + 1): per row
+    // (k n[1] + j) the first entry of that row in colour c's list
     void* fix = nullptr;
+    int32_t* fixrows = nullptr;
     int64_t nfix[2] = {0, 0};
 };
 
@@ -273,6 +287,7 @@ struct cfp_ctx {
     int mg_smooth = 2;
     int mg_post = 2;
     int mg_tma = 1;            // 1: TMA-fed FP32 half-sweeps where a level supports them
+    int mg_fuse = 0;           // 1: and the fused black-then-red passes (opts.mg_tma == 2)
     int* dwait = nullptr;      // device word: nonzero once a bounded pipeline wait timed out
     int ring_grid = 0;         // CTAs of the apply ring's persistent grid (0: not set up)
     std::vector<cfp::MgLevel> mg;
@@ -360,6 +375,9 @@ void launch_mg_half_sweep(cfp_ctx* c, cudaStream_t s);
 // the V-cycle's restriction / prolongation between levels 0 and 1 (false: one level only)
 template <class T>
 bool launch_mg_transfer(cfp_ctx* c, bool prolong, cudaStream_t s);
+// the fused black-then-red pass on the fine level; false where it does not apply
+template <class T>
+bool launch_mg_pair(cfp_ctx* c, cudaStream_t s);
 void launch_qf(cfp_ctx* c, const double* f, double* out, cudaStream_t s);
 void launch_rhs_finish(cfp_ctx* c, const double* qf, const double* bg, const double* g_ibi,
                        double* rhs, cudaStream_t s);

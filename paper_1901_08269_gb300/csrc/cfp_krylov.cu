@@ -453,6 +453,8 @@ cfp_status time_kernel_t(cfp_ctx* c, int prec, int kernel, int reps, double* ms,
         else if (kernel == CFP_KERNEL_RBGS || kernel == CFP_KERNEL_MG_SWEEP) launch_mg_half_sweep<T>(c, c->stream);
         else if (kernel == CFP_KERNEL_PROLONG || kernel == CFP_KERNEL_RESTRICT)
             launch_mg_transfer<T>(c, kernel == CFP_KERNEL_PROLONG, c->stream);
+        else if (kernel == CFP_KERNEL_MG_PAIR)
+            launch_mg_pair<T>(c, c->stream);
         else
             k_update_xr<T><<<kUpdBlocks, kUpdThreads, 0, c->stream>>>(V.x, V.r, V.ph, V.sh, V.s, V.t, V.rh, st,
                                                                       c->partial, c->N);
@@ -477,6 +479,7 @@ cfp_status time_kernel_t(cfp_ctx* c, int prec, int kernel, int reps, double* ms,
                : kernel == CFP_KERNEL_RBGS || kernel == CFP_KERNEL_MG_SWEEP ? 1.5 * w * nint
                : kernel == CFP_KERNEL_PROLONG ? (0.5 * (1.0 + 2.0 * w) + w / 8.0) * nint
                : kernel == CFP_KERNEL_RESTRICT ? (0.5 * w + (1.0 + w) / 8.0) * nint
+               : kernel == CFP_KERNEL_MG_PAIR ? 2.5 * w * nint
                                                : 8.0 * w * (double)c->N;
     return CFP_OK;
 }
@@ -531,18 +534,26 @@ cfp_status tune_apply(cfp_ctx* c, int prec, int kind, int rows, int planes, int 
 }
 
 cfp_status time_kernel(cfp_ctx* c, int kernel, int prec, int reps, double* ms, double* bytes) {
-    if (kernel < CFP_KERNEL_APPLY || kernel > CFP_KERNEL_RESTRICT || reps < 1 || !ms)
+    if (kernel < CFP_KERNEL_APPLY || kernel > CFP_KERNEL_MG_PAIR || reps < 1 || !ms)
         return fail(CFP_EINVAL, "bad kernel id, reps or output pointer");
     CFP_TRY(ensure_work(c, prec == CFP_PREC_MIXED));
     if (kernel != CFP_KERNEL_APPLY && kernel != CFP_KERNEL_UPDATE) CFP_TRY(ensure_mg(c, prec == CFP_PREC_MIXED ? 1 : 0));
     if ((kernel == CFP_KERNEL_PROLONG || kernel == CFP_KERNEL_RESTRICT) && c->mg.size() < 2)
         return fail(CFP_EINVAL, "the grid has a single multigrid level: no transfer to time");
+    if (kernel == CFP_KERNEL_MG_PAIR) {
+        if (prec != CFP_PREC_MIXED) return fail(CFP_EINVAL, "the fused pass is FP32 only");
+        CFP_TRY(ensure_mg(c, 1));
+        if (!c->mg[0].tma || !c->mg[0].pair)
+            return fail(CFP_EINVAL, "the fine level has no fused pass (fewer than 192 nodes per row)");
+    }
     CFP_TRY(prec == CFP_PREC_MIXED ? time_kernel_t<float>(c, 1, kernel, reps, ms, bytes)
                                    : time_kernel_t<double>(c, 0, kernel, reps, ms, bytes));
     return check_waits(c);
 }
 
-int mg_key(const cfp_ctx* c) { return c->mg_smooth * 1000 + c->mg_post + (c->mg_tma ? 1000000 : 0); }
+int mg_key(const cfp_ctx* c) {
+    return c->mg_smooth * 1000 + c->mg_post + (c->mg_tma ? 1000000 : 0) + (c->mg_fuse ? 2000000 : 0);
+}
 
 cfp_status check_waits(cfp_ctx* c) {
     int w = 0;
@@ -593,6 +604,7 @@ cfp_status cfp::solve_impl(cfp_ctx* c, const double* f, const double* g, const d
     c->mg_smooth = std::max(1, opts.mg_smooth);
     c->mg_post = opts.mg_post > 0 ? opts.mg_post : c->mg_smooth;
     c->mg_tma = opts.mg_tma != 0;
+    c->mg_fuse = opts.mg_tma == 2;
     const bool mixed = opts.precision == CFP_PREC_MIXED;
     // the multigrid option and the red-black sweeps (on the fine level's split arrays)
     if (c->precond_kind == CFP_PRECOND_MG || (c->precond_kind == CFP_PRECOND_RBGS && opts.sweeps > 0))
@@ -990,6 +1002,7 @@ cfp_status prepare_device_solve(cfp_ctx* c, const cfp_opts& opts) {
     c->mg_smooth = std::max(1, opts.mg_smooth);
     c->mg_post = opts.mg_post > 0 ? opts.mg_post : c->mg_smooth;
     c->mg_tma = opts.mg_tma != 0;
+    c->mg_fuse = opts.mg_tma == 2;
     if (c->precond_kind == CFP_PRECOND_MG || (c->precond_kind == CFP_PRECOND_RBGS && opts.sweeps > 0))
         CFP_TRY(ensure_mg(c, 1));
     if (c->precond_kind == CFP_PRECOND_ILU) CFP_TRY(ensure_ilu(c, 1));

@@ -192,11 +192,16 @@ WIDE = {
 }
 
 
+@pytest.mark.parametrize("nu,post", [(2, 2), (4, 3)])
 @pytest.mark.parametrize("name", list(WIDE))
-def test_fp32_vcycle_tma_smoother(name):
+def test_fp32_vcycle_tma_smoother(name, nu, post):
     """The FP32 V-cycle (the mixed solve's inner preconditioner) with the
-    TMA-fed half-sweeps: bitwise equal to the plain-load half-sweeps (same
-    arithmetic), and the numpy V-cycle in FP64 to FP32 accuracy."""
+    TMA-fed half-sweeps (mg_tma 1), and with the fused black-then-red passes
+    as well (mg_tma 2: nu - 1 before the coarse correction, post - 1 after
+    it, on every level of >= 192 nodes per row, the fine level's
+    Shortley-Weller rows inside the pass): bitwise equal to the plain-load
+    half-sweeps (same arithmetic), and the numpy V-cycle in FP64 to FP32
+    accuracy."""
     w = WIDE[name]()
     P = O.Problem(w.x, w.y, w.z, w.bodies, w.fluid_inside)
     otype = P.classify()
@@ -205,24 +210,71 @@ def test_fp32_vcycle_tma_smoother(name):
     levels = build_levels(w.x, w.y, w.z, otype, P.export(O.MAT_K))
     rng = np.random.default_rng(5)
     rho = np.where(levels[0]["unk"], rng.standard_normal(w.N), 0.0)
-    want = vcycle(levels, rho, 2, post=2)
+    want = vcycle(levels, rho, nu, post=post)
     ctx = cfp.Context(w.x, w.y, w.z, w.bodies, w.fluid_inside)
     ctx.classify_points()
     rho_t = torch.as_tensor(rho, device="cuda")
     got = {}
-    for tma in (1, 0, 1):
+    for tma in (1, 0, 2, 1, 2):
         phi = torch.full((w.N,), 7.0, dtype=torch.float64, device="cuda")
-        ctx.precondition_ex(rho_t, phi, precond=cfp.PRECOND_MG, mg_smooth=2, mg_post=2,
+        ctx.precondition_ex(rho_t, phi, precond=cfp.PRECOND_MG, mg_smooth=nu, mg_post=post,
                             precision=cfp.PREC_MIXED, mg_tma=tma)
         if tma in got:
             assert torch.equal(phi, got[tma])  # repeatable
         got[tma] = phi
     assert torch.equal(got[1], got[0])
+    assert torch.equal(got[2], got[0])
     g = got[1].cpu().numpy()
     u = levels[0]["unk"]
     assert np.all(g[~u] == 0.0)
     err = np.max(np.abs(g[u] - want[u])) / np.max(np.abs(want[u]))
     assert err <= 1e-5, err
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", list(WIDE))
+def test_fp32_rbgs_fused_passes(name):
+    """The red-black preconditioner in FP32 with the fused passes (mg_tma 2;
+    8 sweeps on the fine level: the first red half-sweep, seven fused
+    black-then-red passes, the last black half-sweep) bitwise equal to the
+    same sweeps as one launch per half-sweep, TMA-fed or plain, and within
+    FP32 rounding of the FP64 sweeps."""
+    w = WIDE[name]()
+    ctx = cfp.Context(w.x, w.y, w.z, w.bodies, w.fluid_inside)
+    types = torch.empty(w.N, dtype=torch.uint8, device="cuda")
+    ctx.classify_points(types)
+    unk = (types == cfp.REGULAR) | (types == cfp.IRREGULAR)
+    rng = np.random.default_rng(9)
+    rho_t = torch.as_tensor(rng.standard_normal(w.N), device="cuda") * unk
+    got = {}
+    for tma in (2, 0, 1):
+        phi = torch.full((w.N,), 7.0, dtype=torch.float64, device="cuda")
+        ctx.precondition_ex(rho_t, phi, precond=cfp.PRECOND_RBGS, sweeps=8, precision=cfp.PREC_MIXED, mg_tma=tma)
+        got[tma] = phi
+    assert torch.equal(got[2], got[0]) and torch.equal(got[1], got[0])
+    ref = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+    ctx.precondition_ex(rho_t, ref, precond=cfp.PRECOND_RBGS, sweeps=8, precision=cfp.PREC_FP64)
+    err = (got[1] - ref).abs().max().item() / ref.abs().max().item()
+    assert err <= 1e-5, err
+    ctx.close()
+
+
+def test_mixed_solve_with_fused_passes_is_bitwise_the_default():
+    """The whole mixed solve (graph-captured V-cycles, refinement) with the
+    fused black-then-red passes gives the default solve's bits."""
+    w = WIDE["wide-300"]()
+    ctx = cfp.Context(w.x, w.y, w.z, w.bodies, w.fluid_inside)
+    ctx.classify_points()
+    f, g = w.fields(torch, "cuda")
+    gi = w.g_at(ctx.ibi_points(), torch)
+    out = {}
+    for tma in (1, 2):
+        u = torch.zeros(w.N, dtype=torch.float64, device="cuda")
+        info = ctx.solve(f, g, gi, u, tol=1e-12, precision=cfp.PREC_MIXED, precond=cfp.PRECOND_MG,
+                         mg_smooth=4, mg_post=3, mg_tma=tma)
+        assert info.status == 0 and info.rel_residual <= 1e-12
+        out[tma] = (u, info.iterations, info.refinements)
+    assert torch.equal(out[1][0], out[2][0]) and out[1][1:] == out[2][1:]
     ctx.close()
 
 
@@ -239,8 +291,19 @@ def test_kernel_timer_covers_every_kernel():
             ms, by = ctx.time_kernel(kid, prec, reps=2)
             assert ms > 0.0 and by == per
     with pytest.raises(cfp.CfpError):
-        ctx.time_kernel(6, cfp.PREC_FP64, reps=1)
+        ctx.time_kernel(7, cfp.PREC_FP64, reps=1)
+    # the fused pass needs a fine level of >= 192 nodes per row, in FP32
+    for prec in (cfp.PREC_MIXED, cfp.PREC_FP64):
+        with pytest.raises(cfp.CfpError) as e:
+            ctx.time_kernel(cfp.KERNEL_MG_PAIR, prec, reps=1)
+        assert e.value.status == cfp.EINVAL
     ctx.close()
+    wide = WIDE["wide-257"]()
+    wc = cfp.Context(wide.x, wide.y, wide.z, wide.bodies, wide.fluid_inside)
+    wc.classify_points()
+    ms, by = wc.time_kernel(cfp.KERNEL_MG_PAIR, cfp.PREC_MIXED, reps=2)
+    assert ms > 0.0 and by == 2.5 * 4 * (len(wide.x) - 2) * (len(wide.y) - 2) * (len(wide.z) - 2)
+    wc.close()
     # a grid with a single multigrid level has no transfer to time
     x = W.uniform_grid(0, 1, 9)
     small = cfp.Context(x, x, x, [])
