@@ -330,20 +330,23 @@ __device__ __forceinline__ float2 f2b(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 
 // DotAcc<float> on both halves at once: a running sum and its lost
-// low-order part per column
+// low-order part per column, the latter kept negated (cn = -c), so that no
+// step needs a negation: v = x y - c = fma(x, y, cn); t = s + v; the new
+// c = (t - s) - v, that is cn = (s - t) + v, with s - t formed exactly as
+// fma(t, -1, s).  Round-to-nearest is symmetric, so every value is the
+// negation of the plain form's, bit for bit.
 struct DotAcc2 {
-    float2 s = {0.f, 0.f}, c = {0.f, 0.f};
+    float2 s = {0.f, 0.f}, cn = {0.f, 0.f};
     __device__ __forceinline__ void add(float2 x, float2 y) {
-        const float2 v = fma2(x, y, make_float2(-c.x, -c.y));
+        const float2 v = fma2(x, y, cn);
         const float2 t = add2(s, v);
-        c = sub2(sub2(t, s), v);
+        cn = add2(fma2(t, make_float2(-1.f, -1.f), s), v);
         s = t;
     }
     __device__ __forceinline__ double total() const {
-        return ((double)s.x - (double)c.x) + ((double)s.y - (double)c.y);
+        return ((double)s.x + (double)cn.x) + ((double)s.y + (double)cn.y);
     }
 };
 
