@@ -487,137 +487,231 @@ __device__ bool moment_solve(int M, const double* xi, double xe, int ns, const d
     }
 }
 
-struct RowCtx {
-    int idx[3];
-    int64_t lin;
-    int64_t st[3];
-    RawAcc* corr;
-    BibAcc* bib;
-    int ndeg;
-    int err;
+// The modified operators of one line: the line's solid pattern `mask`
+// (bit 2: node -1, bit 1: node 0, bit 0: node +1 solid) fixes each
+// operator's expansion offset e, walk direction sg, walk length G (5 grid
+// nodes for the six-point operators of Eqs. mod1-mod4, 4 for the five-point
+// ones of Eqs. mod2_case2 / mod2_case22) and the surviving R nodes with their
+// L weights (a, 1, c of the line's centre).
+struct OpSpec {
+    int e, sg, G, ns;
+    int surv[2];
+    double Ls[2];
 };
+__device__ __forceinline__ int line_nops(int mask) { return mask == 2 ? 2 : 1; }
+__device__ __forceinline__ OpSpec op_spec(int mask, int k, double a, double c) {
+    switch (mask) {
+        case 1: return OpSpec{0, -1, 5, 2, {-1, 0}, {a, 1.0}};    // +1 solid (Eqs. mod1_top, mod1, mat1)
+        case 4: return OpSpec{0, +1, 5, 2, {0, 1}, {1.0, c}};     // -1 solid (Eqs. mod3_top, mod3, mat3)
+        case 3: return OpSpec{-1, -1, 5, 1, {-1, 0}, {a, 0.0}};   // 0 and +1 solid (Eqs. mod2_top, mod2, mat2)
+        case 6: return OpSpec{1, +1, 5, 1, {1, 0}, {c, 0.0}};     // -1 and 0 solid (Eqs. mod4_top, mod4, mat4)
+        case 2:                                                   // middle solid: Eqs. mod2_case2, mod2_case22
+            return k == 0 ? OpSpec{-1, -1, 4, 1, {-1, 0}, {a, 0.0}} : OpSpec{1, +1, 4, 1, {1, 0}, {c, 0.0}};
+        default: return OpSpec{0, -1, 5, 1, {0, 0}, {1.0, 0.0}};  // 5: fluid node between two solid nodes
+    }
+}
 
-// One modified operator along axis d of the line with centre index vector
-// base (base[d] = the irregular point's index along d).  The expansion node
-// is at offset e; the operator is bounded on side -sg by a solid node whose
-// IBI it uses and walks e, e+sg, ... over up to G grid nodes (5 for the
-// six-point operators of Eqs. mod1-mod4, 4 for the five-point operators of
-// Eqs. mod2_case2 / mod2_case22).  If the walk meets a solid node first,
-// that edge's IBI closes the set; if it leaves the grid, the set ends at the
-// box (fewer points, counted as degenerate).
-__device__ void modified_op(const SideArgs& S, RowCtx& R, const int base[3], int d, double w, int e,
-                            int sg, int G, int ns, const int* surv, const double* Ls) {
-    if (R.err) return;
-    const int nd = S.a.n[d];
-    double xi[7], xs[3], cc[7];
+// One of the 27 lines of an irregular point's row (Eq. lhsrhs_xxyyzz_mod),
+// L = 9 d + 3 (o1 + 1) + (o2 + 1): axis d, offsets o1, o2 along the two
+// other axes; its weight w (the L coefficients across), its centre index
+// vector `base`, the line centre's a and c, and its solid pattern.
+struct Line {
+    int d, m, mask;
+    int base[3];
+    int64_t bl;
+    double w, a, c;
+};
+__device__ __forceinline__ void line_at(const SideArgs& S, const int idx[3], const int64_t st[3], int L, Line& ln) {
+    const int d = L / 9, o1 = (L / 3) % 3 - 1, o2 = L % 3 - 1;
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    ln.d = d;
+    ln.m = idx[d];
+    ln.a = S.ax[d].a[ln.m];
+    ln.c = S.ax[d].c[ln.m];
+    ln.w = Lc(S.ax[t1], idx[t1], o1) * Lc(S.ax[t2], idx[t2], o2);
+    ln.base[0] = idx[0];
+    ln.base[1] = idx[1];
+    ln.base[2] = idx[2];
+    ln.base[t1] += o1;
+    ln.base[t2] += o2;
+    ln.bl = lin3(ln.base[0], ln.base[1], ln.base[2], S.a.n[0], S.a.n[1]);
+    int mask = 0;
+    for (int s = -1; s <= 1; ++s) mask = (mask << 1) | (S.a.type[ln.bl + s * st[d]] == CFP_SOLID);
+    ln.mask = mask;
+}
+
+// The walk of one modified operator: from the expansion node e along sg over
+// up to G grid nodes; a solid node met first closes the set with its edge's
+// IBI; leaving the grid ends it at the box (fewer points, degenerate).  Its
+// grid nodes (coordinates, offsets from the row's point) and IBIs, or an
+// error detail.
+struct OpWalk {
+    int ng, nib, err;
+    bool deg;
+    double xi[7];
     int offs[6];
     int ib[2];
-    int ng = 0, nib = 0;
-    int f[3] = {base[0], base[1], base[2]};
-    f[d] += e;
+};
+__device__ void op_walk(const SideArgs& S, const Line& ln, const OpSpec& o, int64_t lin, const int64_t st[3],
+                        OpWalk& W) {
+    const int d = ln.d, nd = S.a.n[d];
+    W.ng = 0;
+    W.nib = 0;
+    W.err = 0;
+    W.deg = false;
+    int f[3] = {ln.base[0], ln.base[1], ln.base[2]};
+    f[d] += o.e;
     const int64_t fl = lin3(f[0], f[1], f[2], S.a.n[0], S.a.n[1]);
     const uint8_t ft = S.a.type[fl];
-    if (ft != CFP_REGULAR && ft != CFP_IRREGULAR) { R.err = DETAIL_BOXIBI; return; }
-    ib[nib] = ibi_index(S, fl, 2 * d + (sg > 0 ? 0 : 1));
-    if (ib[nib] < 0) { R.err = DETAIL_MISSINGIBI; return; }
-    ++nib;
-    for (int q = 0; q < G; ++q) {
+    if (ft != CFP_REGULAR && ft != CFP_IRREGULAR) { W.err = DETAIL_BOXIBI; return; }
+    W.ib[0] = ibi_index(S, fl, 2 * d + (o.sg > 0 ? 0 : 1));
+    if (W.ib[0] < 0) { W.err = DETAIL_MISSINGIBI; return; }
+    W.nib = 1;
+    for (int q = 0; q < o.G; ++q) {
         int p[3] = {f[0], f[1], f[2]};
-        p[d] += q * sg;
+        p[d] += q * o.sg;
         if (p[d] < 0 || p[d] >= nd) break;
         const int64_t l = lin3(p[0], p[1], p[2], S.a.n[0], S.a.n[1]);
         if (S.a.type[l] == CFP_SOLID) {
-            const int64_t pl = l - sg * R.st[d];
+            const int64_t pl = l - o.sg * st[d];
             const uint8_t pt = S.a.type[pl];
-            if (pt != CFP_REGULAR && pt != CFP_IRREGULAR) { R.err = DETAIL_BOXIBI; return; }
-            ib[nib] = ibi_index(S, pl, 2 * d + (sg > 0 ? 1 : 0));
-            if (ib[nib] < 0) { R.err = DETAIL_MISSINGIBI; return; }
-            ++nib;
+            if (pt != CFP_REGULAR && pt != CFP_IRREGULAR) { W.err = DETAIL_BOXIBI; return; }
+            W.ib[W.nib] = ibi_index(S, pl, 2 * d + (o.sg > 0 ? 1 : 0));
+            if (W.ib[W.nib] < 0) { W.err = DETAIL_MISSINGIBI; return; }
+            ++W.nib;
             break;
         }
-        xi[ng] = S.X[d][p[d]];
-        offs[ng] = (int)(l - R.lin);
-        ++ng;
+        W.xi[W.ng] = S.X[d][p[d]];
+        W.offs[W.ng] = (int)(l - lin);
+        ++W.ng;
     }
-    const int M = ng + nib;
-    if (M < 3) { R.err = DETAIL_FEWPOINTS; return; }
-    if (ng < G || nib > 1) R.ndeg++;
-    for (int q = 0; q < nib; ++q) xi[ng + q] = S.ibi_xyz[3 * (int64_t)ib[q] + d];
-    const double xe = S.X[d][f[d]];
-    for (int s = 0; s < ns; ++s) xs[s] = S.X[d][base[d] + surv[s]];
-    double hs = 0.0;
-    for (int q = 1; q < M; ++q) hs = fmax(hs, fabs(xi[q] - xe));
-    if (!moment_solve(M, xi, xe, ns, xs, Ls, hs, cc)) { R.err = DETAIL_SINGULAR; return; }
-    for (int q = 0; q < ng; ++q)
-        if (!R.corr->add(offs[q], w * cc[q])) { R.err = DETAIL_OVERFLOW; return; }
-    for (int q = 0; q < nib; ++q)
-        if (!R.bib->add(ib[q], w * cc[ng + q])) { R.err = DETAIL_OVERFLOW; return; }
+    if (W.ng + W.nib < 3) { W.err = DETAIL_FEWPOINTS; return; }
+    W.deg = W.ng < o.G || W.nib > 1;
 }
 
-// Corrections that turn the regular 27-point row at an irregular point into
-// its modified row: for each of the 27 lines (Eq. lhsrhs_xxyyzz_mod) with a
-// solid node, minus the regular R operator at its fluid nodes, plus the
-// modified operator(s); IBI weights go to bib (script B of Eq. bc).
-__device__ void build_row(const SideArgs& S, RowCtx& R) {
-    for (int d = 0; d < 3; ++d) {
-        const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-        const int m = R.idx[d];
-        const Axis<double>& A = S.ax[d];
-        const double a = A.a[m], c = A.c[m];
-        for (int o1 = -1; o1 <= 1; ++o1)
-            for (int o2 = -1; o2 <= 1; ++o2) {
-                const double w = Lc(S.ax[t1], R.idx[t1], o1) * Lc(S.ax[t2], R.idx[t2], o2);
-                int base[3] = {R.idx[0], R.idx[1], R.idx[2]};
-                base[t1] += o1;
-                base[t2] += o2;
-                const int64_t bl = lin3(base[0], base[1], base[2], S.a.n[0], S.a.n[1]);
-                int sol[3];
-                for (int s = -1; s <= 1; ++s) sol[s + 1] = S.a.type[bl + s * R.st[d]] == CFP_SOLID;
-                const int mask = (sol[0] << 2) | (sol[1] << 1) | sol[2];
-                if (mask == 0 || mask == 7) continue;  // regular or dropped line
-                for (int s = -1; s <= 1; ++s)
-                    if (!sol[s + 1])
-                        if (!R.corr->add((int)(bl + s * R.st[d] - R.lin), -w * Rc(A, m, s))) {
-                            R.err = DETAIL_OVERFLOW;
-                            return;
-                        }
-                switch (mask) {
-                case 1: {  // +1 solid (Eqs. mod1_top, mod1, mat1)
-                    const int sv[2] = {-1, 0};
-                    const double Ls[2] = {a, 1.0};
-                    modified_op(S, R, base, d, w, 0, -1, 5, 2, sv, Ls);
-                } break;
-                case 4: {  // -1 solid (Eqs. mod3_top, mod3, mat3)
-                    const int sv[2] = {0, 1};
-                    const double Ls[2] = {1.0, c};
-                    modified_op(S, R, base, d, w, 0, +1, 5, 2, sv, Ls);
-                } break;
-                case 3: {  // 0 and +1 solid (Eqs. mod2_top, mod2, mat2)
-                    const int sv[1] = {-1};
-                    const double Ls[1] = {a};
-                    modified_op(S, R, base, d, w, -1, -1, 5, 1, sv, Ls);
-                } break;
-                case 6: {  // -1 and 0 solid (Eqs. mod4_top, mod4, mat4)
-                    const int sv[1] = {1};
-                    const double Ls[1] = {c};
-                    modified_op(S, R, base, d, w, 1, +1, 5, 1, sv, Ls);
-                } break;
-                case 2: {  // middle solid: Eqs. mod2_case2 and mod2_case22
-                    const int svm[1] = {-1};
-                    const double Lsm[1] = {a};
-                    modified_op(S, R, base, d, w, -1, -1, 4, 1, svm, Lsm);
-                    const int svp[1] = {1};
-                    const double Lsp[1] = {c};
-                    modified_op(S, R, base, d, w, 1, +1, 4, 1, svp, Lsp);
-                } break;
-                default: {  // 5: fluid node between two solid nodes
-                    const int sv[1] = {0};
-                    const double Ls[1] = {1.0};
-                    modified_op(S, R, base, d, w, 0, -1, 5, 1, sv, Ls);
-                } break;
+// An operator whose moments are still to be matched: the slot of its
+// point, its line and operator index (code = 2 L + k), and where its
+// correction adds and IBI weights go in the point's scratch slices.
+struct SideTask {
+    int slot, code, cpos, bpos;
+};
+
+// The first error of a row in the order of its lines, operators and steps:
+// key (2 L + k) x 4 + step (0: the R subtraction overflows the slice; 1:
+// the walk fails; 2: the moment matrix is singular; 3: the operator's adds
+// overflow), times 16, plus the error detail.  The sequential order in which
+// a row is built decides which error is reported.
+__device__ __forceinline__ int side_err(int L, int k, int step, int detail) {
+    return (((2 * L + k) * 4 + step) << 4) | detail;
+}
+constexpr int kSideNoErr = 0x7fffffff;
+
+// Plans the row of every irregular point (one thread per point), walking its
+// 27 lines in order up to its first error: the R subtraction of every line
+// with a solid node (Eq. cor: minus the regular R operator at the line's
+// fluid nodes) and the walk of its modified operator(s).  COUNT: only the
+// number of operators; otherwise the R subtraction's adds are stored, each
+// operator becomes a task at its place (task_off[s] onwards) with the
+// positions of its adds, and the row's counts, first error and degenerate
+// operators are kept for k_side_finish.
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_side_plan(SideArgs S, int* ntask, const int* task_off, SideTask* tasks,
+                                                   int* ccount, int* bcount, int* ferr, int* ndegs, int32_t* toff,
+                                                   double* tval) {
+    const int nx = S.a.n[0], ny = S.a.n[1];
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S.a.n_irr;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lin = S.a.irr_lin[s];
+        const int idx[3] = {(int)(lin % nx), (int)((lin / nx) % ny), (int)(lin / ((int64_t)nx * ny))};
+        const int64_t st[3] = {1, nx, (int64_t)nx * ny};
+        int cn = 0, bn = 0, nt = 0, ndeg = 0, err = kSideNoErr;
+        const int t0 = COUNT ? 0 : task_off[s];
+        for (int L = 0; L < 27 && err == kSideNoErr; ++L) {
+            Line ln;
+            line_at(S, idx, st, L, ln);
+            if (ln.mask == 0 || ln.mask == 7) continue;  // regular or dropped line
+            for (int q = -1; q <= 1 && err == kSideNoErr; ++q)
+                if (!((ln.mask >> (1 - q)) & 1)) {
+                    if (cn == kMaxRaw) {
+                        err = side_err(L, 0, 0, DETAIL_OVERFLOW);
+                        break;
+                    }
+                    if (!COUNT) {
+                        toff[s * kMaxRaw + cn] = (int32_t)(ln.bl + q * st[ln.d] - lin);
+                        tval[s * kMaxRaw + cn] = -ln.w * Rc(S.ax[ln.d], ln.m, q);
+                    }
+                    ++cn;
                 }
-                if (R.err) return;
+            for (int k = 0; k < line_nops(ln.mask) && err == kSideNoErr; ++k) {
+                const OpSpec o = op_spec(ln.mask, k, ln.a, ln.c);
+                OpWalk W;
+                op_walk(S, ln, o, lin, st, W);
+                if (W.err) {
+                    err = side_err(L, k, 1, W.err);
+                    break;
+                }
+                ndeg += W.deg ? 1 : 0;
+                if (!COUNT) tasks[t0 + nt] = SideTask{(int)s, 2 * L + k, cn, bn};
+                ++nt;
+                cn += W.ng;
+                bn += W.nib;
+                // adds past the slice: the operator still runs, for a singular
+                // matrix comes first, but stores nothing
+                if (cn > kMaxRaw || bn > kMaxBib) err = side_err(L, k, 3, DETAIL_OVERFLOW);
             }
+        }
+        if (COUNT) {
+            ntask[s] = nt;
+        } else {
+            ccount[s] = cn;
+            bcount[s] = bn;
+            ferr[s] = err;
+            ndegs[s] = ndeg;
+        }
+    }
+}
+
+// One modified operator per thread: its walk again, the moment matching of
+// Eqs. mat1-mat4 (matrix M of Eq. M), and its correction adds and IBI
+// weights (script B of Eq. bc), scaled by the line's weight, at the places
+// k_side_plan gave them.
+__global__ void __launch_bounds__(64) k_side_solve(SideArgs S, const SideTask* tasks, int64_t ntasks, int* ferr,
+                                                   int32_t* toff, double* tval, int32_t* tbidx, double* tbval) {
+    const int nx = S.a.n[0], ny = S.a.n[1];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntasks;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const SideTask T = tasks[t];
+        const int64_t s = T.slot;
+        const int L = T.code >> 1, k = T.code & 1;
+        const int64_t lin = S.a.irr_lin[s];
+        const int idx[3] = {(int)(lin % nx), (int)((lin / nx) % ny), (int)(lin / ((int64_t)nx * ny))};
+        const int64_t st[3] = {1, nx, (int64_t)nx * ny};
+        Line ln;
+        line_at(S, idx, st, L, ln);
+        const OpSpec o = op_spec(ln.mask, k, ln.a, ln.c);
+        OpWalk W;
+        op_walk(S, ln, o, lin, st, W);
+        const int d = ln.d, ng = W.ng, nib = W.nib, M = ng + nib;
+        for (int q = 0; q < nib; ++q) W.xi[ng + q] = S.ibi_xyz[3 * (int64_t)W.ib[q] + d];
+        const double xe = S.X[d][ln.base[d] + o.e];
+        double xs[2];
+        for (int q = 0; q < o.ns; ++q) xs[q] = S.X[d][ln.base[d] + o.surv[q]];
+        double hs = 0.0;
+        for (int q = 1; q < M; ++q) hs = fmax(hs, fabs(W.xi[q] - xe));
+        double cc[7];
+        if (!moment_solve(M, W.xi, xe, o.ns, xs, o.Ls, hs, cc)) {
+            atomicMin(&ferr[s], side_err(L, k, 2, DETAIL_SINGULAR));
+            continue;
+        }
+        if (T.cpos + ng > kMaxRaw || T.bpos + nib > kMaxBib) continue;
+        for (int q = 0; q < ng; ++q) {
+            toff[s * kMaxRaw + T.cpos + q] = W.offs[q];
+            tval[s * kMaxRaw + T.cpos + q] = ln.w * cc[q];
+        }
+        for (int q = 0; q < nib; ++q) {
+            tbidx[s * kMaxBib + T.bpos + q] = W.ib[q];
+            tbval[s * kMaxBib + T.bpos + q] = ln.w * cc[ng + q];
+        }
     }
 }
 
@@ -628,52 +722,33 @@ __device__ void record_error(DevError* e, int code, int lin, int detail) {
     }
 }
 
-// Builds the row of every irregular point once: its correction adds (in the
-// order of the lines) and IBI weights go to fixed-capacity slices of the
-// scratch (kMaxRaw / kMaxBib per slot) with their counts, its K row to krow.
-// k_side_merge then merges equal offsets and a last kernel compacts the
-// scratch into CSR order.
-__global__ void __launch_bounds__(64) k_side(SideArgs S, int* ccount, int* bcount, int32_t* toff, double* tval,
-                                             int32_t* tbidx, double* tbval, double* krow,
-                                             unsigned long long* ndeg, DevError* err) {
+// Per irregular point: its first error (none: the counts stand and its
+// degenerate operators are counted), and its Shortley-Weller row of K.
+__global__ void k_side_finish(SideArgs S, int* ccount, int* bcount, const int* ferr, const int* ndegs,
+                              double* krow, unsigned long long* ndeg, DevError* err) {
     const int nx = S.a.n[0], ny = S.a.n[1];
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S.a.n_irr;
          s += (int64_t)gridDim.x * blockDim.x) {
-        RawAcc corr{0, toff + s * kMaxRaw, tval + s * kMaxRaw};
-        BibAcc bib{0, tbidx + s * kMaxBib, tbval + s * kMaxBib};
-        RowCtx R;
-        R.lin = S.a.irr_lin[s];
-        R.idx[0] = (int)(R.lin % nx);
-        R.idx[1] = (int)((R.lin / nx) % ny);
-        R.idx[2] = (int)(R.lin / ((int64_t)nx * ny));
-        R.st[0] = 1;
-        R.st[1] = nx;
-        R.st[2] = (int64_t)nx * ny;
-        R.corr = &corr;
-        R.bib = &bib;
-        R.ndeg = 0;
-        R.err = 0;
-        build_row(S, R);
-        if (R.err) {
-            record_error(err, CFP_EGEOM, (int)R.lin, R.err);
+        const int64_t lin = S.a.irr_lin[s];
+        if (ferr[s] != kSideNoErr) {
+            record_error(err, CFP_EGEOM, (int)lin, ferr[s] & 15);
             ccount[s] = 0;
             bcount[s] = 0;
             continue;
         }
-        ccount[s] = corr.n;
-        bcount[s] = bib.n;
-        if (R.ndeg) atomicAdd(ndeg, (unsigned long long)R.ndeg);
+        if (ndegs[s]) atomicAdd(ndeg, (unsigned long long)ndegs[s]);
+        const int idx[3] = {(int)(lin % nx), (int)((lin / nx) % ny), (int)(lin / ((int64_t)nx * ny))};
         // Shortley-Weller row of K (Eqs. 2ndorder_coef_mod, A7_mod): the IBI
         // distance replaces the spacing on a solid side, whose term is dropped.
         double kr[7];
         kr[0] = 0.0;
         for (int d = 0; d < 3; ++d) {
-            const int m = R.idx[d];
+            const int m = idx[d];
             const double xm = S.X[d][m];
             double fw = S.X[d][m + 1] - xm;
             double bw = xm - S.X[d][m - 1];
-            const int im = ibi_index(S, R.lin, 2 * d);
-            const int ip = ibi_index(S, R.lin, 2 * d + 1);
+            const int im = ibi_index(S, lin, 2 * d);
+            const int ip = ibi_index(S, lin, 2 * d + 1);
             if (im >= 0) bw = xm - S.ibi_xyz[3 * (int64_t)im + d];
             if (ip >= 0) fw = S.ibi_xyz[3 * (int64_t)ip + d] - xm;
             const double ca = 2.0 / (bw * (fw + bw));
@@ -923,11 +998,32 @@ cfp_status classify(cfp_ctx* c) {
     int32_t* tbidx = toff + (size_t)nsl * kMaxRaw;
     CFP_CUDA(pool_malloc(&c->krow, sizeof(double) * 7 * std::max<int64_t>(nirr, 1), c->stream));
     CFP_CUDA(pool_malloc(&c->krow32, sizeof(float) * 7 * std::max<int64_t>(nirr, 1), c->stream));
-    if (nirr)
-        k_side<<<grid_for(nirr, 64), 64, 0, c->stream>>>(S, cnt, cnt2, toff, tval, tbidx, tbval, c->krow, ndeg,
-                                                        c->derr);
-    if (nirr) c->launches += 1;
-    CFP_CUDA(cudaGetLastError());
+    if (nirr) {
+        // plan (count, then place), one thread per operator for the moment
+        // matching, finish; the adds land in the order the row is built in
+        int *ntask = nullptr, *task_off = nullptr, *ferr = nullptr, *ndegs = nullptr;
+        SideTask* tasks = nullptr;
+        CFP_CUDA(pool_malloc(&ntask, sizeof(int) * nirr, c->stream));
+        CFP_CUDA(pool_malloc(&task_off, sizeof(int) * nirr, c->stream));
+        CFP_CUDA(pool_malloc(&ferr, sizeof(int) * nirr, c->stream));
+        CFP_CUDA(pool_malloc(&ndegs, sizeof(int) * nirr, c->stream));
+        k_side_plan<true><<<grid_for(nirr, 128), 128, 0, c->stream>>>(S, ntask, nullptr, nullptr, nullptr, nullptr,
+                                                                      nullptr, nullptr, nullptr, nullptr);
+        c->launches += 1;
+        CFP_CUDA(cudaGetLastError());
+        long long ntasks = 0;
+        CFP_TRY(scan(c, FetchInt{ntask}, SinkOffsets{task_off}, nirr, c->dtotal, &ntasks));
+        CFP_CUDA(pool_malloc(&tasks, sizeof(SideTask) * std::max<long long>(ntasks, 1), c->stream));
+        k_side_plan<false><<<grid_for(nirr, 128), 128, 0, c->stream>>>(S, ntask, task_off, tasks, cnt, cnt2, ferr,
+                                                                       ndegs, toff, tval);
+        if (ntasks)
+            k_side_solve<<<grid_for(ntasks, 64), 64, 0, c->stream>>>(S, tasks, ntasks, ferr, toff, tval, tbidx,
+                                                                    tbval);
+        k_side_finish<<<grid_for(nirr, 128), 128, 0, c->stream>>>(S, cnt, cnt2, ferr, ndegs, c->krow, ndeg, c->derr);
+        c->launches += ntasks ? 3 : 2;
+        CFP_CUDA(cudaGetLastError());
+        for (void* q : {(void*)ntask, (void*)task_off, (void*)ferr, (void*)ndegs, (void*)tasks}) pool_free(q, c->stream);
+    }
     if (nirr) {
         k_side_merge<<<grid_for(32 * nirr, 32 * kMergeWarps), 32 * kMergeWarps, 0, c->stream>>>(nirr, cnt, toff, tval);
         c->launches += 1;
