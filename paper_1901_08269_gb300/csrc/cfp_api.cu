@@ -153,7 +153,7 @@ cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny, cons
     chk(cudaMalloc(&c->dcoef32, sizeof(float) * ncoef), "cudaMalloc");
     for (int d = 0; d < 3; ++d) chk(cudaMalloc(&c->dX[d], sizeof(double) * n[d]), "cudaMalloc");
     chk(cudaMalloc(&c->dbodies, sizeof(cfp_body) * std::max(nbodies, 1)), "cudaMalloc");
-    chk(cudaMalloc(&c->dbound2, sizeof(double) * std::max(nbodies, 1)), "cudaMalloc");
+    chk(cudaMalloc(&c->dsphere32, sizeof(float4) * std::max(nbodies, 1)), "cudaMalloc");
     chk(cudaMalloc(&c->type, (size_t)N), "cudaMalloc");
     chk(cudaMalloc(&c->slot, sizeof(int32_t) * (size_t)N), "cudaMalloc");
     chk(cudaMalloc(&c->dtotal, sizeof(long long) * 8), "cudaMalloc");
@@ -180,17 +180,33 @@ cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny, cons
                 "cudaMemcpyAsync");
             // bounding radius: sphere r, ellipsoid largest semi-axis, torus R + r;
             // the 1e-3 relative margin keeps phi far from zero outside it
-            // (R is a rotation, so the body frame keeps distances)
-            static thread_local std::vector<double> b2;
-            b2.assign(nbodies, 0.0);
+            // (R is a rotation, so the body frame keeps distances).  The
+            // device tests the squared distance in FP32, from the FP32
+            // coordinates and centre: per axis its error is at most
+            // 2.0001 u A (A = the largest |coordinate| + |centre|, u = 2^-24),
+            // the squared distance's at most 7.01 u sum A^2; the threshold
+            // adds 16 u sum A^2 and rounds up, so an FP32 distance above it
+            // means an exact one above the bound.
+            double amax[3];
+            for (int d = 0; d < 3; ++d) {
+                amax[d] = 0.0;
+                for (int i = 0; i < n[d]; ++i) amax[d] = std::max(amax[d], fabs(src[d][i]));
+            }
+            static thread_local std::vector<float4> sp;
+            sp.assign(nbodies, float4{0.f, 0.f, 0.f, 0.f});
             for (int m = 0; m < nbodies; ++m) {
                 const cfp_body& b = bodies[m];
                 const double r = b.kind == CFP_SPHERE ? b.p[0]
                                : b.kind == CFP_ELLIPSOID ? std::max(b.p[0], std::max(b.p[1], b.p[2]))
                                                          : b.p[0] + b.p[1];
-                b2[m] = (r * 1.001) * (r * 1.001);
+                double a2 = 0.0;
+                for (int d = 0; d < 3; ++d) a2 += (amax[d] + fabs(b.c[d])) * (amax[d] + fabs(b.c[d]));
+                const double thr = (r * 1.001) * (r * 1.001) + 16.0 * ldexp(1.0, -24) * a2;
+                float tf = (float)thr;
+                if ((double)tf < thr) tf = nextafterf(tf, INFINITY);
+                sp[m] = float4{(float)b.c[0], (float)b.c[1], (float)b.c[2], tf};
             }
-            chk(cudaMemcpy(c->dbound2, b2.data(), sizeof(double) * nbodies, cudaMemcpyHostToDevice), "cudaMemcpy");
+            chk(cudaMemcpy(c->dsphere32, sp.data(), sizeof(float4) * nbodies, cudaMemcpyHostToDevice), "cudaMemcpy");
         }
         chk(cudaGetLastError(), "k_metrics");
         chk(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
@@ -211,7 +227,7 @@ void cfp_ctx_destroy(cfp_ctx* c) {
         if (c->gexec[q]) cudaGraphExecDestroy(c->gexec[q]);
     free_mg(c);
     free_ilu(c);
-    void* ptrs[] = {c->dcoef64, c->dcoef32, c->dX[0], c->dX[1], c->dX[2], c->dbodies, c->dbound2, c->type, c->slot, c->irr_lin,
+    void* ptrs[] = {c->dcoef64, c->dcoef32, c->dX[0], c->dX[1], c->dX[2], c->dbodies, c->dsphere32, c->type, c->slot, c->irr_lin,
                     c->ibi_off, c->ibi_xyz, c->corr_ptr, c->corr_off, c->corr_val, c->corr_val32, c->bib_ptr,
                     c->bib_idx, c->bib_val, c->krow, c->krow32, c->side_scratch, c->scan_bsum, c->dtotal, c->derr, c->dwait, c->nn_wflip, c->v64, c->v32,
                     c->partial, c->kst, c->rst, c->hs_f, c->hs_g, c->hs_u, c->hs_gi};

@@ -61,26 +61,34 @@ __device__ __forceinline__ double edge_pos(double xa, double xb, double t) {
 struct GeoArgs {
     const double* X[3];
     const cfp_body* bodies;
-    const double* bound2;  // per body: squared radius of a sphere around it, with margin
+    const float4* sphere;  // per body: FP32 centre and threshold of the squared distance (bounding sphere)
     int nb, inside;
     int n[3];
 };
 
-// Sign of the level set at a grid node.  A body is evaluated exactly only
-// when the node lies inside its bounding sphere; outside it phi > 0 holds
+// Sign of the level set at a point.  A body is evaluated exactly only when
+// the point may lie inside its bounding sphere; outside it phi > 0 holds
 // with a margin far above rounding, so the sign (and the classification)
-// is the one the exact evaluation gives.
+// is the one the exact evaluation gives.  The sphere test runs in FP32
+// against a threshold that exceeds the FP32 squared distance of every point
+// within the sphere (set on the host from a bound on the rounding), so it
+// skips only points outside the sphere: the FP64 level set is evaluated
+// wherever it was with an FP64 test, at a fraction of the FP64 work.
 __device__ bool node_solid(const GeoArgs& g, double x, double y, double z) {
     bool solid = false;
     double phi = INFINITY;
+    const float xf = (float)x, yf = (float)y, zf = (float)z;
     for (int m = 0; m < g.nb; ++m) {
         const cfp_body& b = g.bodies[m];
-        const double dx = x - b.c[0], dy = y - b.c[1], dz = z - b.c[2];
-        const double d2 = dx * dx + dy * dy + dz * dz;
         if (g.inside) {
             const double v = body_phi(b, x, y, z);
             if (v < phi) phi = v;
-        } else if (d2 <= g.bound2[m]) {
+            continue;
+        }
+        const float4 sp = g.sphere[m];
+        const float dx = __fsub_rn(xf, sp.x), dy = __fsub_rn(yf, sp.y), dz = __fsub_rn(zf, sp.z);
+        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        if (d2 <= sp.w) {
             const double v = body_phi(b, x, y, z);
             if (v < phi) phi = v;
         }
@@ -900,7 +908,7 @@ cfp_status classify(cfp_ctx* c) {
         g.n[d] = c->n[d];
     }
     g.bodies = c->dbodies;
-    g.bound2 = c->dbound2;
+    g.sphere = c->dsphere32;
     g.nb = (int)c->bodies.size();
     g.inside = c->fluid_inside;
 

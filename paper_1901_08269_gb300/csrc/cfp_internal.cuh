@@ -218,7 +218,7 @@ struct cfp_ctx {
     double* dcoef64 = nullptr;  // 8 arrays per axis, n[d] each
     float* dcoef32 = nullptr;
     cfp_body* dbodies = nullptr;
-    double* dbound2 = nullptr;  // per body: squared bounding radius with margin
+    float4* dsphere32 = nullptr;  // per body: FP32 centre and FP32 bounding threshold (see k_classify_solid)
 
     // classification and side data
     bool classified = false;
