@@ -116,23 +116,49 @@ __global__ void k_classify_solid(GeoArgs g, uint8_t* type, int64_t N) {
     }
 }
 
-__global__ void k_classify_irregular(uint8_t* type, int nx, int ny, int nz) {
-    const int64_t nin = (int64_t)(nx - 2) * (ny - 2) * (nz - 2);
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nin;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int i = 1 + (int)(q % (nx - 2));
-        const int j = 1 + (int)((q / (nx - 2)) % (ny - 2));
-        const int k = 1 + (int)(q / ((int64_t)(nx - 2) * (ny - 2)));
-        const int64_t l = lin3(i, j, k, nx, ny);
-        if (type[l] != CFP_REGULAR) continue;
-        bool irr = false;
-        for (int r = -1; r <= 1; ++r)
-            for (int s = -1; s <= 1; ++s)
-                for (int o = -1; o <= 1; ++o)
-                    irr |= type[lin3(i + o, j + s, k + r, nx, ny)] == CFP_SOLID;
-        // Only the solid flags are read, and a node turns irregular only
-        // from regular, so the in-place update does not race.
-        if (irr) type[l] = CFP_IRREGULAR;
+// A regular interior node turns irregular if one of its 26 neighbours is
+// solid.  Each thread owns node i of row j and marches the planes of one z
+// chunk: per plane it loads the types of rows j - 1, j, j + 1 at i, and the
+// warp ORs the solid flags with its x neighbours (lanes i - 1, i + 1) by
+// shuffles, so the 3 x 3 (x, y) dilation of a plane costs three loads per
+// node; three consecutive planes' dilations decide the plane between them.
+// A warp covers nodes i0 .. i0 + 31 and marks i0 + 1 .. i0 + 30 (its edge
+// lanes only feed their neighbours).  Only the solid flags are read, and a
+// node turns irregular only from regular, so the in-place update does not
+// race.
+constexpr int kIrrPlanes = 16;  // planes per thread
+constexpr int kIrrWarps = 8;    // warps per block
+
+__global__ void __launch_bounds__(32 * kIrrWarps) k_classify_irregular(uint8_t* type, int nx, int ny, int nz) {
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * kIrrWarps + (threadIdx.x >> 5)) * 30 + lane;
+    const int j = 1 + blockIdx.y;
+    const int k0 = 1 + blockIdx.z * kIrrPlanes, k1 = min(k0 + kIrrPlanes, nz - 1);
+    const bool inx = i < nx;
+    const bool mine = lane >= 1 && lane <= 30 && i <= nx - 2;
+    const int64_t row = (int64_t)nx;
+    uint8_t* col = type + ((int64_t)j * nx + (inx ? i : 0));  // node (i, j) of plane 0
+    const int64_t pl = (int64_t)nx * ny;
+    // the dilated solid flag of plane k at (i, j), and the node's own type
+    auto dil = [&](int k, uint8_t& own) -> bool {
+        bool s = false;
+        own = CFP_SOLID;
+        if (inx) {
+            const uint8_t* c = col + k * pl;
+            own = c[0];
+            s = c[-row] == CFP_SOLID || own == CFP_SOLID || c[row] == CFP_SOLID;
+        }
+        const unsigned b = s ? 1u : 0u;
+        return (b | __shfl_up_sync(0xffffffffu, b, 1) | __shfl_down_sync(0xffffffffu, b, 1)) != 0u;
+    };
+    uint8_t tm, t0, tp;
+    bool dm = dil(k0 - 1, tm), d0 = dil(k0, t0);
+    for (int k = k0; k < k1; ++k) {
+        const bool dp = dil(k + 1, tp);
+        if (mine && t0 == CFP_REGULAR && (dm || d0 || dp)) col[k * pl] = CFP_IRREGULAR;
+        dm = d0;
+        d0 = dp;
+        t0 = tp;
     }
 }
 
@@ -915,8 +941,12 @@ cfp_status classify(cfp_ctx* c) {
     launch_metrics(c);  // the 1D grid metrics are rebuilt with every classification
     k_classify_solid<<<grid_for(N, 256), 256, 0, c->stream>>>(g, c->type, N);
     c->launches += 2;
-    k_classify_irregular<<<grid_for((int64_t)(nx - 2) * (ny - 2) * (nz - 2), 256), 256, 0, c->stream>>>(
-        c->type, nx, ny, nz);
+    {
+        const int nw = (nx - 2 + 29) / 30;
+        const dim3 gi((unsigned)((nw + kIrrWarps - 1) / kIrrWarps), (unsigned)(ny - 2),
+                      (unsigned)((nz - 2 + kIrrPlanes - 1) / kIrrPlanes));
+        k_classify_irregular<<<gi, 32 * kIrrWarps, 0, c->stream>>>(c->type, nx, ny, nz);
+    }
     CFP_CUDA(cudaGetLastError());
 
     long long h = 0;
