@@ -153,7 +153,7 @@ cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny, cons
     chk(cudaMalloc(&c->dcoef32, sizeof(float) * ncoef), "cudaMalloc");
     for (int d = 0; d < 3; ++d) chk(cudaMalloc(&c->dX[d], sizeof(double) * n[d]), "cudaMalloc");
     chk(cudaMalloc(&c->dbodies, sizeof(cfp_body) * std::max(nbodies, 1)), "cudaMalloc");
-    chk(cudaMalloc(&c->dsphere32, sizeof(float4) * std::max(nbodies, 1)), "cudaMalloc");
+    chk(cudaMalloc(&c->dbody32, sizeof(Body32) * std::max(nbodies, 1)), "cudaMalloc");
     chk(cudaMalloc(&c->type, (size_t)N), "cudaMalloc");
     chk(cudaMalloc(&c->slot, sizeof(int32_t) * (size_t)N), "cudaMalloc");
     chk(cudaMalloc(&c->dtotal, sizeof(long long) * 8), "cudaMalloc");
@@ -192,8 +192,8 @@ cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny, cons
                 amax[d] = 0.0;
                 for (int i = 0; i < n[d]; ++i) amax[d] = std::max(amax[d], fabs(src[d][i]));
             }
-            static thread_local std::vector<float4> sp;
-            sp.assign(nbodies, float4{0.f, 0.f, 0.f, 0.f});
+            static thread_local std::vector<Body32> sp;
+            sp.assign(nbodies, Body32{});
             for (int m = 0; m < nbodies; ++m) {
                 const cfp_body& b = bodies[m];
                 const double r = b.kind == CFP_SPHERE ? b.p[0]
@@ -204,9 +204,17 @@ cfp_status cfp_ctx_create(const double* x, int nx, const double* y, int ny, cons
                 const double thr = (r * 1.001) * (r * 1.001) + 16.0 * ldexp(1.0, -24) * a2;
                 float tf = (float)thr;
                 if ((double)tf < thr) tf = nextafterf(tf, INFINITY);
-                sp[m] = float4{(float)b.c[0], (float)b.c[1], (float)b.c[2], tf};
+                Body32& B = sp[m];
+                B.kind = b.kind;
+                for (int q = 0; q < 3; ++q) {
+                    B.c[q] = (float)b.c[q];
+                    B.p[q] = (float)b.p[q];
+                    B.ip[q] = b.kind == CFP_ELLIPSOID ? (float)(1.0 / b.p[q]) : 0.f;
+                }
+                for (int q = 0; q < 9; ++q) B.R[q] = (float)b.R[q];
+                B.thr = tf;
             }
-            chk(cudaMemcpy(c->dsphere32, sp.data(), sizeof(float4) * nbodies, cudaMemcpyHostToDevice), "cudaMemcpy");
+            chk(cudaMemcpy(c->dbody32, sp.data(), sizeof(Body32) * nbodies, cudaMemcpyHostToDevice), "cudaMemcpy");
         }
         chk(cudaGetLastError(), "k_metrics");
         chk(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
@@ -227,7 +235,7 @@ void cfp_ctx_destroy(cfp_ctx* c) {
         if (c->gexec[q]) cudaGraphExecDestroy(c->gexec[q]);
     free_mg(c);
     free_ilu(c);
-    void* ptrs[] = {c->dcoef64, c->dcoef32, c->dX[0], c->dX[1], c->dX[2], c->dbodies, c->dsphere32, c->type, c->slot, c->irr_lin,
+    void* ptrs[] = {c->dcoef64, c->dcoef32, c->dX[0], c->dX[1], c->dX[2], c->dbodies, c->dbody32, c->type, c->slot, c->irr_lin,
                     c->ibi_off, c->ibi_xyz, c->corr_ptr, c->corr_off, c->corr_val, c->corr_val32, c->bib_ptr,
                     c->bib_idx, c->bib_val, c->krow, c->krow32, c->side_scratch, c->scan_bsum, c->dtotal, c->derr, c->dwait, c->nn_wflip, c->v64, c->v32,
                     c->partial, c->kst, c->rst, c->hs_f, c->hs_g, c->hs_u, c->hs_gi};

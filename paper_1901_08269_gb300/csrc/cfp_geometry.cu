@@ -61,41 +61,85 @@ __device__ __forceinline__ double edge_pos(double xa, double xb, double t) {
 struct GeoArgs {
     const double* X[3];
     const cfp_body* bodies;
-    const float4* sphere;  // per body: FP32 centre and threshold of the squared distance (bounding sphere)
+    const Body32* b32;     // per body: FP32 copy (certified sign, bounding-sphere threshold)
     int nb, inside;
     int n[3];
 };
 
-// Sign of the level set at a point.  A body is evaluated exactly only when
-// the point may lie inside its bounding sphere; outside it phi > 0 holds
-// with a margin far above rounding, so the sign (and the classification)
-// is the one the exact evaluation gives.  The sphere test runs in FP32
-// against a threshold that exceeds the FP32 squared distance of every point
-// within the sphere (set on the host from a bound on the rounding), so it
-// skips only points outside the sphere: the FP64 level set is evaluated
-// wherever it was with an FP64 test, at a fraction of the FP64 work.
+constexpr float kU32 = 5.9604645e-8f;  // 2^-24, the unit roundoff of FP32
+
+// The sign of body b's level set at a point from an FP32 evaluation: -1 or
+// +1 where the FP32 value lies farther from zero than twice a bound on its
+// rounding error (the factor covers the bound's own FP32 rounding and
+// body_phi's FP64 one, both far smaller), so that body_phi has that sign;
+// 0 where only body_phi can tell.  With u = 2^-24, A_j = |x_j| + |c_j|
+// and W_i = sum_j |R_ji| A_j (>= |q_i|; q_i's error is at most 6.01 u W_i):
+//   sphere     |phi32 - phi| <= 16.1 u sum W_i^2 + 4.01 u p^2;
+//   ellipsoid  with V_i = W_i / p_i: <= 20.1 u sum V_i^2 + 1.01 u;
+//   torus      rho's error E_rho <= 14.05 u (W_0^2 + W_1^2) / rho32 + u rho32,
+//              s = rho - R's E_s <= E_rho + u (rho32 + 2 R), S = |s32| + E_s:
+//              <= 2 E_s S + 3.01 u S^2 + 15.05 u W_2^2 + 4.01 u r^2.
+__device__ int body_sign32(const Body32& b, float x, float y, float z) {
+    const float d0 = __fsub_rn(x, b.c[0]), d1 = __fsub_rn(y, b.c[1]), d2 = __fsub_rn(z, b.c[2]);
+    const float a0 = fabsf(x) + fabsf(b.c[0]), a1 = fabsf(y) + fabsf(b.c[1]), a2 = fabsf(z) + fabsf(b.c[2]);
+    const float* R = b.R;
+    const float q0 = __fadd_rn(__fadd_rn(__fmul_rn(R[0], d0), __fmul_rn(R[3], d1)), __fmul_rn(R[6], d2));
+    const float q1 = __fadd_rn(__fadd_rn(__fmul_rn(R[1], d0), __fmul_rn(R[4], d1)), __fmul_rn(R[7], d2));
+    const float q2 = __fadd_rn(__fadd_rn(__fmul_rn(R[2], d0), __fmul_rn(R[5], d1)), __fmul_rn(R[8], d2));
+    const float W0 = fabsf(R[0]) * a0 + fabsf(R[3]) * a1 + fabsf(R[6]) * a2;
+    const float W1 = fabsf(R[1]) * a0 + fabsf(R[4]) * a1 + fabsf(R[7]) * a2;
+    const float W2 = fabsf(R[2]) * a0 + fabsf(R[5]) * a1 + fabsf(R[8]) * a2;
+    float phi, m;
+    if (b.kind == CFP_SPHERE) {
+        const float s = __fadd_rn(__fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)), __fmul_rn(q2, q2));
+        const float pp = __fmul_rn(b.p[0], b.p[0]);
+        phi = __fsub_rn(s, pp);
+        m = 2.f * kU32 * (16.1f * (W0 * W0 + W1 * W1 + W2 * W2) + 4.01f * pp);
+    } else if (b.kind == CFP_ELLIPSOID) {
+        const float e0 = __fmul_rn(q0, b.ip[0]), e1 = __fmul_rn(q1, b.ip[1]), e2 = __fmul_rn(q2, b.ip[2]);
+        const float s = __fadd_rn(__fadd_rn(__fmul_rn(e0, e0), __fmul_rn(e1, e1)), __fmul_rn(e2, e2));
+        phi = __fsub_rn(s, 1.f);
+        const float V0 = W0 * b.ip[0], V1 = W1 * b.ip[1], V2 = W2 * b.ip[2];
+        m = 2.f * kU32 * (20.1f * (V0 * V0 + V1 * V1 + V2 * V2) + 1.01f);
+    } else {
+        const float t = __fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1));
+        const float rho = __fsqrt_rn(t);
+        if (!(rho > 0.f)) return 0;  // on the torus axis: no bound on rho's error
+        const float s = __fsub_rn(rho, b.p[0]);
+        phi = __fsub_rn(__fadd_rn(__fmul_rn(s, s), __fmul_rn(q2, q2)), __fmul_rn(b.p[1], b.p[1]));
+        const float er = 14.05f * kU32 * (W0 * W0 + W1 * W1) / rho + kU32 * rho;
+        const float es = er + kU32 * (rho + 2.f * b.p[0]);
+        const float S = fabsf(s) + es;
+        m = 2.f * (2.f * es * S + kU32 * (3.01f * S * S + 15.05f * W2 * W2 + 4.01f * b.p[1] * b.p[1]));
+    }
+    return phi > m ? 1 : (phi < -m ? -1 : 0);
+}
+
+// Whether a point is solid (fluid outside the bodies: some body's level
+// set <= 0; fluid inside: every body's >= 0).  Each body's sign comes from
+// body_sign32 where it can tell, else from body_phi, so it is the sign
+// body_phi gives.  Outside mode, a body is looked at only when the point may
+// lie inside its bounding sphere (outside it phi > 0 holds with a margin far
+// above rounding); that test runs in FP32 against a threshold above the
+// FP32 squared distance of every point within the sphere (set on the host
+// from a bound on the rounding), so it skips only points outside.
 __device__ bool node_solid(const GeoArgs& g, double x, double y, double z) {
-    bool solid = false;
-    double phi = INFINITY;
     const float xf = (float)x, yf = (float)y, zf = (float)z;
     for (int m = 0; m < g.nb; ++m) {
-        const cfp_body& b = g.bodies[m];
-        if (g.inside) {
-            const double v = body_phi(b, x, y, z);
-            if (v < phi) phi = v;
-            continue;
+        const Body32& b = g.b32[m];
+        if (!g.inside) {
+            const float dx = __fsub_rn(xf, b.c[0]), dy = __fsub_rn(yf, b.c[1]), dz = __fsub_rn(zf, b.c[2]);
+            const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            if (d2 > b.thr) continue;
         }
-        const float4 sp = g.sphere[m];
-        const float dx = __fsub_rn(xf, sp.x), dy = __fsub_rn(yf, sp.y), dz = __fsub_rn(zf, sp.z);
-        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-        if (d2 <= sp.w) {
-            const double v = body_phi(b, x, y, z);
-            if (v < phi) phi = v;
+        int sg = body_sign32(b, xf, yf, zf);
+        if (sg == 0) {
+            const double v = body_phi(g.bodies[m], x, y, z);
+            sg = g.inside ? (v < 0.0 ? -1 : 1) : (v <= 0.0 ? -1 : 1);
         }
+        if (sg < 0) return !g.inside;  // outside mode: solid; inside mode: fluid
     }
-    if (g.inside) return -phi <= 0.0;
-    solid = phi <= 0.0;
-    return solid;
+    return g.inside;
 }
 
 // ------------------------------------------------------------ classification
@@ -934,7 +978,7 @@ cfp_status classify(cfp_ctx* c) {
         g.n[d] = c->n[d];
     }
     g.bodies = c->dbodies;
-    g.sphere = c->dsphere32;
+    g.b32 = c->dbody32;
     g.nb = (int)c->bodies.size();
     g.inside = c->fluid_inside;
 

@@ -196,6 +196,15 @@ struct MgLevel {
 }  // namespace cfp
 
 // ------------------------------------------------------------------ context
+// FP32 copy of a body for the certified sign of its level set (the
+// classification's fast path): centre, rotation, parameters, reciprocal
+// semi-axes (ellipsoid), and the threshold of the FP32 bounding-sphere test.
+struct Body32 {
+    float c[3], R[9], p[3], ip[3];
+    float thr;
+    int kind;
+};
+
 struct cfp_ctx {
     int n[3] = {0, 0, 0};
     int64_t N = 0;
@@ -218,7 +227,7 @@ struct cfp_ctx {
     double* dcoef64 = nullptr;  // 8 arrays per axis, n[d] each
     float* dcoef32 = nullptr;
     cfp_body* dbodies = nullptr;
-    float4* dsphere32 = nullptr;  // per body: FP32 centre and FP32 bounding threshold (see k_classify_solid)
+    Body32* dbody32 = nullptr;  // per body: its FP32 copy for the certified level-set sign
 
     // classification and side data
     bool classified = false;
