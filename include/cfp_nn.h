@@ -157,7 +157,7 @@ cfp_status cfp_unet_check(cfp_unet* net);
  *     y = net(r1), alpha = (y, r1) / (y, B y) (the step in the energy norm;
  *     0 unless (y, B y) < 0), z2 = z1 + alpha y, zn = z2 + P(v - B z2); it
  *     keeps zn if ||v - B zn|| < ||v - B z1||, else z1 (the plain
- *     preconditioner as fallback and judge at every step).  Not linear in
+ *     preconditioner as fallback and arbiter at every step).  Not linear in
  *     v, hence the flexible method.  info->refinements counts the steps that
  *     kept the network's direction.
  *   net_guess: with net, the initial iterate is u0 = alpha net(rhs) with the

@@ -9,7 +9,7 @@
 // P the inner preconditioner of K (pre- and post-smoothing), alpha the step
 // along y in the energy norm (independent of the output's scale), and keeps
 // zn only if ||v - B zn|| < ||v - B z1||: the plain preconditioner stays the
-// fallback and the judge at every step.
+// fallback and the arbiter at every step.
 //
 // Everything stays on the device: the Krylov basis V (m + 1 fields) and the
 // directions Z (m fields), the Hessenberg matrix, the Givens rotations, the
