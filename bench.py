@@ -33,7 +33,7 @@ FALLBACK_HBM_GBS = 6800.0
 # preconditioner (8 red-black sweeps) to tol 1e-15, measured by the GPU path
 # with the same preconditioner; the CPU baselines extrapolate with it since
 # the oracle cannot run the 513^3 solve itself.
-FP64_RBGS_ITERS_513 = 579
+FP64_RBGS_ITERS_513 = 535
 
 
 def parse():
