@@ -11,7 +11,9 @@
 // 2ndorder_xx, 2ndorder_coef_mod, A7_mod).
 //
 // The level set is evaluated with explicitly rounded operations (no
-// contraction) so that the classification is reproducible bit for bit.
+// contraction) so that the classification is reproducible bit for bit; an
+// FP32 evaluation with a bound on its rounding decides the sign wherever the
+// bound can tell, which gives the same bits with a fraction of the FP64 work.
 #include <math.h>
 
 #include <algorithm>
